@@ -1,0 +1,325 @@
+"""Benchmark: time to a 1e-8 relative residual of sketched FGMRES on one GB300.
+
+A step is one full solve (every step of the method: residual, inner sGMRES cycles, outer FGMRES steps, final
+iterate and recomputed true residual) of the 3D convection-diffusion system on a 128^3 grid (n = 2,097,152,
+nnz = 14,581,760; beta = (50, 30, 10); b ~ N(0,1) seed 0; inner m = 100, truncation k = 2, sketch s = 400 with 8
+nonzeros per column, seed 1; tol 1e-8), with b and A resident in HBM.  The headline is the plain FP64 solver; the
+FP32-inner and BF16-basis forms are reported beside it on the same inputs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--profile-case]
+
+``--impl reference`` times the CPU oracle (plain FP64 NumPy/SciPy restatement of the method) on a bounded sample
+of the same workload.  ``--profile-case`` runs two short solves for ncu captures and prints nothing else.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "time to 1e-8 rel. residual; inner-cycle HBM GB/s vs peak; FP32-inner vs FP64"
+CFG = workloads.CONFIGS["cd3d_128"]
+WORKLOAD = ("cd3d_128: 3D convection-diffusion 128^3, upwind 7-point, beta=(50,30,10), b~N(0,1) seed 0, x0=0; "
+            "inner sGMRES m=100, k(truncation)=2, sparse-sign sketch s=400 zeta=8 seed 1; FGMRES tol 1e-8")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def alg_bytes_inner_spmv(n, nnz, t, zeta, s, nblk, sv):
+    """Compulsory bytes of one fused inner SpMV + dots + sketch launch (stated in the design doc)."""
+    a = nnz * (sv + 4) + 4 * (n + 1)          # CSR values + column indices + row pointers
+    vec = n * sv * (1 + max(t - 1, 0)) + n * sv  # b_i (gathered once) + older window vectors + w written
+    sk = 2 * n * zeta + 4 * (nblk * s + 1) + sv * nblk * (s + t)  # gather lists, segment table, partials
+    return a + vec + sk
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2506_18408_gb300 import Solver, build
+
+    build.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    A = CFG.build_matrix()
+    b = CFG.build_rhs(A.n)
+    n, nnz = A.n, A.nnz
+    stream = torch.cuda.current_stream()
+    solver = Solver(n, A.row_ptr, A.col, A.val, sketch_seed=CFG.sketch_seed, zeta=CFG.zeta,
+                    max_outer=CFG.max_outer, stream=stream.cuda_stream)
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.empty_like(bd)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2 (129 MB)
+
+    if args.profile_case:
+        solver.set("max_outer", 2)
+        solver.solve(bd, m=CFG.m, s=CFG.s, k=CFG.t, tol=CFG.tol, out=xd)
+        solver.set("precision", "fp32")
+        solver.solve(bd, m=CFG.m, s=CFG.s, k=CFG.t, tol=CFG.tol, out=xd)
+        torch.cuda.synchronize()
+        return
+
+    def timed(precision, K, W, profile=False):
+        solver.set("precision", precision)
+        solver.set("profile", 0)
+        for _ in range(W):
+            solver.solve(bd, m=CFG.m, s=CFG.s, k=CFG.t, tol=CFG.tol, out=xd)
+        solver.set("profile", 1 if profile else 0)
+        times, infos = [], []
+        for _ in range(K):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            _, info = solver.solve(bd, m=CFG.m, s=CFG.s, k=CFG.t, tol=CFG.tol, out=xd)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            infos.append(info)
+        solver.set("profile", 0)
+        return times, infos
+
+    with ClockSampler(local) as clk:
+        t64, i64 = timed("fp64", args.steps, args.warmup, profile=True)
+    t32, i32 = timed("fp32", args.steps, max(3, args.warmup // 2))
+    t16, i16 = timed("bf16", args.steps, max(3, args.warmup // 2))
+    sec = statistics.mean(t64)
+    if dist is not None:
+        tt = torch.tensor([sec], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        sec = float(tt.item())
+
+    # end to end through the public API with pinned host buffers (copies inside the timed region)
+    solver.set("precision", "fp64")
+    bh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    bh.numpy()[:] = b
+    xh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    e2e = []
+    for _ in range(max(2, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info_e = solver.solve(bh.numpy(), m=CFG.m, s=CFG.s, k=CFG.t, tol=CFG.tol, out=xh.numpy())
+        e2e.append(time.perf_counter() - t0)
+    assert info_e["status"] == 0
+
+    last = i64[-1]
+    launches = sum(i["kernel_launches"] for i in i64) / len(i64)
+    k1_ms = sum(i["t_inner_spmv_ms"] for i in i64) / sum(i["n_inner_spmv"] for i in i64)
+    hbm, peak_src = _peaks()
+    from paper_2506_18408_gb300 import sfgmres as py
+
+    # the library's row-block geometry (same rule as the C code): nblk = ceil(n / Bn)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    q, Bn = 1, 32
+    while True:
+        per = -(-n // (sms * q))
+        Bn = -(-per // 32) * 32
+        if Bn <= 8192:
+            break
+        q *= 2
+    nblk = -(-n // Bn)
+    abytes = alg_bytes_inner_spmv(n, nnz, CFG.t, CFG.zeta, CFG.s, nblk, 8)
+    achieved = abytes / (k1_ms / 1e3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get("inner_spmv_fp64_cd3d_128")
+    except Exception:
+        pass
+
+    cpu = cpu_baseline(last["outer_iters"]) if (rank == 0 and not args.no_cpu) else None
+    if rank == 0:
+        res = {
+            "metric": METRIC, "value": sec, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "parallelism": "replicas" if world > 1 else "1gpu",
+                       "l2": "inputs larger than L2 (A is 183 MB) and a 256 MB buffer written between steps"},
+            "solve": {"outer_iters": last["outer_iters"], "total_inner": last["total_inner"],
+                      "rel_res_true": last["rel_res_true"], "inner_k": last["inner_k"],
+                      "solves_per_s": 1.0 / sec},
+            "variants": {
+                "fp32_inner": {"value": statistics.mean(t32), "unit": "s", "outer_iters": i32[-1]["outer_iters"],
+                               "total_inner": i32[-1]["total_inner"], "rel_res_true": i32[-1]["rel_res_true"]},
+                "bf16_basis": {"value": statistics.mean(t16), "unit": "s", "outer_iters": i16[-1]["outer_iters"],
+                               "total_inner": i16[-1]["total_inner"], "rel_res_true": i16[-1]["rel_res_true"]},
+            },
+            "roofline": {"kernel": "k_inner_spmv (fused SpMV + truncated-Arnoldi dots + sketch partials, FP64)",
+                         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_source": peak_src, "traffic": traffic,
+                         "alg_bytes_per_launch": abytes, "avg_launch_ms": k1_ms},
+            "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": 8 * n,
+                    "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": int(round(launches)) * args.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(res))
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(outer_iters):
+    """Oracle (as it stands) on a bounded sample: the first outer FGMRES iteration (one full inner cycle of m = 100
+    sGMRES steps plus the outer step) of the same workload, extrapolated to the solve's outer iteration count."""
+    from oracle import fgmres as ofg
+
+    A = CFG.build_matrix().to_scipy()
+    b = CFG.build_rhs(A.shape[0])
+    from oracle import sketch as osk
+
+    osk.sketch_matrix(A.shape[0], CFG.s, CFG.zeta, CFG.sketch_seed)  # sketch construction outside the sample
+    t0 = time.perf_counter()
+    ofg.fgmres(A, b, m=CFG.m, s=CFG.s, t=CFG.t, tol=CFG.tol, max_outer=1, zeta=CFG.zeta,
+               sketch_seed=CFG.sketch_seed)
+    dt = time.perf_counter() - t0
+    return {"value": dt * outer_iters, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"1 outer iteration (100 inner steps + outer step) timed = {dt:.2f} s, x {outer_iters} "
+                      "outer iterations of the GPU solve"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import fgmres as ofg
+    from oracle import sketch as osk
+
+    A = CFG.build_matrix().to_scipy()
+    b = CFG.build_rhs(A.shape[0])
+    osk.sketch_matrix(A.shape[0], CFG.s, CFG.zeta, CFG.sketch_seed)
+    # a step = one bounded sample: 20 inner sGMRES steps (C1 cap) + the outer step, scaled to a full solve of
+    # 1000 inner steps (10 outer iterations of m = 100, the measured shape of the GPU solve)
+    inner_steps = 20
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ofg.fgmres(A, b, m=inner_steps, s=CFG.s, t=CFG.t, tol=CFG.tol, max_outer=1, zeta=CFG.zeta,
+                   sketch_seed=CFG.sketch_seed, c3=False)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt * (1000 / inner_steps))
+    v = statistics.mean(times)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": f"{inner_steps} inner steps + 1 outer step per timed step, scaled x"
+                                   f"{1000 // inner_steps} to 1000 inner steps"},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * sfgmres.h -- C ABI of the GB300 sketched-FGMRES solver.
+ *
+ * The library solves A x = b for a large sparse nonsymmetric A in CSR form (Section 1 of Guettel & Pearson,
+ * "Stabilizing randomized GMRES through flexible GMRES") by FGMRES (Algorithm 1) whose variable preconditioner is
+ * one cycle of sketched GMRES (Eq. 3; Section 3): a truncated-Arnoldi Krylov basis (Section 4.1), a seeded
+ * sparse-sign subspace embedding S (Eq. 1), and the sketched least-squares problem solved through a Gram-Schmidt QR
+ * with reorthogonalisation, with the inner length chosen by the stop rules C1-C3 of Section 3 (C3 uses the
+ * residual bound of Eq. 5 and the FFOM residual of Eq. 4).
+ *
+ * Every step of the solve runs in this library's CUDA kernels (sm_103a).  The library uses the CUDA runtime only
+ * for memory, streams and events; it has no CPU fallback.
+ *
+ * Conventions
+ *  - Parameter names follow the paper's inner notation through this mapping: `m` = maximum inner sGMRES basis size
+ *    (the paper's k_max, rule C1), `k` = Arnoldi truncation depth (the paper's t), `s` = sketch rows (m <= s << n).
+ *  - Return values: 0 (SFGMRES_OK) on success, positive values for numerical outcomes that still leave a valid
+ *    result, negative values for errors; sfgmres_last_error() then describes the error.
+ *  - Pointers: "device" means memory the current CUDA device can address (cudaMalloc, torch CUDA tensors);
+ *    "host" means ordinary or pinned host memory.  Where an argument accepts both, the library inspects the
+ *    pointer with cudaPointerGetAttributes and stages host data through device buffers it owns.
+ *  - A handle is bound to the device that was current at sfgmres_create and to one CUDA stream; calls on one
+ *    handle must not overlap in time (the handle owns the workspaces).  Different handles are independent.
+ *  - Every call that launches kernels returns only after its work has completed on the handle's stream.
+ */
+#ifndef SFGMRES_H
+#define SFGMRES_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SFGMRES_API __attribute__((visibility("default")))
+#else
+#define SFGMRES_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------------------------ */
+#define SFGMRES_OK 0               /* converged: ||b - A x|| <= tol * ||b|| (recomputed, not estimated) */
+#define SFGMRES_NOT_CONVERGED 1    /* outer budget exhausted; x holds the last FGMRES iterate (still valid) */
+#define SFGMRES_BREAKDOWN 2        /* an inner cycle produced no correction (first sketched column zero);
+                                      x holds the last FGMRES iterate */
+#define SFGMRES_ERR_INVALID_ARG (-1)
+#define SFGMRES_ERR_CUDA (-2)
+#define SFGMRES_ERR_OOM (-3)
+#define SFGMRES_ERR_NAN (-4)       /* NaN or Inf met in b, x0 or a reduction */
+
+/* ---- sfgmres_create flags ---------------------------------------------------------------------------------- */
+#define SFGMRES_CSR_HOST 1         /* row_ptr/col_idx/vals are host pointers (default: device pointers) */
+
+/* ---- option keys for sfgmres_set_option / sfgmres_get_option ---------------------------------------------- */
+#define SFGMRES_OPT_PRECISION 1      /* inner-cycle precision: 0 = FP64 (default), 1 = FP32 values/basis/sketch
+                                        with FP32 accumulation, 2 = as 1 with the basis stored in BF16.  The outer
+                                        FGMRES, the sketched QR and least squares, z = B y and the residual
+                                        recomputation are FP64 in every mode. */
+#define SFGMRES_OPT_ZETA 2           /* nonzeros per sketch column, 1..16 (default 8; 1 = Clarkson-Woodruff) */
+#define SFGMRES_OPT_COND_THRESHOLD 3 /* rule C2 threshold on the condition proxy of S A B_k (default 1e15) */
+#define SFGMRES_OPT_C3 4             /* rule C3 (Eq. 5 bound stops the inner cycle): 1 = on (default), 0 = off */
+#define SFGMRES_OPT_MAX_OUTER 5      /* outer FGMRES iteration budget (default 50) */
+#define SFGMRES_OPT_SKETCH_KIND 6    /* 0 = sparse-sign (default), 1 = identity (requires s == n; tests) */
+#define SFGMRES_OPT_PROFILE 7        /* 1 = time the kernels with CUDA events (see sfgmres_stats), default 0 */
+#define SFGMRES_OPT_SPMV_VECTOR 8    /* lanes per CSR row in the SpMV (2,4,8,16,32); 0 = chosen from nnz/n */
+
+/* ---- solve statistics ------------------------------------------------------------------------------------- */
+/* Filled by sfgmres_solve when a non-NULL pointer is passed.  The array members are caller-owned host arrays of
+ * length hist_cap (or NULL); entries beyond outer_iters (or beyond hist_cap) are left untouched. */
+typedef struct {
+    int32_t status;          /* same as the return value */
+    int32_t outer_iters;     /* FGMRES iterations performed */
+    int32_t total_inner;     /* sum over cycles of the inner basis size k */
+    int32_t hist_cap;        /* capacity of the arrays below (set by the caller) */
+    int32_t* inner_k;        /* inner basis size k of each cycle */
+    int32_t* inner_reason;   /* rule that ended each cycle: 1 = C1, 2 = C2, 3 = C3, 4 = Arnoldi breakdown,
+                                5 = degenerate (no column accepted) */
+    double* res_est;         /* ||beta e1 - H_j y_j|| / ||b|| after each outer step (Givens estimate) */
+    double* ffom_res;        /* FFOM residual norm (Eq. 4) / ||b|| after each outer step */
+    double rel_res_true;     /* recomputed ||b - A x|| / ||b|| of the returned x */
+    double rel_res_est;      /* last Givens estimate */
+    int64_t kernel_launches; /* kernels this call launched */
+    /* with SFGMRES_OPT_PROFILE = 1 (otherwise 0): */
+    double t_inner_spmv_ms;  /* total device time of the fused inner SpMV + dot + sketch kernel */
+    int64_t n_inner_spmv;    /* its launches */
+    double t_inner_axpy_ms;  /* total device time of the truncated-Arnoldi update kernel */
+    int64_t n_inner_axpy;
+    double t_qr_ms;          /* total device time of the sketched-QR update kernel */
+    int64_t n_qr;
+    double t_total_ms;       /* device time of the whole solve (first to last kernel) */
+} sfgmres_stats;
+
+typedef struct sfgmres_ctx* sfgmres_t;
+
+/* Create a solver handle for the n x n matrix A given in CSR form (Section 1: A x = b, A large, sparse,
+ * nonsymmetric), and the seed of the subspace embedding S (Eq. 1), which is drawn afresh from SplitMix64 for every
+ * sketch size s but always from this seed.
+ *   out        receives the handle (host pointer; *out is NULL on failure)
+ *   n, nnz     order and number of stored entries; 1 <= n, 0 <= nnz < 2^31
+ *   row_ptr    int64[n+1], nondecreasing, row_ptr[0] = 0, row_ptr[n] = nnz
+ *   col_idx    int32[nnz], column indices in [0, n) (any order within a row; repeated entries are summed)
+ *   vals       float64[nnz]
+ *   flags      SFGMRES_CSR_HOST if the three arrays are host pointers, else 0 (device pointers)
+ *   stream     cudaStream_t to run on (NULL: the library creates a non-blocking stream of its own)
+ * The library copies the CSR arrays (the caller may free them on return) and validates them: a violation of the
+ * rules above returns SFGMRES_ERR_INVALID_ARG.  Allocation failure returns SFGMRES_ERR_OOM. */
+SFGMRES_API int sfgmres_create(sfgmres_t* out, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                   const double* vals, uint64_t sketch_seed, int32_t flags, void* stream);
+
+/* Set / read an option (SFGMRES_OPT_*).  Values are passed as double.  Unknown keys or out-of-range values return
+ * SFGMRES_ERR_INVALID_ARG and leave the option unchanged. */
+SFGMRES_API int sfgmres_set_option(sfgmres_t h, int32_t key, double value);
+SFGMRES_API int sfgmres_get_option(sfgmres_t h, int32_t key, double* value);
+
+/* Solve A x = b by FGMRES (Algorithm 1) preconditioned with sGMRES cycles (Section 3), starting from x0.
+ *   b, x0, x   n float64 each, device or host pointers (see Conventions); x0 may be NULL (zero initial guess)
+ *              and may alias x.  x is written on every non-error return.
+ *   m          maximum inner basis size (rule C1), 1 <= m <= 1024, m <= s
+ *   s          sketch rows, zeta <= s <= 4096 (identity sketch: s == n <= 4096)
+ *   k          Arnoldi truncation depth t of the inner basis, 0 <= k <= 8
+ *   tol        target relative residual ||b - A x|| / ||b||, 0 < tol < 1
+ *   st         optional statistics (may be NULL)
+ * Special cases: ||b|| = 0 gives x = 0 and SFGMRES_OK; if ||b - A x0|| <= tol ||b|| then x = x0, 0 iterations.
+ * The outer loop stops when the Givens estimate meets tol and the recomputed residual confirms it; otherwise it
+ * continues until SFGMRES_OPT_MAX_OUTER iterations (SFGMRES_NOT_CONVERGED).  Returns a status code. */
+SFGMRES_API int sfgmres_solve(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m, int32_t s, int32_t k,
+                  double tol, sfgmres_stats* st);
+
+/* One sGMRES preconditioner application z = B_k y_k ~ A^{-1} v (Eq. 3 with r0 = v, x0 = 0; Section 3), with rules
+ * C1 and C2 only (C3 needs an outer iteration).  v must have unit 2-norm (it is the outer Arnoldi vector).
+ *   v, z       n float64, device pointers
+ *   m, s, k    as for sfgmres_solve
+ *   basis      optional device float64[(m+1) * n], column-major: receives the normalised basis vectors b_1..b_kb
+ *              (kb = k_out, plus one more vector when C2 dropped a column); NULL to skip
+ *   y          optional device float64[m]: receives y_k (first k_out entries); NULL to skip
+ *   k_out      host int32: receives k;   reason_out: host int32 (may be NULL): rule that ended the cycle
+ * Returns SFGMRES_OK, or SFGMRES_BREAKDOWN when no column was accepted (z = 0). */
+SFGMRES_API int sfgmres_inner_cycle(sfgmres_t h, const double* v, double* z, int32_t m, int32_t s, int32_t k, double* basis,
+                        double* y, int32_t* k_out, int32_t* reason_out);
+
+/* c = S v for the handle's embedding with s rows (Eq. 1).  v: device float64[n], c: device float64[s]. */
+SFGMRES_API int sfgmres_sketch_apply(sfgmres_t h, int32_t s, const double* v, double* c);
+
+/* The nonzero pattern of S with s rows: for column j and slot l < zeta, rows[j*zeta + l] in [0, s) and
+ * signs[j*zeta + l] in {+1, -1} (the value is sign / sqrt(zeta)).  rows: device int32[n*zeta],
+ * signs: device int8[n*zeta].  Draw rule (SplitMix64, counter-based): slot q = j*zeta + l draws its row from
+ * outputs 128q + 2a (attempt a = 0..63, first row not used by slots 0..l-1 of the column; cyclic probe after 64
+ * collisions; row = ((h >> 32) * s) >> 32) and its sign from bit 63 of output 128q + 1. */
+SFGMRES_API int sfgmres_sketch_pattern(sfgmres_t h, int32_t s, int32_t* rows, int8_t* signs);
+
+/* y = A x in FP64 (device pointers, n each). */
+SFGMRES_API int sfgmres_spmv(sfgmres_t h, const double* x, double* y);
+
+/* Release the handle and everything it owns.  NULL is accepted. */
+SFGMRES_API int sfgmres_destroy(sfgmres_t h);
+
+/* Description of the last error on this handle (h == NULL: of the last failed sfgmres_create in this thread).
+ * The string stays valid until the next call on the same handle. */
+SFGMRES_API const char* sfgmres_last_error(sfgmres_t h);
+
+/* Library version string. */
+SFGMRES_API const char* sfgmres_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFGMRES_H */

@@ -1,0 +1,123 @@
+// Shared device helpers and solver-state layouts of the sketched-FGMRES CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace sfg {
+
+constexpr int kWarp = 32;
+constexpr int kMaxTrunc = 8;    // largest Arnoldi truncation depth t
+constexpr int kMaxZeta = 16;    // largest number of nonzeros per sketch column
+constexpr int kMaxS = 4096;     // largest sketch size
+constexpr int kMaxM = 1024;     // largest inner basis size
+constexpr int kBlockRowsMax = 8192;  // rows per row block (local sketch offsets need <= 15 bits)
+
+// ------------------------------------------------------------------------------------------------------------
+// Precision traits.  VT: storage type of inner basis vectors; AT: arithmetic / accumulation type; MT: matrix values.
+template <typename T> struct Num;
+template <> struct Num<double> {
+    __device__ __forceinline__ static double to_f(double x) { return x; }
+};
+template <> struct Num<float> {
+    __device__ __forceinline__ static float to_f(float x) { return x; }
+};
+
+__device__ __forceinline__ double load_as(const double* p, double) { return __ldg(p); }
+__device__ __forceinline__ float load_as(const float* p, float) { return __ldg(p); }
+__device__ __forceinline__ float load_as(const __nv_bfloat16* p, float) { return __bfloat162float(*p); }
+__device__ __forceinline__ double ld_plain(const double* p) { return *p; }
+__device__ __forceinline__ float ld_plain(const float* p) { return *p; }
+__device__ __forceinline__ float ld_plain(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+__device__ __forceinline__ void store_as(double* p, double v) { *p = v; }
+__device__ __forceinline__ void store_as(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_as(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+// ------------------------------------------------------------------------------------------------------------
+// Deterministic reductions (fixed shuffle trees, fixed shared-memory order).
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over all threads of the block; result valid in every thread.  `red` holds >= 32 T.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    T r = (lane < nw) ? red[lane] : T(0);
+    r = warp_sum(r);
+    return r;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014), counter form: output k of the stream started at state `seed`.
+__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm64_draw(uint64_t seed, uint64_t k) {
+    return sm64_mix(seed + (k + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+
+// Rows and signs of sketch column j (zeta distinct rows in [0, s)).  Draw rule: slot q = j*zeta + l takes its row
+// from outputs 128q + 2a for attempts a = 0..63 (first row unused by the column's earlier slots; after 64
+// collisions, the next free row cyclically after the last candidate), row = ((h >> 32) * s) >> 32, and its sign
+// from bit 63 of output 128q + 1 (0 = +).
+__device__ __forceinline__ void sketch_column(uint64_t seed, int64_t j, int zeta, int s, int* rows, int* neg) {
+    for (int l = 0; l < zeta; ++l) {
+        const uint64_t base = (uint64_t)(j * zeta + l) * 128ull;
+        int cand = 0;
+        bool dup = true;
+        for (int a = 0; a < 64 && dup; ++a) {
+            const uint64_t h = sm64_draw(seed, base + 2ull * (uint64_t)a);
+            cand = (int)(((h >> 32) * (uint64_t)s) >> 32);
+            dup = false;
+            for (int q = 0; q < l; ++q) dup |= (rows[q] == cand);
+        }
+        while (dup) {
+            cand = (cand + 1 == s) ? 0 : cand + 1;
+            dup = false;
+            for (int q = 0; q < l; ++q) dup |= (rows[q] == cand);
+        }
+        rows[l] = cand;
+        neg[l] = (int)(sm64_draw(seed, base + 1ull) >> 63);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Device-resident solver state (one instance per handle).
+struct CycleState {
+    int stopped;   // the inner cycle has ended (no more columns)
+    int k;         // accepted inner basis size
+    int reason;    // 1 C1, 2 C2, 3 C3, 4 breakdown, 5 degenerate
+    int c3_on;     // rule C3 active for this cycle
+    double dmax, dmin;    // extremes of |r_ll| for the condition proxy
+    double rho;           // sketched residual of the last accepted column
+    double c3_scale;      // FFOM residual of the previous outer step (beta at the first)
+    double c3_tol;        // tol * ||b||
+    double cond_thr;
+};
+
+struct OuterState {
+    int j;            // index of the current outer step (0-based)
+    int conv_est;     // the Givens estimate met the tolerance at the last step
+    int breakdown;    // h_{j+1,j} == 0 (exact) at the last step
+    int nan;          // NaN/Inf seen in a reduction
+    double beta;      // ||r0||
+    double bnorm;     // ||b||
+    double est;       // |g_{j+1}|
+    double ffom;      // |g_{j+1}| / |c_j| (FFOM residual, Eq. 4)
+    double true_res2; // ||b - A x||^2 of the last recomputation
+    double tol_abs;   // tol * ||b||
+};
+
+}  // namespace sfg

@@ -1,0 +1,194 @@
+// Sparse-sign subspace embedding S (Eq. 1; Clarkson-Woodruff when zeta = 1, Section 4.1) on the device.
+//
+// S is never stored densely.  Its pattern is drawn once per sketch size from SplitMix64 (counter form, see
+// sketch_column in common.cuh) and regrouped into *gather lists*: for each row block b of the vectors (the same
+// blocks the fused inner kernel uses) and each sketch row r, the list of (local offset, sign) of the columns j in
+// block b with S_rj != 0.  A kernel that holds block b of a vector in shared memory then forms its partial S x by
+// summing each sketch row's list in a fixed order -- deterministic, no atomics on floating-point data.
+#include "kernels.h"
+
+#include <mutex>
+#include <unordered_map>
+
+namespace sfg {
+
+thread_local int64_t g_launches = 0;
+
+void set_smem(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> done;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find(func);
+    if (it != done.end() && it->second >= bytes) return;
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done[func] = bytes;
+}
+
+// Pattern: rows[j*zeta + l], neg[j*zeta + l] (1 = negative sign).  kind 1 = identity (zeta = 1, row = j).
+__global__ void k_sketch_pattern(int n, int s, int zeta, int kind, uint64_t seed, int* __restrict__ rows,
+                                 int8_t* __restrict__ neg) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    if (kind == 1) {
+        rows[j] = (int)j;
+        neg[j] = 0;
+        return;
+    }
+    int r[kMaxZeta], ng[kMaxZeta];
+    sketch_column(seed, j, zeta, s, r, ng);
+    for (int l = 0; l < zeta; ++l) {
+        rows[j * zeta + l] = r[l];
+        neg[j * zeta + l] = (int8_t)ng[l];
+    }
+}
+
+void launch_sketch_pattern(const Plan&, int n, int s, int zeta, int kind, uint64_t seed, int* rows, int8_t* neg,
+                           cudaStream_t st) {
+    k_sketch_pattern<<<(n + 255) / 256, 256, 0, st>>>(n, s, zeta, kind, seed, rows, neg);
+    ++g_launches;
+}
+
+// counts[b*s + r] = number of nonzeros of sketch row r among the columns of block b
+__global__ void k_seg_count(int n, int s, int zeta, int Bn, const int* __restrict__ rows, int* __restrict__ counts) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int b = (int)(j / Bn);
+    for (int l = 0; l < zeta; ++l) atomicAdd(counts + (int64_t)b * s + rows[j * zeta + l], 1);
+}
+
+// Exclusive prefix sum of counts[0..len) into seg[0..len] (single block; len up to a few million).
+__global__ void k_scan_single(const int* __restrict__ counts, int* __restrict__ seg, int len) {
+    __shared__ int sums[1024];
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int chunk = (len + T - 1) / T;
+    const int a = min(len, tid * chunk), bnd = min(len, a + chunk);
+    int local = 0;
+    for (int i = a; i < bnd; ++i) local += counts[i];
+    sums[tid] = local;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {  // Hillis-Steele inclusive scan of the per-thread totals
+        int v = (tid >= off) ? sums[tid - off] : 0;
+        __syncthreads();
+        sums[tid] += v;
+        __syncthreads();
+    }
+    int run = sums[tid] - local;
+    for (int i = a; i < bnd; ++i) {
+        seg[i] = run;
+        run += counts[i];
+    }
+    if (tid == T - 1) seg[len] = sums[T - 1];
+}
+
+// Fill the gather lists of block b (one warp per block).  Entries of a list appear in the order
+// (column chunk of 32, slot l, lane), which is fixed, so the sums formed from them are reproducible.
+__global__ void k_seg_fill(int n, int s, int zeta, int Bn, const int* __restrict__ rows,
+                           const int8_t* __restrict__ neg, const int* __restrict__ seg,
+                           uint16_t* __restrict__ ent) {
+    extern __shared__ int cursor[];
+    const int b = blockIdx.x, lane = threadIdx.x;
+    for (int r = lane; r < s; r += 32) cursor[r] = 0;
+    __syncwarp();
+    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int base = r0; base < r1; base += 32) {
+        const int j = base + lane;
+        const bool ok = j < r1;
+        for (int l = 0; l < zeta; ++l) {
+            const int r = ok ? rows[(int64_t)j * zeta + l] : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, r);
+            if (ok) {
+                const int rank = __popc(peers & lt);
+                const int pos = seg[(int64_t)b * s + r] + cursor[r] + rank;
+                ent[pos] = (uint16_t)((j - r0) | (neg[(int64_t)j * zeta + l] ? 0x8000 : 0));
+            }
+            __syncwarp();
+            if (ok && lane == __ffs(peers) - 1) cursor[r] += __popc(peers);
+            __syncwarp();
+        }
+    }
+}
+
+void launch_sketch_build(int n, int s, int zeta, int Bn, int nblk, const int* rows, const int8_t* neg, int* counts,
+                         int* seg, uint16_t* ent, cudaStream_t st) {
+    k_seg_count<<<(n + 255) / 256, 256, 0, st>>>(n, s, zeta, Bn, rows, counts);
+    k_scan_single<<<1, 1024, 0, st>>>(counts, seg, nblk * s);
+    k_seg_fill<<<nblk, 32, s * sizeof(int), st>>>(n, s, zeta, Bn, rows, neg, seg, ent);
+    g_launches += 3;
+}
+
+// Per-block partial sketch of xs = xscale * x; optionally stores (VT)xs into dst.  The value fed to the sketch is
+// the stored (rounded) one, so S is applied to exactly the vector kept in the basis.
+template <typename VT, typename AT>
+__global__ void __launch_bounds__(512) k_sketch_partials(int n, int Bn, int s, const double* __restrict__ x,
+                                                         const double* __restrict__ xscale, VT* __restrict__ dst,
+                                                         const int* __restrict__ seg,
+                                                         const uint16_t* __restrict__ ent, AT* __restrict__ part) {
+    extern __shared__ unsigned char smem_raw[];
+    AT* xb = reinterpret_cast<AT*>(smem_raw);
+    const int b = blockIdx.x;
+    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
+    const double sc = xscale ? *xscale : 1.0;
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        AT v = (AT)(sc * x[r]);
+        if (dst) {
+            store_as(dst + r, v);
+            v = ld_plain(dst + r);
+        }
+        xb[r - r0] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int rr = warp; rr < s; rr += nw) {
+        const int a = seg[(int64_t)b * s + rr], e = seg[(int64_t)b * s + rr + 1];
+        AT acc = AT(0);
+        for (int q = a + lane; q < e; q += 32) {
+            const unsigned en = ent[q];
+            const AT v = xb[en & 0x7fffu];
+            acc += (en & 0x8000u) ? -v : v;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) part[(int64_t)b * s + rr] = acc;
+    }
+}
+
+void launch_sketch_partials(const Plan& p, const double* x, const double* xscale_dev, void* dst, void* part) {
+    const size_t sm = (size_t)p.Bn * (p.prec == kFP64 ? 8 : 4);
+    if (p.prec == kFP64) {
+        set_smem((const void*)k_sketch_partials<double, double>, sm);
+        k_sketch_partials<double, double><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.s, x, xscale_dev, (double*)dst,
+                                                                    p.seg, p.ent, (double*)part);
+    } else if (p.prec == kFP32) {
+        set_smem((const void*)k_sketch_partials<float, float>, sm);
+        k_sketch_partials<float, float><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.s, x, xscale_dev, (float*)dst,
+                                                                  p.seg, p.ent, (float*)part);
+    } else {
+        set_smem((const void*)k_sketch_partials<__nv_bfloat16, float>, sm);
+        k_sketch_partials<__nv_bfloat16, float><<<p.nblk, 512, sm, p.st>>>(
+            p.n, p.Bn, p.s, x, xscale_dev, (__nv_bfloat16*)dst, p.seg, p.ent, (float*)part);
+    }
+    ++g_launches;
+}
+
+template <typename AT>
+__global__ void k_sketch_reduce(int nblk, int s, double scale, const AT* __restrict__ part, double* __restrict__ out,
+                                double* __restrict__ out2) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= s) return;
+    AT acc = AT(0);
+    for (int b = 0; b < nblk; ++b) acc += part[(int64_t)b * s + r];
+    const double v = scale * (double)acc;
+    out[r] = v;
+    if (out2) out2[r] = v;
+}
+
+void launch_sketch_reduce(const Plan& p, const void* part, double* out, double* out2) {
+    const int th = 128, gr = (p.s + th - 1) / th;
+    if (p.prec == kFP64)
+        k_sketch_reduce<double><<<gr, th, 0, p.st>>>(p.nblk, p.s, p.sk_scale, (const double*)part, out, out2);
+    else
+        k_sketch_reduce<float><<<gr, th, 0, p.st>>>(p.nblk, p.s, p.sk_scale, (const float*)part, out, out2);
+    ++g_launches;
+}
+
+}  // namespace sfg
