@@ -40,7 +40,11 @@ struct sfgmres_ctx {
     uint64_t seed = 0;
     cudaStream_t st = nullptr;
     bool own_stream = false;
+    cudaStream_t qst = nullptr;       // side stream of the sketched-QR cluster kernel
+    cudaEvent_t ev_c = nullptr;       // "sketched column ready" (main -> side)
+    cudaEvent_t ev_q = nullptr;       // "cycle's QR updates done" (side -> main)
     int sms = 152;
+    int maxlen = 0;                   // longest CSR row
 
     // options
     int prec = kFP64, zeta = 8, c3 = 1, max_outer = 50, kind = 0, profile = 0, vec_opt = 0;
@@ -50,7 +54,7 @@ struct sfgmres_ctx {
     int Bn = 0, nblk = 0, vec = 8;
 
     // sketch gather lists (cached for one (s, zeta, kind))
-    int sk_s = -1, sk_zeta = -1, sk_kind = -1;
+    int sk_s = -1, sk_zeta = -1, sk_kind = -1, sk_headroom = 0;
     int* seg = nullptr;
     uint16_t* ent = nullptr;
 
@@ -119,7 +123,9 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int choose_vec(int64_t nnz, int n) {
+// Lanes per CSR row: one thread per row when every row is short (stencils), else a sub-warp sized by the mean.
+int choose_vec(int64_t nnz, int n, int maxlen) {
+    if (maxlen <= 16) return 1;
     const double avg = n ? (double)nnz / n : 1.0;
     if (avg <= 3.0) return 2;
     if (avg <= 6.0) return 4;
@@ -152,6 +158,10 @@ __global__ void k_validate_csr(int n, int64_t nnz, const int64_t* __restrict__ r
         if (i == 0 && v != 0) atomicOr(bad, 2);
         if (i == n && v != nnz) atomicOr(bad, 4);
         if (i < n && rp64[i + 1] < v) atomicOr(bad, 8);
+        if (i < n) {
+            const int64_t len = rp64[i + 1] - v;
+            if (len > 0) atomicMax(bad + 1, (int)min(len, (int64_t)INT32_MAX));
+        }
         rp32[i] = (int)v;
     }
     if (i < nnz) {
@@ -211,6 +221,17 @@ int build_sketch(sfgmres_ctx* h, int s) {
     cudaFree(rows);
     cudaFree(neg);
     cudaFree(counts);
+    {
+        // FP64 sketch terms are 53-bit integers summed exactly in 64 bits: lists longer than 1023 entries get
+        // extra right shifts so that no sum can overflow
+        std::vector<int> hs(nseg);
+        CK(cudaMemcpy(hs.data(), h->seg, nseg * sizeof(int), cudaMemcpyDeviceToHost));
+        int longest = 0;
+        for (int64_t q = 0; q + 1 < nseg; ++q) longest = std::max(longest, hs[q + 1] - hs[q]);
+        int H = 0;
+        while ((longest >> H) >= 1023) ++H;
+        h->sk_headroom = H;
+    }
     h->sk_s = s;
     h->sk_zeta = zeta;
     h->sk_kind = h->kind;
@@ -237,7 +258,7 @@ int prepare(sfgmres_ctx* h, int m, int s, int t, int jmax, Plan* p) {
     if ((rc = ensure(h, h->U, (size_t)(m + 1) * n * vt))) return rc;
     if ((rc = ensure(h, h->W, n * at))) return rc;
     if ((rc = ensure(h, h->sigma, (m + 1) * 8))) return rc;
-    if ((rc = ensure(h, h->normpart, nb * at))) return rc;
+    if ((rc = ensure(h, h->normpart, 2 * nb * at))) return rc;
     if ((rc = ensure(h, h->hpart, nb * kMaxTrunc * at))) return rc;
     if ((rc = ensure(h, h->cpart, nb * s * at))) return rc;
     if ((rc = ensure(h, h->C, (size_t)m * s * 8))) return rc;
@@ -290,6 +311,7 @@ int prepare(sfgmres_ctx* h, int m, int s, int t, int jmax, Plan* p) {
     P.seg = h->seg;
     P.ent = h->ent;
     P.sk_scale = (h->kind == 1) ? 1.0 : 1.0 / std::sqrt((double)h->sk_zeta);
+    P.sk_headroom = h->sk_headroom;
     P.prec = h->prec;
     P.m = m;
     P.t = t;
@@ -348,16 +370,18 @@ int check_params(sfgmres_ctx* h, int m, int s, int t) {
 }
 
 // ---- profiling helpers ----
-void ev_begin(sfgmres_ctx* h, std::vector<EventPair>& pool, size_t idx) {
+void ev_begin(sfgmres_ctx*, std::vector<EventPair>& pool, size_t idx, cudaStream_t st) {
     if (idx >= pool.size()) {
         EventPair e;
         cudaEventCreate(&e.a);
         cudaEventCreate(&e.b);
         pool.push_back(e);
     }
-    cudaEventRecord(pool[idx].a, h->st);
+    cudaEventRecord(pool[idx].a, st);
 }
-void ev_end(sfgmres_ctx* h, std::vector<EventPair>& pool, size_t idx) { cudaEventRecord(pool[idx].b, h->st); }
+void ev_end(sfgmres_ctx*, std::vector<EventPair>& pool, size_t idx, cudaStream_t st) {
+    cudaEventRecord(pool[idx].b, st);
+}
 double ev_sum(const std::vector<EventPair>& pool, size_t count) {
     double tot = 0.0;
     for (size_t i = 0; i < count; ++i) {
@@ -368,21 +392,28 @@ double ev_sum(const std::vector<EventPair>& pool, size_t count) {
 }
 
 // One inner cycle (Section 3) on u_0 = vscale * v; j >= 0 inside a solve (C3 as configured), j < 0 standalone.
-void run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const double* vscale, int c3, double* z) {
+// The sketched-QR update of step i runs on the side stream after step i's sketch column is ready, overlapping the
+// next step's SpMV; the main stream waits for the last QR update before the least-squares solve.
+int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const double* vscale, int c3, double* z) {
     launch_cycle_start(P, j, v, vscale, c3, h->cond_thr);
     for (int i = 0; i < P.m; ++i) {
         const bool last = (i == P.m - 1);
-        if (h->profile) ev_begin(h, h->ev_spmv, h->n_spmv);
+        if (h->profile) ev_begin(h, h->ev_spmv, h->n_spmv, h->st);
         launch_inner_spmv(P, i);
-        if (h->profile) ev_end(h, h->ev_spmv, h->n_spmv++);
-        if (h->profile) ev_begin(h, h->ev_axpy, h->n_axpy);
+        if (h->profile) ev_end(h, h->ev_spmv, h->n_spmv++, h->st);
+        if (h->profile) ev_begin(h, h->ev_axpy, h->n_axpy, h->st);
         launch_inner_axpy(P, i, last);
-        if (h->profile) ev_end(h, h->ev_axpy, h->n_axpy++);
-        if (h->profile) ev_begin(h, h->ev_qr, h->n_qr);
-        launch_inner_qr(P, i);
-        if (h->profile) ev_end(h, h->ev_qr, h->n_qr++);
+        if (h->profile) ev_end(h, h->ev_axpy, h->n_axpy++, h->st);
+        CK(cudaEventRecord(h->ev_c, h->st));
+        CK(cudaStreamWaitEvent(h->qst, h->ev_c, 0));
+        if (h->profile) ev_begin(h, h->ev_qr, h->n_qr, h->qst);
+        CK(launch_inner_qr(P, i, h->qst));
+        if (h->profile) ev_end(h, h->ev_qr, h->n_qr++, h->qst);
     }
+    CK(cudaEventRecord(h->ev_q, h->qst));
+    CK(cudaStreamWaitEvent(h->st, h->ev_q, 0));
     launch_inner_finish(P, z);
+    return 0;
 }
 
 }  // namespace
@@ -430,7 +461,7 @@ int sfgmres_create(sfgmres_t* out, int64_t n, int64_t nnz, const int64_t* row_pt
     if (cudaMalloc(&h->rp, (n + 1) * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&h->col, std::max<int64_t>(nnz, 1) * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&h->val, std::max<int64_t>(nnz, 1) * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&rp64, (n + 1) * sizeof(int64_t)) != cudaSuccess || cudaMalloc(&bad, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&rp64, (n + 1) * sizeof(int64_t)) != cudaSuccess || cudaMalloc(&bad, 2 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         if (rp64) cudaFree(rp64);
         if (bad) cudaFree(bad);
@@ -442,15 +473,17 @@ int sfgmres_create(sfgmres_t* out, int64_t n, int64_t nnz, const int64_t* row_pt
         cudaMemcpyAsync(h->col, col_idx, nnz * sizeof(int), kind, h->st);
         cudaMemcpyAsync(h->val, vals, nnz * sizeof(double), kind, h->st);
     }
-    cudaMemsetAsync(bad, 0, sizeof(int), h->st);
+    cudaMemsetAsync(bad, 0, 2 * sizeof(int), h->st);
     const int64_t cover = std::max<int64_t>(n + 1, nnz);
     k_validate_csr<<<(int)((cover + 255) / 256), 256, 0, h->st>>>((int)n, nnz, rp64, h->col, h->rp, bad);
-    int hbad = 0;
-    cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+    int hbad2[2] = {0, 0};
+    cudaMemcpyAsync(hbad2, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st);
     ce = cudaStreamSynchronize(h->st);
     cudaFree(rp64);
     cudaFree(bad);
     if (ce != cudaSuccess) return bail(SFGMRES_ERR_CUDA, std::string("CSR upload: ") + cudaGetErrorString(ce));
+    const int hbad = hbad2[0];
+    h->maxlen = hbad2[1];
     if (hbad) {
         char buf[160];
         snprintf(buf, sizeof buf, "invalid CSR (code %d: 1 range, 2 row_ptr[0]!=0, 4 row_ptr[n]!=nnz, "
@@ -458,7 +491,7 @@ int sfgmres_create(sfgmres_t* out, int64_t n, int64_t nnz, const int64_t* row_pt
         return bail(SFGMRES_ERR_INVALID_ARG, buf);
     }
     choose_blocks(h->n, h->sms, &h->Bn, &h->nblk);
-    h->vec = choose_vec(nnz, h->n);
+    h->vec = choose_vec(nnz, h->n, h->maxlen);
     if (cudaMallocHost(&h->h_ost, sizeof(OuterState)) != cudaSuccess ||
         cudaMallocHost(&h->h_cyc, sizeof(CycleState)) != cudaSuccess) {
         cudaGetLastError();
@@ -466,6 +499,14 @@ int sfgmres_create(sfgmres_t* out, int64_t n, int64_t nnz, const int64_t* row_pt
     }
     cudaEventCreate(&h->ev_t0);
     cudaEventCreate(&h->ev_t1);
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (cudaStreamCreateWithPriority(&h->qst, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_c, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_q, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(SFGMRES_ERR_CUDA, "stream/event creation failed");
+    }
     *out = h;
     return SFGMRES_OK;
 }
@@ -494,6 +535,12 @@ int sfgmres_destroy(sfgmres_t h) {
         }
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);
+    if (h->ev_c) cudaEventDestroy(h->ev_c);
+    if (h->ev_q) cudaEventDestroy(h->ev_q);
+    if (h->qst) {
+        cudaStreamSynchronize(h->qst);
+        cudaStreamDestroy(h->qst);
+    }
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
     delete h;
     return SFGMRES_OK;
@@ -535,7 +582,7 @@ int sfgmres_set_option(sfgmres_t h, int32_t key, double v) {
             if (!(iv == 0 || iv == 2 || iv == 4 || iv == 8 || iv == 16 || iv == 32) || iv != v)
                 return fail(h, SFGMRES_ERR_INVALID_ARG, "spmv vector width must be 0, 2, 4, 8, 16 or 32");
             h->vec_opt = iv;
-            h->vec = iv ? iv : choose_vec(h->nnz, h->n);
+            h->vec = iv ? iv : choose_vec(h->nnz, h->n, h->maxlen);
             return 0;
         default:
             return fail(h, SFGMRES_ERR_INVALID_ARG, "unknown option key");
@@ -614,7 +661,8 @@ int sfgmres_solve(sfgmres_t h, const double* b, const double* x0, double* x, int
     } else {
         status = SFGMRES_NOT_CONVERGED;
         for (int j = 0; j < jmax; ++j) {
-            run_cycle(h, P, j, P.Vb + (int64_t)j * h->n, P.nu + j, h->c3, P.Z + (int64_t)j * h->n);
+            if ((rc = run_cycle(h, P, j, P.Vb + (int64_t)j * h->n, P.nu + j, h->c3, P.Z + (int64_t)j * h->n)))
+                return rc;
             launch_outer_step(P, j);
             CK(cudaMemcpyAsync(h->h_ost, P.ost, sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
             CK(cudaStreamSynchronize(h->st));
@@ -716,7 +764,7 @@ int sfgmres_inner_cycle(sfgmres_t h, const double* v, double* z, int32_t m, int3
     CK(cudaSetDevice(h->dev));
     Plan P;
     if ((rc = prepare(h, m, s, k, 0, &P))) return rc;
-    run_cycle(h, P, -1, v, nullptr, 0, z);
+    if ((rc = run_cycle(h, P, -1, v, nullptr, 0, z))) return rc;
     CK(cudaMemcpyAsync(h->h_cyc, P.cyc, sizeof(CycleState), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());

@@ -13,6 +13,7 @@ constexpr int kMaxZeta = 16;    // largest number of nonzeros per sketch column
 constexpr int kMaxS = 4096;     // largest sketch size
 constexpr int kMaxM = 1024;     // largest inner basis size
 constexpr int kBlockRowsMax = 8192;  // rows per row block (local sketch offsets need <= 15 bits)
+constexpr int kQrCluster = 8;        // CTAs of the cluster that runs the sketched QR update
 
 // ------------------------------------------------------------------------------------------------------------
 // Precision traits.  VT: storage type of inner basis vectors; AT: arithmetic / accumulation type; MT: matrix values.
@@ -30,6 +31,28 @@ __device__ __forceinline__ float load_as(const __nv_bfloat16* p, float) { return
 __device__ __forceinline__ double ld_plain(const double* p) { return *p; }
 __device__ __forceinline__ float ld_plain(const float* p) { return *p; }
 __device__ __forceinline__ float ld_plain(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// Value as it will read back after store_as (identity except for BF16 rounding).
+__device__ __forceinline__ double stored_value(double v, const double*) { return v; }
+__device__ __forceinline__ float stored_value(float v, const float*) { return v; }
+__device__ __forceinline__ float stored_value(float v, const __nv_bfloat16*) {
+    return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+// x * 2^p for FP64 with integer operations only (no FP64 instruction): exact for normal results; zero, Inf and
+// NaN pass through; a result below the normal range is flushed to a signed zero (such entries are below 2^-1022
+// times the vector's norm and do not matter), one above it becomes a signed infinity.
+__device__ __forceinline__ double mul_pow2(double x, int p) {
+    const long long bits = __double_as_longlong(x);
+    const long long sign = bits & (long long)0x8000000000000000ull;
+    const int e = (int)((bits >> 52) & 0x7FF);
+    const int ne = e + p;
+    long long outb = bits + ((long long)p << 52);
+    if (e == 0x7FF) outb = bits;
+    else if (e == 0 || ne <= 0) outb = sign;
+    else if (ne >= 0x7FF) outb = sign | 0x7FF0000000000000ll;
+    return __longlong_as_double(outb);
+}
 
 __device__ __forceinline__ void store_as(double* p, double v) { *p = v; }
 __device__ __forceinline__ void store_as(float* p, float v) { *p = v; }
@@ -96,10 +119,13 @@ __device__ __forceinline__ void sketch_column(uint64_t seed, int64_t j, int zeta
 // ------------------------------------------------------------------------------------------------------------
 // Device-resident solver state (one instance per handle).
 struct CycleState {
-    int stopped;   // the inner cycle has ended (no more columns)
+    int stopped;   // the inner cycle has ended (written only by the sketched-QR kernel)
     int k;         // accepted inner basis size
-    int reason;    // 1 C1, 2 C2, 3 C3, 4 breakdown, 5 degenerate
+    int reason;    // 1 C1, 2 C2, 3 C3, 4 Arnoldi breakdown, 5 degenerate, 6 non-finite value
     int c3_on;     // rule C3 active for this cycle
+    int brk_step;  // first step i whose input basis vector u_i has zero (or non-finite) norm; INT_MAX if none
+    int brk_reason;  // 4 zero norm, 6 non-finite
+    int pad0, pad1;
     double dmax, dmin;    // extremes of |r_ll| for the condition proxy
     double rho;           // sketched residual of the last accepted column
     double c3_scale;      // FFOM residual of the previous outer step (beta at the first)

@@ -1,102 +1,204 @@
 // One sketched-GMRES cycle on the device (Section 3; Eq. 3 with r0 = v_j and zero initial guess).
 //
-// Per inner step i (0-based; the paper's i+1):
-//   k_inner_spmv  w = A b_i (b_i = sigma_i u_i), the truncated-Arnoldi dot products u_l^T w for the last t basis
-//                 vectors (Section 4.1), and the per-block partial sketch of w -- all from one pass over A, with the
-//                 row block of w held in shared memory for the sketch gather lists.
-//   k_inner_axpy  reduces the dots (every CTA, same order) and its slice of the sketch partials into the column
-//                 S A b_i, then u_{i+1} = w - sum_l h_l b_l and per-block partial ||u_{i+1}||^2.  The norm is reduced
-//                 by the next step's k_inner_spmv, which folds 1/||u_{i+1}|| into its SpMV (deferred normalisation).
-//   k_inner_qr    one CTA: Gram-Schmidt with one reorthogonalisation pass of S A b_i against Q (Section 3, C2), the
-//                 condition proxy max|r_ll|/min|r_ll| (rule C2), the running sketched residual (rule C3) and C1.
-// After the cycle: k_inner_finish solves R_k y = Q_k^T S v_j and forms z_j = B_k y_k in FP64.
+// Storage: the basis vectors are kept unnormalised, b_l = sigma_l u_l; scale factors live in scalars and a stored
+// vector is only ever rescaled by a power of two.  Per inner step i (0-based; the paper's i+1):
+//   k_inner_spmv  w' = A u_i, the truncated-Arnoldi dot products u_l^T w' for the last t basis vectors
+//                 (Section 4.1), and the per-block partial sketch S w' -- one pass over A; the row block of w' stays
+//                 in shared memory for the sketch gather lists.  In FP64 the sketch partials are accumulated exactly
+//                 in 64-bit fixed point (integer adds), which keeps the scarce FP64 pipe for the SpMV.
+//   k_inner_axpy  sigma_i = 1/||u_i||, h_l = b_l^T A b_i, the sketched column S A b_i = sigma_i S w', and the next
+//                 stored vector u_{i+1} = 2^p_i (w' - sum_l sigma_l^2 (u_l^T w') u_l), with 2^p_i the power of two
+//                 nearest below sigma_i (an exact rescaling that keeps stored norms O(||A||) instead of growing like
+//                 ||A||^i), and its per-block norm partials.
+//   k_inner_qr    a cluster of CTAs: Gram-Schmidt with one reorthogonalisation pass of S A b_i against Q
+//                 (Section 3, C2), the condition proxy max|r_ll|/min|r_ll| (rule C2), the running sketched residual
+//                 (rule C3) and C1.  It runs on a second stream, overlapping the next step's SpMV; a step that runs
+//                 past the end of the cycle is discarded.
+// After the cycle: k_inner_ls solves R_k y = (Q^T S v)_k and k_inner_gemv forms z_j = B_k y_k (FP64 output).
 #include "kernels.h"
 #include "spmv.cuh"
 
+#include <climits>
 #include <algorithm>
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
 
 namespace sfg {
 
 // ---------------------------------------------------------------------------------------------------------------
+// 64-bit fixed-point image of w relative to the block exponent Eb (max biased exponent in the block, >= 1):
+// w ~= q * 2^(Eb + H - 1075), |q| <= 2^53, rounded to nearest (ties away from zero).  Integer operations only.
+__device__ __forceinline__ long long to_fixed(double w, int Eb, int H) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(w);
+    const int e = (int)((bits >> 52) & 0x7FFull);
+    unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
+    int ee = e;
+    if (e != 0) M |= (1ull << 52);
+    else ee = 1;
+    const int d = Eb - ee + H;
+    unsigned long long q;
+    if (d <= 0) q = M;
+    else if (d >= 55) q = 0;
+    else q = (M + (1ull << (d - 1))) >> d;
+    return (bits >> 63) ? -(long long)q : (long long)q;
+}
+
+__device__ __forceinline__ int exp_of(double w) {
+    const int e = (int)(((unsigned long long)__double_as_longlong(w) >> 52) & 0x7FFull);
+    return e > 0 ? e : 1;
+}
+
+// Per-block sketch partials from the gather lists: out(rr, sum over the list of sketch row rr of +-x[offset]).
+// A warp takes 4 sketch rows at a time and issues the list loads of all four before any gather, so each warp keeps
+// several independent loads in flight; sums are formed lane-strided, then by a fixed shuffle tree.
+template <typename T, typename F>
+__device__ __forceinline__ void gather_rows(int b, int s, const int* __restrict__ seg,
+                                            const uint16_t* __restrict__ ent, const T* __restrict__ x, F out) {
+    constexpr int RW = 4, KU = 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int rb = warp * RW; rb < s; rb += nw * RW) {
+        int a[RW], e[RW];
+        int maxc = 0;
+#pragma unroll
+        for (int u = 0; u < RW; ++u) {
+            const int rr = rb + u;
+            a[u] = (rr < s) ? seg[(int64_t)b * s + rr] : 0;
+            e[u] = (rr < s) ? seg[(int64_t)b * s + rr + 1] : 0;
+            maxc = max(maxc, e[u] - a[u]);
+        }
+        T acc[RW];
+#pragma unroll
+        for (int u = 0; u < RW; ++u) acc[u] = T(0);
+        for (int off = lane; off < maxc; off += 32 * KU) {
+            unsigned en[RW][KU];
+#pragma unroll
+            for (int u = 0; u < RW; ++u)
+#pragma unroll
+                for (int k = 0; k < KU; ++k) {
+                    const int q = a[u] + off + 32 * k;
+                    en[u][k] = (q < e[u]) ? (unsigned)ent[q] : 0xFFFFFFFFu;
+                }
+#pragma unroll
+            for (int u = 0; u < RW; ++u)
+#pragma unroll
+                for (int k = 0; k < KU; ++k) {
+                    if (en[u][k] != 0xFFFFFFFFu) {
+                        const T v = x[en[u][k] & 0x7fffu];
+                        acc[u] += (en[u][k] & 0x8000u) ? -v : v;
+                    }
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < RW; ++u) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+            if (lane == 0 && rb + u < s) out(rb + u, acc[u]);
+        }
+    }
+}
+
+// Stores the block of w' and forms its dot products with the NW window vectors u_lo.. (per-block partials into
+// hpart); returns the thread's largest FP64 exponent of w' (for the fixed-point sketch).
+template <int NW, typename VT, typename AT>
+__device__ __forceinline__ int dots_window(int n, int r0, int r1, const VT* __restrict__ Ub, int lo,
+                                           const AT* __restrict__ wblk, AT* __restrict__ W, AT* __restrict__ hpart,
+                                           int b, AT* red) {
+    AT acc[NW > 0 ? NW : 1];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) acc[q] = AT(0);
+    int emax = 1;
+#pragma unroll 2
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const AT w = wblk[r - r0];
+        W[r] = w;
+        if constexpr (sizeof(AT) == 8) emax = max(emax, exp_of((double)w));
+#pragma unroll
+        for (int q = 0; q < NW; ++q) acc[q] += ld_plain(Ub + (int64_t)(lo + q) * n + r) * w;
+    }
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const AT v = block_sum_lean(acc[q], red);
+        if (threadIdx.x == 0) hpart[(int64_t)b * kMaxTrunc + q] = v;
+    }
+    return emax;
+}
+
+// u_{i+1} = 2^p2 (w' - sum_q coef_q u_{lo+q}) over rows [r0, r1), stored in VT; returns the thread's partial
+// squared norm of the stored values.
+template <int NW, typename VT, typename AT>
+__device__ __forceinline__ AT axpy_window(int n, int r0, int r1, VT* __restrict__ Ub, int lo, int i,
+                                          const AT* __restrict__ W, const AT* coef, int p2, AT sc2) {
+    AT cf[NW > 0 ? NW : 1];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) cf[q] = coef[q];
+    VT* un = Ub + (int64_t)(i + 1) * n;
+    AT nacc = AT(0);
+#pragma unroll 2
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        AT u = W[r];
+#pragma unroll
+        for (int q = 0; q < NW; ++q) u -= cf[q] * ld_plain(Ub + (int64_t)(lo + q) * n + r);
+        if constexpr (sizeof(AT) == 8) u = mul_pow2((double)u, p2);
+        else u = u * sc2;
+        store_as(un + r, u);
+        const AT us = stored_value(u, un);  // the norm of the vector as stored
+        nacc += us * us;
+    }
+    return nacc;
+}
+
+// ---------------------------------------------------------------------------------------------------------------
 template <int V, int U, typename MT, typename VT, typename AT>
 __global__ void __launch_bounds__(512, 2)
-    k_inner_spmv(int n, int Bn, int nblk, int s, int t, int i, const int* __restrict__ rp,
-                 const int* __restrict__ col, const MT* __restrict__ val, const VT* __restrict__ Ub,
-                 AT* __restrict__ W, double* __restrict__ sigma, const AT* __restrict__ normpart,
-                 AT* __restrict__ hpart, AT* __restrict__ cpart, const int* __restrict__ seg,
-                 const uint16_t* __restrict__ ent, CycleState* __restrict__ cyc) {
+    k_inner_spmv(int n, int Bn, int s, int t, int i, int H, const int* __restrict__ rp, const int* __restrict__ col,
+                 const MT* __restrict__ val, const VT* __restrict__ Ub, AT* __restrict__ W, AT* __restrict__ hpart,
+                 AT* __restrict__ cpart, const int* __restrict__ seg, const uint16_t* __restrict__ ent,
+                 const CycleState* __restrict__ cyc) {
     extern __shared__ unsigned char smem_raw[];
     AT* wblk = reinterpret_cast<AT*>(smem_raw);
-    __shared__ AT red[32];
-    __shared__ AT sig_sh;
-    __shared__ int stop_sh;
-    if (threadIdx.x == 0) stop_sh = cyc->stopped;
+    __shared__ AT red[512];
+    __shared__ int stop_sh, emax_sh[16];
+    if (threadIdx.x == 0) stop_sh = (cyc->stopped || cyc->brk_step <= i) ? 1 : 0;
     __syncthreads();
     if (stop_sh) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int b = blockIdx.x;
-    // sigma_i: 1/||u_i|| from the previous step's per-block partials (same fixed order in every CTA)
-    if (warp == 0) {
-        AT sig;
-        if (i == 0) {
-            sig = (AT)sigma[0];
-        } else {
-            AT acc = AT(0);
-            for (int q = lane; q < nblk; q += 32) acc += normpart[q];
-            acc = warp_sum(acc);
-            sig = AT(1) / sqrt(acc);
-            if (lane == 0) {
-                const bool bad = !(acc > AT(0)) || !isfinite((double)acc);
-                if (b == 0) sigma[i] = (double)sig;
-                if (bad) {
-                    if (b == 0) {
-                        cyc->stopped = 1;  // eta == 0: invariant Krylov space (k stays i); NaN: stop too
-                        cyc->reason = (acc == AT(0)) ? 4 : 6;
-                    }
-                    stop_sh = 1;
-                }
-            }
-        }
-        if (lane == 0) sig_sh = sig;
-    }
-    __syncthreads();
-    if (stop_sh) return;
-    const AT sig = sig_sh;
     const int r0 = b * Bn, r1 = min(n, r0 + Bn);
-    const VT* x = Ub + (int64_t)i * n;
-    spmv_rows_to_smem<V, U, MT, VT, AT>(rp, col, val, x, r0, r1, sig, wblk);
+    spmv_rows_to_smem<V, U, MT, VT, AT>(rp, col, val, Ub + (int64_t)i * n, r0, r1, wblk);
     __syncthreads();
-    // w to global and the truncated-Arnoldi dots against u_lo..u_i
+    // w' to global and the truncated-Arnoldi dots against u_lo..u_i (window size a compile-time count)
     const int lo = (t > 0) ? max(0, i - t + 1) : i + 1;
     const int nwin = i + 1 - lo;
-    AT acc[kMaxTrunc];
-#pragma unroll
-    for (int q = 0; q < kMaxTrunc; ++q) acc[q] = AT(0);
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        const AT w = wblk[r - r0];
-        W[r] = w;
-#pragma unroll
-        for (int q = 0; q < kMaxTrunc; ++q)
-            if (q < nwin) acc[q] += ld_plain(Ub + (int64_t)(lo + q) * n + r) * w;
+    int emax = 1;
+    switch (nwin) {
+        case 0: emax = dots_window<0>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
+        case 1: emax = dots_window<1>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
+        case 2: emax = dots_window<2>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
+        case 3: emax = dots_window<3>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
+        case 4: emax = dots_window<4>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
+        case 5: emax = dots_window<5>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
+        case 6: emax = dots_window<6>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
+        case 7: emax = dots_window<7>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
+        default: emax = dots_window<8>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
     }
-#pragma unroll
-    for (int q = 0; q < kMaxTrunc; ++q) {
-        if (q < nwin) {
-            const AT v = block_sum(acc[q], red);
-            if (threadIdx.x == 0) hpart[(int64_t)b * kMaxTrunc + q] = v;
-        }
-    }
-    // partial sketch of w: one warp per sketch row, fixed order
-    for (int rr = warp; rr < s; rr += nw) {
-        const int a = seg[(int64_t)b * s + rr], e = seg[(int64_t)b * s + rr + 1];
-        AT sacc = AT(0);
-        for (int q = a + lane; q < e; q += 32) {
-            const unsigned en = ent[q];
-            const AT v = wblk[en & 0x7fffu];
-            sacc += (en & 0x8000u) ? -v : v;
-        }
-        sacc = warp_sum(sacc);
-        if (lane == 0) cpart[(int64_t)b * s + rr] = sacc;
+    if constexpr (sizeof(AT) == 8) {
+        // exact fixed-point sketch partials: block exponent, in-place conversion, integer gather sums
+        emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
+        if (lane == 0) emax_sh[warp] = emax;
+        __syncthreads();
+        int Eb = 1;
+        for (int q = 0; q < nw; ++q) Eb = max(Eb, emax_sh[q]);
+        long long* qblk = reinterpret_cast<long long*>(wblk);
+        for (int r = threadIdx.x; r < r1 - r0; r += blockDim.x) qblk[r] = to_fixed((double)wblk[r], Eb, H);
+        __syncthreads();
+        const double scale_fx = ldexp(1.0, Eb + H - 1075);
+        gather_rows<long long>(b, s, seg, ent, qblk, [&](int rr, long long v) {
+            cpart[(int64_t)b * s + rr] = (Eb >= 2047) ? (AT)NAN : (AT)((double)v * scale_fx);
+        });
+    } else {
+        __syncthreads();
+        gather_rows<AT>(b, s, seg, ent, wblk, [&](int rr, AT v) { cpart[(int64_t)b * s + rr] = v; });
     }
 }
 
@@ -104,121 +206,200 @@ __global__ void __launch_bounds__(512, 2)
 template <typename VT, typename AT>
 __global__ void __launch_bounds__(512)
     k_inner_axpy(int n, int Bn, int nblk, int s, int t, int i, int last, double sk_scale, VT* __restrict__ Ub,
-                 const AT* __restrict__ W, const double* __restrict__ sigma, AT* __restrict__ normpart,
+                 const AT* __restrict__ W, double* __restrict__ sigma, AT* __restrict__ normpart,
                  const AT* __restrict__ hpart, const AT* __restrict__ cpart, double* __restrict__ C,
                  double* __restrict__ hco, CycleState* __restrict__ cyc) {
-    __shared__ AT red[32];
+    __shared__ AT red[512];
     __shared__ AT coef_sh[kMaxTrunc];
+    __shared__ double sig_sh;
     __shared__ int stop_sh;
-    if (threadIdx.x == 0) stop_sh = cyc->stopped;
+    if (threadIdx.x == 0) stop_sh = (cyc->stopped || cyc->brk_step <= i) ? 1 : 0;
     __syncthreads();
     if (stop_sh) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int b = blockIdx.x;
-    const int lo = (t > 0) ? max(0, i - t + 1) : i + 1;
-    const int nwin = i + 1 - lo;
-    // h_l = sigma_l * (u_l^T w); the update coefficient of u_l is h_l * sigma_l
-    if (warp < nwin) {
-        AT acc = AT(0);
-        for (int q = lane; q < nblk; q += 32) acc += hpart[(int64_t)q * kMaxTrunc + warp];
-        acc = warp_sum(acc);
+    // sigma_i = 1/||u_i|| from the previous step's partials (double-buffered by step parity)
+    if (warp == 0) {
+        double sig = 1.0;
+        bool bad = false;
+        int why = 4;
+        if (i == 0) {
+            sig = sigma[0];
+        } else {
+            AT a = AT(0);
+            const AT* np = normpart + (int64_t)(i & 1) * nblk;
+            for (int q = lane; q < nblk; q += 32) a += np[q];
+            a = warp_sum(a);
+            const double a2 = (double)a;
+            bad = !(a2 > 0.0) || !isfinite(a2);
+            why = (a2 == 0.0) ? 4 : 6;
+            sig = 1.0 / sqrt(a2);
+        }
         if (lane == 0) {
-            const AT sl = (AT)sigma[lo + warp];
-            const AT h = sl * acc;
-            coef_sh[warp] = h * sl;
-            if (b == 0) hco[(int64_t)i * kMaxTrunc + warp] = (double)h;
+            sig_sh = sig;
+            if (bad) {
+                stop_sh = 1;
+                if (b == 0) {
+                    cyc->brk_reason = why;
+                    atomicMin(&cyc->brk_step, i);
+                }
+            } else if (b == 0) {
+                sigma[i] = sig;
+            }
         }
     }
-    // this CTA's slice of the sketch column S A b_i
-    for (int rr = b * blockDim.x + threadIdx.x; rr < s; rr += gridDim.x * blockDim.x) {
-        AT acc = AT(0);
-        for (int q = 0; q < nblk; ++q) acc += cpart[(int64_t)q * s + rr];
-        C[(int64_t)i * s + rr] = sk_scale * (double)acc;
+    __syncthreads();
+    if (stop_sh) return;
+    const double sig_i = sig_sh;
+    const int lo = (t > 0) ? max(0, i - t + 1) : i + 1;
+    const int nwin = i + 1 - lo;
+    // h_l = sigma_l sigma_i (u_l^T w'); the stored update uses sigma_l^2 (u_l^T w')
+    if (warp < nwin) {
+        AT a = AT(0);
+        for (int q = lane; q < nblk; q += 32) a += hpart[(int64_t)q * kMaxTrunc + warp];
+        a = warp_sum(a);
+        if (lane == 0) {
+            const int l = lo + warp;
+            const double sl = (l == i) ? sig_i : sigma[l];
+            coef_sh[warp] = (AT)(sl * sl * (double)a);
+            if (b == 0) hco[(int64_t)i * kMaxTrunc + warp] = sl * sig_i * (double)a;
+        }
+    }
+    // sketched column S A b_i = sigma_i S w': one warp per sketch row across the grid
+    const double csc = sk_scale * sig_i;
+    for (int rr = b * nw + warp; rr < s; rr += nblk * nw) {
+        AT a = AT(0);
+        for (int q = lane; q < nblk; q += 32) a += cpart[(int64_t)q * s + rr];
+        a = warp_sum(a);
+        if (lane == 0) C[(int64_t)i * s + rr] = csc * (double)a;
     }
     if (last) return;
     __syncthreads();
     const int r0 = b * Bn, r1 = min(n, r0 + Bn);
-    VT* un = Ub + (int64_t)(i + 1) * n;
-    AT nacc = AT(0);
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        AT u = W[r];
-#pragma unroll
-        for (int q = 0; q < kMaxTrunc; ++q)
-            if (q < nwin) u -= coef_sh[q] * ld_plain(Ub + (int64_t)(lo + q) * n + r);
-        store_as(un + r, u);
-        nacc += u * u;
+    int p2;
+    frexp(sig_i, &p2);  // sigma_i = f * 2^p2, f in [0.5, 1): rescale by 2^(p2-1)
+    p2 -= 1;
+    const AT sc2 = (AT)ldexp(1.0, p2);
+    AT nacc;
+    switch (nwin) {
+        case 0: nacc = axpy_window<0>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
+        case 1: nacc = axpy_window<1>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
+        case 2: nacc = axpy_window<2>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
+        case 3: nacc = axpy_window<3>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
+        case 4: nacc = axpy_window<4>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
+        case 5: nacc = axpy_window<5>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
+        case 6: nacc = axpy_window<6>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
+        case 7: nacc = axpy_window<7>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
+        default: nacc = axpy_window<8>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
     }
-    nacc = block_sum(nacc, red);
-    if (threadIdx.x == 0) normpart[b] = nacc;
+    nacc = block_sum_lean(nacc, red);
+    if (threadIdx.x == 0) normpart[(int64_t)((i + 1) & 1) * nblk + b] = nacc;
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// Sketched QR update of column i (one CTA).
-__global__ void __launch_bounds__(512)
+// Sketched QR update of column i on a cluster of CTAs; CTA q of the cluster owns rows [s q / nq, s (q+1) / nq) of
+// Q and of the working vectors, and partial dot products are exchanged through distributed shared memory and summed
+// in rank order (deterministic).  Every early exit is decided from values all CTAs of the cluster share.
+__global__ void __launch_bounds__(256)
     k_inner_qr(int s, int m, int i, const double* __restrict__ C, double* __restrict__ Q, double* __restrict__ R,
                double* __restrict__ d, double* __restrict__ e, double* __restrict__ rho,
                CycleState* __restrict__ cyc) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int q = (int)cl.block_rank(), nq = (int)cl.num_blocks();
+    const int rlo = (int)((int64_t)s * q / nq), rhi = (int)((int64_t)s * (q + 1) / nq), nr = rhi - rlo;
+    const int nrmax = (s + nq - 1) / nq;
     extern __shared__ double qsm[];
-    double* p = qsm;          // [s]
-    double* a = qsm + s;      // [i] projection coefficients
-    __shared__ double red[32];
-    __shared__ int stop_sh;
-    if (threadIdx.x == 0) stop_sh = cyc->stopped;
-    __syncthreads();
-    if (stop_sh) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r = threadIdx.x; r < s; r += blockDim.x) p[r] = C[(int64_t)i * s + r];
-    for (int l = threadIdx.x; l < i; l += blockDim.x) R[(int64_t)i * m + l] = 0.0;
+    double* p = qsm;               // [nrmax] this CTA's rows of the working vector
+    double* apart = qsm + nrmax;   // [m] partial projections over this CTA's rows
+    double* a = apart + m;         // [m] full projections
+    __shared__ double red[256];
+    __shared__ double scal[4];
+    __shared__ int code_sh;
+    // state read by every CTA before the first cluster barrier (rank 0 writes it only after the last one)
+    const double dmax0 = cyc->dmax, dmin0 = cyc->dmin, thr = cyc->cond_thr;
+    if (q == 0 && threadIdx.x == 0) code_sh = cyc->stopped ? 1 : (cyc->brk_step <= i ? 2 : 0);
+    cl.sync();
+    const int code = *cl.map_shared_rank(&code_sh, 0);
+    cl.sync();
+    if (code) {
+        if (code == 2 && q == 0 && threadIdx.x == 0) {
+            cyc->stopped = 1;  // u_i has zero (or non-finite) norm: the cycle keeps k = i columns
+            cyc->reason = cyc->brk_reason;
+        }
+        return;
+    }
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) p[r] = C[(int64_t)i * s + rlo + r];
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
-        for (int l = warp; l < i; l += nw) {
+        for (int l = threadIdx.x; l < i; l += blockDim.x) {
+            const double* ql = Q + (int64_t)l * s + rlo;
             double acc = 0.0;
-            const double* ql = Q + (int64_t)l * s;
-            for (int r = lane; r < s; r += 32) acc += ql[r] * p[r];
-            acc = warp_sum(acc);
-            if (lane == 0) a[l] = acc;
+            for (int r = 0; r < nr; ++r) acc += ql[r] * p[r];
+            apart[l] = acc;
         }
-        __syncthreads();
-        for (int r = threadIdx.x; r < s; r += blockDim.x) {
+        cl.sync();
+        for (int l = threadIdx.x; l < i; l += blockDim.x) {
+            double acc = 0.0;
+            for (int qq = 0; qq < nq; ++qq) acc += cl.map_shared_rank(apart, qq)[l];
+            a[l] = acc;
+        }
+        cl.sync();  // every CTA has read the partials before the next pass overwrites them
+        for (int r = threadIdx.x; r < nr; r += blockDim.x) {
             double v = p[r];
-            for (int l = 0; l < i; ++l) v -= a[l] * Q[(int64_t)l * s + r];
+            for (int l = 0; l < i; ++l) v -= a[l] * Q[(int64_t)l * s + rlo + r];
             p[r] = v;
         }
-        for (int l = threadIdx.x; l < i; l += blockDim.x) R[(int64_t)i * m + l] += a[l];
+        if (q == 0)
+            for (int l = threadIdx.x; l < i; l += blockDim.x)
+                R[(int64_t)i * m + l] = (pass ? R[(int64_t)i * m + l] : 0.0) + a[l];
         __syncthreads();
     }
-    double nrm2 = 0.0;
-    for (int r = threadIdx.x; r < s; r += blockDim.x) nrm2 += p[r] * p[r];
-    const double rii = sqrt(block_sum(nrm2, red));
-    const double dmax = fmax(cyc->dmax, rii);
-    const double dmin = (i == 0) ? rii : fmin(cyc->dmin, rii);
+    double v2 = 0.0;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) v2 += p[r] * p[r];
+    v2 = block_sum_lean(v2, red);
+    if (threadIdx.x == 0) scal[0] = v2;
+    cl.sync();
+    double nn = 0.0;
+    for (int qq = 0; qq < nq; ++qq) nn += cl.map_shared_rank(scal, qq)[0];
+    const double rii = sqrt(nn);
+    const double dmax = fmax(dmax0, rii);
+    const double dmin = (i == 0) ? rii : fmin(dmin0, rii);
     const double kappa = (dmin > 0.0) ? dmax / dmin : INFINITY;
-    if (!(kappa <= cyc->cond_thr)) {  // C2 (also catches rii == 0 and NaN): drop column i
-        __syncthreads();
-        if (threadIdx.x == 0) {
+    if (!(kappa <= thr)) {  // C2 (also rii == 0 or NaN): drop column i, keep k = i
+        if (q == 0 && threadIdx.x == 0) {
             cyc->stopped = 1;
             cyc->k = i;
             cyc->reason = (i == 0) ? 5 : 2;
         }
+        cl.sync();
         return;
     }
     const double inv = 1.0 / rii;
-    double dacc = 0.0;
-    for (int r = threadIdx.x; r < s; r += blockDim.x) {
-        const double q = p[r] * inv;
-        p[r] = q;
-        Q[(int64_t)i * s + r] = q;
-        dacc += q * e[r];
+    double dd = 0.0;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        const double qv = p[r] * inv;
+        p[r] = qv;
+        Q[(int64_t)i * s + rlo + r] = qv;
+        dd += qv * e[rlo + r];
     }
-    const double di = block_sum(dacc, red);
-    double eacc = 0.0;
-    for (int r = threadIdx.x; r < s; r += blockDim.x) {
-        const double ev = e[r] - di * p[r];
-        e[r] = ev;
-        eacc += ev * ev;
+    dd = block_sum_lean(dd, red);
+    if (threadIdx.x == 0) scal[1] = dd;
+    cl.sync();
+    double di = 0.0;
+    for (int qq = 0; qq < nq; ++qq) di += cl.map_shared_rank(scal, qq)[1];
+    double ee = 0.0;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        const double ev = e[rlo + r] - di * p[r];
+        e[rlo + r] = ev;
+        ee += ev * ev;
     }
-    const double rh = sqrt(block_sum(eacc, red));
-    if (threadIdx.x == 0) {
+    ee = block_sum_lean(ee, red);
+    if (threadIdx.x == 0) scal[2] = ee;
+    cl.sync();
+    double rr2 = 0.0;
+    for (int qq = 0; qq < nq; ++qq) rr2 += cl.map_shared_rank(scal, qq)[2];
+    const double rh = sqrt(rr2);
+    if (q == 0 && threadIdx.x == 0) {
         R[(int64_t)i * m + i] = rii;
         d[i] = di;
         rho[i] = rh;
@@ -234,6 +415,7 @@ __global__ void __launch_bounds__(512)
             cyc->reason = 1;
         }
     }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 // ---------------------------------------------------------------------------------------------------------------
@@ -257,18 +439,42 @@ __global__ void k_inner_ls(int m, const double* __restrict__ R, const double* __
     }
 }
 
-// z = sum_{l<k} coef_l u_l in FP64.
+// z = sum_{l<k} coef_l u_l, FP64 output.  FP64 basis: FP64 FMAs.  FP32/BF16 basis: the FP64 coefficients are
+// split into two FP32 parts and the sum is carried as an unevaluated FP32 pair (TwoSum, and FMA for the exact
+// product error), close to FP64 accuracy on the FP32 pipe.
 template <typename VT>
 __global__ void __launch_bounds__(256) k_inner_gemv(int n, const VT* __restrict__ Ub, const double* __restrict__ coef,
                                                     const CycleState* __restrict__ cyc, double* __restrict__ z) {
     __shared__ double cf[kMaxM];
+    __shared__ float ch[kMaxM], clo[kMaxM];
     const int k = cyc->k;
-    for (int l = threadIdx.x; l < k; l += blockDim.x) cf[l] = coef[l];
+    for (int l = threadIdx.x; l < k; l += blockDim.x) {
+        const double c = coef[l];
+        cf[l] = c;
+        const float hi = (float)c;
+        ch[l] = hi;
+        clo[l] = (float)(c - (double)hi);
+    }
     __syncthreads();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int l = 0; l < k; ++l) acc += cf[l] * (double)ld_plain(Ub + (int64_t)l * n + r);
-        z[r] = acc;
+        if constexpr (sizeof(VT) == 8) {
+            double acc = 0.0;
+            for (int l = 0; l < k; ++l) acc += cf[l] * (double)ld_plain(Ub + (int64_t)l * n + r);
+            z[r] = acc;
+        } else {
+            float sh = 0.f, sl = 0.f;
+            for (int l = 0; l < k; ++l) {
+                const float u = ld_plain(Ub + (int64_t)l * n + r);
+                const float p = ch[l] * u;
+                const float pe = fmaf(ch[l], u, -p) + clo[l] * u;  // exact product error + low-part term
+                const float t1 = sh + p;                             // TwoSum(sh, p)
+                const float bv = t1 - sh;
+                const float err = (sh - (t1 - bv)) + (p - bv);
+                sh = t1;
+                sl += err + pe;
+            }
+            z[r] = (double)sh + (double)sl;
+        }
     }
 }
 
@@ -288,6 +494,8 @@ __global__ void k_cycle_reset(CycleState* cyc, const OuterState* ost, int j, int
     cyc->stopped = 0;
     cyc->k = 0;
     cyc->reason = 0;
+    cyc->brk_step = INT_MAX;
+    cyc->brk_reason = 0;
     cyc->dmax = 0.0;
     cyc->dmin = INFINITY;
     cyc->rho = INFINITY;
@@ -318,8 +526,8 @@ static void inner_spmv_t(const Plan& p, int i, const MT* val) {
     const size_t sm = (size_t)p.Bn * sizeof(AT);
     SFG_SPMV_DISPATCH(p.vec, (set_smem((const void*)k_inner_spmv<VV, UU, MT, VT, AT>, sm),
                               k_inner_spmv<VV, UU, MT, VT, AT><<<p.nblk, 512, sm, p.st>>>(
-                                 p.n, p.Bn, p.nblk, p.s, p.t, i, p.rp, p.col, val, (const VT*)p.U, (AT*)p.W,
-                                 p.sigma, (const AT*)p.normpart, (AT*)p.hpart, (AT*)p.cpart, p.seg, p.ent, p.cyc)));
+                                  p.n, p.Bn, p.s, p.t, i, p.sk_headroom, p.rp, p.col, val, (const VT*)p.U,
+                                  (AT*)p.W, (AT*)p.hpart, (AT*)p.cpart, p.seg, p.ent, p.cyc)));
 }
 
 void launch_inner_spmv(const Plan& p, int i) {
@@ -343,10 +551,24 @@ void launch_inner_axpy(const Plan& p, int i, bool last) {
     ++g_launches;
 }
 
-void launch_inner_qr(const Plan& p, int i) {
-    const size_t sm = (size_t)(p.s + p.m) * sizeof(double);
-    k_inner_qr<<<1, 512, sm, p.st>>>(p.s, p.m, i, p.C, p.Q, p.R, p.d, p.e, p.rho, p.cyc);
+cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st) {
+    const int nrmax = (p.s + kQrCluster - 1) / kQrCluster;
+    const size_t sm = (size_t)(nrmax + 2 * p.m) * sizeof(double);
+    set_smem((const void*)k_inner_qr, sm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kQrCluster, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kQrCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     ++g_launches;
+    return cudaLaunchKernelEx(&cfg, k_inner_qr, p.s, p.m, i, (const double*)p.C, p.Q, p.R, p.d, p.e, p.rho, p.cyc);
 }
 
 void launch_inner_finish(const Plan& p, double* z) {

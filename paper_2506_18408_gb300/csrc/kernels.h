@@ -19,7 +19,7 @@ struct Plan {
     const int* col = nullptr;
     const double* val = nullptr;
     const float* val32 = nullptr;  // FP32 copy (inner FP32/BF16 modes)
-    int vec = 8;                   // SpMV lanes per row
+    int vec = 8;                   // SpMV lanes per row (1 = one thread per row)
 
     // row blocks (shared by all fused kernels and by the sketch gather lists)
     int Bn = 0, nblk = 0;
@@ -30,13 +30,14 @@ struct Plan {
     const int* seg = nullptr;
     const uint16_t* ent = nullptr;
     double sk_scale = 1.0;
+    int sk_headroom = 0;  // extra right shift of the FP64 fixed-point sketch terms (long gather lists)
 
     // inner cycle
     int prec = kFP64, m = 0, t = 0;
     void* U = nullptr;         // basis storage, (m+1) columns of n (VT); column l = u_l, b_l = sigma[l] * u_l
     void* W = nullptr;         // w = A b_i (AT[n])
     double* sigma = nullptr;   // [m+1] 1/||u_l||
-    void* normpart = nullptr;  // AT[nblk]
+    void* normpart = nullptr;  // AT[2 * nblk], double-buffered by step parity
     void* hpart = nullptr;     // AT[nblk * kMaxTrunc]
     void* cpart = nullptr;     // AT[nblk * s]
     double* C = nullptr;       // [m * s]  S A b_i
@@ -92,7 +93,7 @@ void launch_sketch_reduce(const Plan& p, const void* part, double* out, double* 
 void launch_cycle_start(const Plan& p, int j, const double* v, const double* vscale_dev, int c3_on, double cond_thr);
 void launch_inner_spmv(const Plan& p, int i);
 void launch_inner_axpy(const Plan& p, int i, bool last);
-void launch_inner_qr(const Plan& p, int i);
+cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st);  // cluster launch on stream st
 void launch_inner_finish(const Plan& p, double* z);  // y = R^{-1} d, z = sum_l y_l b_l (FP64)
 void launch_export_basis(const Plan& p, double* out, int count);  // out[:, l] = sigma_l * u_l (FP64)
 

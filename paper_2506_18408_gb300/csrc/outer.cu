@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(512, 2)
     const int b = blockIdx.x;
     const int r0 = b * Bn, r1 = min(n, r0 + Bn);
     if (x) {
-        spmv_rows_to_smem<V, U, double, double, double>(rp, col, val, x, r0, r1, 1.0, axb);
+        spmv_rows_to_smem<V, U, double, double, double>(rp, col, val, x, r0, r1, axb);
         __syncthreads();
     }
     double a1 = 0.0, a2 = 0.0;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(512, 2)
     extern __shared__ double wb[];
     const int b = blockIdx.x;
     const int r0 = b * Bn, r1 = min(n, r0 + Bn);
-    spmv_rows_to_smem<V, U, double, double, double>(rp, col, val, z, r0, r1, 1.0, wb);
+    spmv_rows_to_smem<V, U, double, double, double>(rp, col, val, z, r0, r1, wb);
     __syncthreads();
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) Wo[r] = wb[r - r0];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(512, 2)
     extern __shared__ double yb[];
     const int b = blockIdx.x;
     const int r0 = b * Bn, r1 = min(n, r0 + Bn);
-    spmv_rows_to_smem<V, U, double, double, double>(rp, col, val, x, r0, r1, 1.0, yb);
+    spmv_rows_to_smem<V, U, double, double, double>(rp, col, val, x, r0, r1, yb);
     __syncthreads();
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) y[r] = yb[r - r0];
 }

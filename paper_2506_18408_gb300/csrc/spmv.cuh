@@ -5,15 +5,73 @@
 
 namespace sfg {
 
-// out[r - r0] = scale * sum_p val[p] * x[col[p]] for rows r in [r0, r1).
-// Each row is handled by a sub-warp of V lanes; a warp processes U sub-warp rows at once (all their loads issued
-// before the FMAs) so every thread keeps several independent loads in flight.  For a fixed unroll slot the warp's
-// sub-warps read consecutive rows, so the col/val streams are read in contiguous segments.  The per-row sums are
-// combined by a fixed xor-shuffle tree, so the result does not depend on scheduling.
+// CNT entries (compile-time count) of one row chunk: loads first, then exactly CNT FMAs.  Lanes whose row has
+// fewer entries in this chunk are predicated off; the warp issues no instruction for slots no lane needs.
+template <int CNT, typename MT, typename XT, typename AT>
+__device__ __forceinline__ void row_chunk(const int* __restrict__ col, const MT* __restrict__ val,
+                                          const XT* __restrict__ x, int a, int len, int pk, AT& sum) {
+    int c[CNT];
+    AT v[CNT];
+#pragma unroll
+    for (int q = 0; q < CNT; ++q) {
+        if (pk + q < len) {
+            c[q] = __ldg(col + a + pk + q);
+            v[q] = (AT)__ldg(val + a + pk + q);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CNT; ++q)
+        if (pk + q < len) sum += v[q] * load_as(x + c[q], AT());
+}
+
+// out[r - r0] = sum_p val[p] * x[col[p]] for rows r in [r0, r1), one thread per row.
+// Warps walk the rows together; each row is read in chunks of up to 4 entries whose count is the longest row of
+// the warp in that chunk, dispatched to a compile-time count, so the number of FMA instructions a warp issues is
+// exactly its longest row (with no shuffle tree): the FP64 pipe, scarce on this GPU, does only useful work.
+// The next row group's extents are fetched while the current one is summed.  Sums run in entry order.
+template <typename MT, typename XT, typename AT>
+__device__ __forceinline__ void spmv_rows_scalar(const int* __restrict__ rp, const int* __restrict__ col,
+                                                 const MT* __restrict__ val, const XT* __restrict__ x, int r0,
+                                                 int r1, AT* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    int rw = r0 + (threadIdx.x & ~31);
+    int a = 0, len = 0;
+    if (rw + lane < r1) {
+        a = __ldg(rp + rw + lane);
+        len = __ldg(rp + rw + lane + 1) - a;
+    }
+    for (; rw < r1; rw += blockDim.x) {  // warp-uniform loop
+        const int rn = rw + (int)blockDim.x + lane;
+        int an = 0, lenn = 0;
+        if (rn < r1) {
+            an = __ldg(rp + rn);
+            lenn = __ldg(rp + rn + 1) - an;
+        }
+        const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+        AT sum = AT(0);
+        for (int pk = 0; pk < maxlen; pk += 4) {
+            switch (min(maxlen - pk, 4)) {
+                case 1: row_chunk<1>(col, val, x, a, len, pk, sum); break;
+                case 2: row_chunk<2>(col, val, x, a, len, pk, sum); break;
+                case 3: row_chunk<3>(col, val, x, a, len, pk, sum); break;
+                case 4: row_chunk<4>(col, val, x, a, len, pk, sum); break;
+                default: row_chunk<4>(col, val, x, a, len, pk, sum); break;
+            }
+        }
+        if (rw + lane < r1) out[rw + lane - r0] = sum;
+        a = an;
+        len = lenn;
+    }
+}
+
+// Same result with each row handled by a sub-warp of V lanes; a warp processes U sub-warp rows at once (all their
+// loads issued before the FMAs).  For a fixed unroll slot the warp's sub-warps read consecutive rows, so the
+// col/val streams are read in contiguous segments.  Per-row sums are combined by a fixed xor-shuffle tree.
+// Suited to long or irregular rows.
 template <int V, int U, typename MT, typename XT, typename AT>
-__device__ __forceinline__ void spmv_rows_to_smem(const int* __restrict__ rp, const int* __restrict__ col,
-                                                  const MT* __restrict__ val, const XT* __restrict__ x, int r0,
-                                                  int r1, AT scale, AT* __restrict__ out) {
+__device__ __forceinline__ void spmv_rows_vector(const int* __restrict__ rp, const int* __restrict__ col,
+                                                 const MT* __restrict__ val, const XT* __restrict__ x, int r0,
+                                                 int r1, AT* __restrict__ out) {
     constexpr int SUBS = 32 / V;
     constexpr int TILE = SUBS * U;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -55,19 +113,47 @@ __device__ __forceinline__ void spmv_rows_to_smem(const int* __restrict__ rp, co
 #pragma unroll
             for (int o = V / 2; o > 0; o >>= 1) sum[u] += __shfl_xor_sync(0xffffffffu, sum[u], o);
             const int row = tb + u * SUBS + sub;
-            if (sl == 0 && row < r1) out[row - r0] = scale * sum[u];
+            if (sl == 0 && row < r1) out[row - r0] = sum[u];
         }
     }
 }
 
-// Dispatch on the sub-warp width chosen at run time (2..32); U is fixed per width.
-#define SFG_SPMV_DISPATCH(V_RUNTIME, CALL)          \
-    switch (V_RUNTIME) {                            \
+template <int V, int U, typename MT, typename XT, typename AT>
+__device__ __forceinline__ void spmv_rows_to_smem(const int* __restrict__ rp, const int* __restrict__ col,
+                                                  const MT* __restrict__ val, const XT* __restrict__ x, int r0,
+                                                  int r1, AT* __restrict__ out) {
+    if constexpr (V == 1) spmv_rows_scalar<MT, XT, AT>(rp, col, val, x, r0, r1, out);
+    else spmv_rows_vector<V, U, MT, XT, AT>(rp, col, val, x, r0, r1, out);
+}
+
+// Dispatch on the lanes-per-row width chosen at run time (1 = one thread per row, else 2..32).
+#define SFG_SPMV_DISPATCH(V_RUNTIME, CALL)                       \
+    switch (V_RUNTIME) {                                         \
+        case 1: { constexpr int VV = 1, UU = 1; CALL; } break;   \
         case 2: { constexpr int VV = 2, UU = 4; CALL; } break;   \
         case 4: { constexpr int VV = 4, UU = 4; CALL; } break;   \
         case 8: { constexpr int VV = 8, UU = 4; CALL; } break;   \
         case 16: { constexpr int VV = 16, UU = 2; CALL; } break; \
         default: { constexpr int VV = 32, UU = 2; CALL; } break; \
     }
+
+// Sum over the block with few floating-point instructions: every thread's value goes to shared memory, then one
+// warp adds 16 values per lane in a fixed order and finishes with a shuffle tree.  Result valid in every thread.
+// `red` holds blockDim.x values (blockDim.x <= 1024, a multiple of 32).
+template <typename T>
+__device__ __forceinline__ T block_sum_lean(T v, T* red) {
+    __syncthreads();
+    red[threadIdx.x] = v;
+    __syncthreads();
+    __shared__ T res;
+    if (threadIdx.x < 32) {
+        T acc = T(0);
+        for (int q = threadIdx.x; q < (int)blockDim.x; q += 32) acc += red[q];
+        acc = warp_sum(acc);
+        if (threadIdx.x == 0) res = acc;
+    }
+    __syncthreads();
+    return res;
+}
 
 }  // namespace sfg
