@@ -148,6 +148,26 @@ SFGMRES_API int sfgmres_sketch_apply(sfgmres_t h, int32_t s, const double* v, do
  * collisions; row = ((h >> 32) * s) >> 32) and its sign from bit 63 of output 128q + 1. */
 SFGMRES_API int sfgmres_sketch_pattern(sfgmres_t h, int32_t s, int32_t* rows, int8_t* signs);
 
+/* c = S v without allocating anything, for callers that cannot call cudaMalloc (code whose device-memory plan is
+ * fixed in advance, such as a captured or replayed sequence of work or a loop with a no-allocation rule, or an
+ * application whose device memory belongs to another allocator).  The paper has no counterpart: it is the sketch
+ * application of sfgmres_sketch_apply (same embedding for the same n, s, zeta and seed; results agree up to
+ * summation rounding) without a handle.
+ *   n, s, zeta     vector length, sketch rows and nonzeros per column: 1 <= zeta <= 16, zeta <= s <= 4096,
+ *                  1 <= n <= 65536 * floor(2^20 / s); larger sizes return SFGMRES_ERR_INVALID_ARG
+ *   sketch_seed    seed of the embedding
+ *   v, c           device float64[n] input and float64[s] output, owned by the caller
+ *   stream         cudaStream_t to enqueue on (NULL: the default stream); the call returns after enqueueing, and c
+ *                  is ready when the stream reaches that point
+ * Scratch: a fixed 8 MiB static device array (2^20 doubles) in the library, held on every GPU that loads the
+ * library until the process exits.  All calls share it and it keeps the last call's contents; every call overwrites
+ * the part it reads, so nothing needs to start at zero.  Calls whose work overlaps on the GPU (different streams,
+ * different host threads) race on it and must be serialised by the caller.  The first call on a device looks up the
+ * array's device address with that device current; make that first call before any stream capture.  Errors:
+ * SFGMRES_ERR_INVALID_ARG (sizes, NULL), SFGMRES_ERR_CUDA (launch); sfgmres_last_error(NULL) describes them. */
+SFGMRES_API int sfgmres_sketch_apply_noalloc(int64_t n, int32_t s, int32_t zeta, uint64_t sketch_seed,
+                                             const double* v, double* c, void* stream);
+
 /* y = A x in FP64 (device pointers, n each). */
 SFGMRES_API int sfgmres_spmv(sfgmres_t h, const double* x, double* y);
 

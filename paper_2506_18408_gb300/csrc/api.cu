@@ -29,6 +29,10 @@ struct EventPair {
 
 }  // namespace
 
+namespace sfg {
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace sfg
+
 struct sfgmres_ctx {
     int dev = 0;
     int n = 0;

@@ -117,6 +117,29 @@ __device__ __forceinline__ void sketch_column(uint64_t seed, int64_t j, int zeta
 }
 
 // ------------------------------------------------------------------------------------------------------------
+// 64-bit fixed-point image of w relative to the block exponent Eb (max biased exponent in the block, >= 1):
+// w ~= q * 2^(Eb + H - 1075), |q| <= 2^53, rounded to nearest (ties away from zero).  Integer operations only.
+__device__ __forceinline__ long long to_fixed(double w, int Eb, int H) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(w);
+    const int e = (int)((bits >> 52) & 0x7FFull);
+    unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
+    int ee = e;
+    if (e != 0) M |= (1ull << 52);
+    else ee = 1;
+    const int d = Eb - ee + H;
+    unsigned long long q;
+    if (d <= 0) q = M;
+    else if (d >= 55) q = 0;
+    else q = (M + (1ull << (d - 1))) >> d;
+    return (bits >> 63) ? -(long long)q : (long long)q;
+}
+
+__device__ __forceinline__ int exp_of(double w) {
+    const int e = (int)(((unsigned long long)__double_as_longlong(w) >> 52) & 0x7FFull);
+    return e > 0 ? e : 1;
+}
+
+// ------------------------------------------------------------------------------------------------------------
 // Device-resident solver state (one instance per handle).
 struct CycleState {
     int stopped;   // the inner cycle has ended (written only by the sketched-QR kernel)

@@ -27,28 +27,6 @@ namespace cg = cooperative_groups;
 namespace sfg {
 
 // ---------------------------------------------------------------------------------------------------------------
-// 64-bit fixed-point image of w relative to the block exponent Eb (max biased exponent in the block, >= 1):
-// w ~= q * 2^(Eb + H - 1075), |q| <= 2^53, rounded to nearest (ties away from zero).  Integer operations only.
-__device__ __forceinline__ long long to_fixed(double w, int Eb, int H) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(w);
-    const int e = (int)((bits >> 52) & 0x7FFull);
-    unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
-    int ee = e;
-    if (e != 0) M |= (1ull << 52);
-    else ee = 1;
-    const int d = Eb - ee + H;
-    unsigned long long q;
-    if (d <= 0) q = M;
-    else if (d >= 55) q = 0;
-    else q = (M + (1ull << (d - 1))) >> d;
-    return (bits >> 63) ? -(long long)q : (long long)q;
-}
-
-__device__ __forceinline__ int exp_of(double w) {
-    const int e = (int)(((unsigned long long)__double_as_longlong(w) >> 52) & 0x7FFull);
-    return e > 0 ? e : 1;
-}
-
 // Per-block sketch partials from the gather lists: out(rr, sum over the list of sketch row rr of +-x[offset]).
 // A warp takes 4 sketch rows at a time and issues the list loads of all four before any gather, so each warp keeps
 // several independent loads in flight; sums are formed lane-strided, then by a fixed shuffle tree.

@@ -28,8 +28,8 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SKETCH_KIND = {"sparse_sign": 0, "identity": 1}
 
 EXPORTED = ["sfgmres_create", "sfgmres_set_option", "sfgmres_get_option", "sfgmres_solve", "sfgmres_inner_cycle",
-            "sfgmres_sketch_apply", "sfgmres_sketch_pattern", "sfgmres_spmv", "sfgmres_destroy",
-            "sfgmres_last_error", "sfgmres_version"]
+            "sfgmres_sketch_apply", "sfgmres_sketch_apply_noalloc", "sfgmres_sketch_pattern", "sfgmres_spmv",
+            "sfgmres_destroy", "sfgmres_last_error", "sfgmres_version"]
 
 
 class Stats(C.Structure):
@@ -60,6 +60,7 @@ def load():
     lib.sfgmres_solve.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, C.POINTER(Stats)]
     lib.sfgmres_inner_cycle.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, C.POINTER(i32), C.POINTER(i32)]
     lib.sfgmres_sketch_apply.argtypes = [vp, i32, vp, vp]
+    lib.sfgmres_sketch_apply_noalloc.argtypes = [i64, i32, i32, u64, vp, vp, vp]
     lib.sfgmres_sketch_pattern.argtypes = [vp, i32, vp, vp]
     lib.sfgmres_spmv.argtypes = [vp, vp, vp]
     lib.sfgmres_destroy.argtypes = [vp]
@@ -143,6 +144,14 @@ def sfgmres_inner_cycle(h: int, v, z, m: int, s: int, k: int, basis=None, y=None
 
 def sfgmres_sketch_apply(h: int, s: int, v, c) -> None:
     _check(h, load().sfgmres_sketch_apply(h, s, _ptr(v), _ptr(c)), allow_positive=False)
+
+
+def sfgmres_sketch_apply_noalloc(n: int, s: int, zeta: int, sketch_seed: int, v, c, stream=None) -> None:
+    """c = S v with no device allocation (for callers that cannot allocate); enqueued on ``stream``."""
+    lib = load()
+    rc = lib.sfgmres_sketch_apply_noalloc(n, s, zeta, sketch_seed, _ptr(v), _ptr(c), stream)
+    if rc != 0:
+        raise SFGMRESError(rc, lib.sfgmres_last_error(None).decode())
 
 
 def sfgmres_sketch_pattern(h: int, s: int, rows, signs) -> None:
