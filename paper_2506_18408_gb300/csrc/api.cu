@@ -206,7 +206,7 @@ int build_sketch(sfgmres_ctx* h, int s) {
     h->sk_s = -1;
     const int64_t tot = (int64_t)h->n * zeta;
     const int64_t nseg = (int64_t)h->nblk * s + 1;
-    if (nseg > INT32_MAX || tot >= INT32_MAX)
+    if (nseg > INT32_MAX || tot + 8 * nseg >= INT32_MAX)
         return fail(h, SFGMRES_ERR_INVALID_ARG, "sketch too large for 32-bit gather lists");
     int* rows = nullptr;
     int8_t* neg = nullptr;
@@ -215,11 +215,16 @@ int build_sketch(sfgmres_ctx* h, int s) {
     CK(cudaMalloc(&neg, tot));
     CK(cudaMalloc(&counts, nseg * sizeof(int)));
     CK(cudaMalloc(&h->seg, nseg * sizeof(int)));
-    CK(cudaMalloc(&h->ent, tot * sizeof(uint16_t)));
     CK(cudaMemsetAsync(counts, 0, nseg * sizeof(int), h->st));
     Plan dummy;
     launch_sketch_pattern(dummy, h->n, s, zeta, h->kind, h->seed, rows, neg, h->st);
-    launch_sketch_build(h->n, s, zeta, h->Bn, h->nblk, rows, neg, counts, h->seg, h->ent, h->st);
+    launch_sketch_count(h->n, s, zeta, h->Bn, h->nblk, rows, counts, h->seg, h->st);
+    std::vector<int> hs(nseg);
+    CK(cudaMemcpyAsync(hs.data(), h->seg, nseg * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const int64_t total = hs[nseg - 1];
+    CK(cudaMalloc(&h->ent, (total + 8) * sizeof(uint16_t)));  // +8: room for one padding group
+    launch_sketch_fill(h->n, s, zeta, h->Bn, h->nblk, rows, neg, h->seg, h->ent, total, h->st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->st));
     cudaFree(rows);
@@ -228,8 +233,6 @@ int build_sketch(sfgmres_ctx* h, int s) {
     {
         // FP64 sketch terms are 53-bit integers summed exactly in 64 bits: lists longer than 1023 entries get
         // extra right shifts so that no sum can overflow
-        std::vector<int> hs(nseg);
-        CK(cudaMemcpy(hs.data(), h->seg, nseg * sizeof(int), cudaMemcpyDeviceToHost));
         int longest = 0;
         for (int64_t q = 0; q + 1 < nseg; ++q) longest = std::max(longest, hs[q + 1] - hs[q]);
         int H = 0;

@@ -134,9 +134,74 @@ __device__ __forceinline__ long long to_fixed(double w, int Eb, int H) {
     return (bits >> 63) ? -(long long)q : (long long)q;
 }
 
+// FP32 analogue: w ~= q * 2^(Eb + H - 179) with |q| <= 2^53 (the 24-bit significand placed 29 bits up, so values
+// within 2^29 of the block maximum are represented exactly).
+__device__ __forceinline__ long long to_fixed(float w, int Eb, int H) {
+    const unsigned bits = __float_as_uint(w);
+    const int e = (int)((bits >> 23) & 0xFFu);
+    unsigned long long M = (unsigned long long)(bits & 0x7FFFFFu);
+    int ee = e;
+    if (e != 0) M |= (1ull << 23);
+    else ee = 1;
+    M <<= 29;
+    const int d = Eb - ee + H;
+    unsigned long long q;
+    if (d <= 0) q = M;
+    else if (d >= 55) q = 0;
+    else q = (M + (1ull << (d - 1))) >> d;
+    return (bits >> 31) ? -(long long)q : (long long)q;
+}
+
+__device__ __forceinline__ int exp_of(float w) {
+    const int e = (int)((__float_as_uint(w) >> 23) & 0xFFu);
+    return e > 0 ? e : 1;
+}
+
+// Value of one unit of the fixed-point image: 2^(Eb + H - 1075) for FP64 data, 2^(Eb + H - 179) for FP32 data.
+__device__ __forceinline__ double fixed_unit(double, int Eb, int H) { return ldexp(1.0, Eb + H - 1075); }
+__device__ __forceinline__ double fixed_unit(float, int Eb, int H) { return ldexp(1.0, Eb + H - 179); }
+__device__ __forceinline__ bool exp_nonfinite(double, int Eb) { return Eb >= 2047; }
+__device__ __forceinline__ bool exp_nonfinite(float, int Eb) { return Eb >= 255; }
+
 __device__ __forceinline__ int exp_of(double w) {
     const int e = (int)(((unsigned long long)__double_as_longlong(w) >> 52) & 0x7FFull);
     return e > 0 ? e : 1;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Sketch gather lists.  For row block b and sketch row r the list ent[seg[b*s + r] .. seg[b*s + r + 1]) holds one
+// 16-bit entry per nonzero S_rj with j in the block: bits 0..14 the offset of j in the block, bit 15 the sign.  Every
+// list starts at a multiple of 8 entries and is padded to a multiple of 8 with entries that point at the block's
+// zero slot (offset Bn), so a list is read with aligned 16-byte loads and no bounds checks.
+template <typename T>
+__device__ __forceinline__ T sum8(const uint4 d, const T* __restrict__ x) {
+    const unsigned w[4] = {d.x, d.y, d.z, d.w};
+    T acc = T(0);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const unsigned en = (w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+        const T v = x[en & 0x7fffu];
+        acc += (en & 0x8000u) ? -v : v;
+    }
+    return acc;
+}
+
+// Sum of +-x[offset] over the list [a, e) in list order (deterministic), four 16-byte loads in flight.
+template <typename T>
+__device__ __forceinline__ T sum_list(const uint16_t* __restrict__ ent, int a, int e, const T* __restrict__ x) {
+    const uint4* p = reinterpret_cast<const uint4*>(ent + a);
+    const int ng = (e - a) >> 3;
+    T acc = T(0);
+    int g = 0;
+    for (; g + 4 <= ng; g += 4) {
+        uint4 d[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = __ldg(p + g + k);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc += sum8(d[k], x);
+    }
+    for (; g < ng; ++g) acc += sum8(__ldg(p + g), x);
+    return acc;
 }
 
 // ------------------------------------------------------------------------------------------------------------

@@ -27,77 +27,71 @@ namespace cg = cooperative_groups;
 namespace sfg {
 
 // ---------------------------------------------------------------------------------------------------------------
-// Per-block sketch partials from the gather lists: out(rr, sum over the list of sketch row rr of +-x[offset]).
-// A warp takes 4 sketch rows at a time and issues the list loads of all four before any gather, so each warp keeps
-// several independent loads in flight; sums are formed lane-strided, then by a fixed shuffle tree.
-template <typename T, typename F>
-__device__ __forceinline__ void gather_rows(int b, int s, const int* __restrict__ seg,
-                                            const uint16_t* __restrict__ ent, const T* __restrict__ x, F out) {
-    constexpr int RW = 4, KU = 2;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int rb = warp * RW; rb < s; rb += nw * RW) {
-        int a[RW], e[RW];
-        int maxc = 0;
-#pragma unroll
-        for (int u = 0; u < RW; ++u) {
-            const int rr = rb + u;
-            a[u] = (rr < s) ? seg[(int64_t)b * s + rr] : 0;
-            e[u] = (rr < s) ? seg[(int64_t)b * s + rr + 1] : 0;
-            maxc = max(maxc, e[u] - a[u]);
-        }
-        T acc[RW];
-#pragma unroll
-        for (int u = 0; u < RW; ++u) acc[u] = T(0);
-        for (int off = lane; off < maxc; off += 32 * KU) {
-            unsigned en[RW][KU];
-#pragma unroll
-            for (int u = 0; u < RW; ++u)
-#pragma unroll
-                for (int k = 0; k < KU; ++k) {
-                    const int q = a[u] + off + 32 * k;
-                    en[u][k] = (q < e[u]) ? (unsigned)ent[q] : 0xFFFFFFFFu;
-                }
-#pragma unroll
-            for (int u = 0; u < RW; ++u)
-#pragma unroll
-                for (int k = 0; k < KU; ++k) {
-                    if (en[u][k] != 0xFFFFFFFFu) {
-                        const T v = x[en[u][k] & 0x7fffu];
-                        acc[u] += (en[u][k] & 0x8000u) ? -v : v;
-                    }
-                }
-        }
-#pragma unroll
-        for (int u = 0; u < RW; ++u) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
-            if (lane == 0 && rb + u < s) out(rb + u, acc[u]);
-        }
+// Phase 1, one thread per row: w' = A u_i fused with storing w' (global W and the shared block copy) and the
+// window dot products acc_q += u_{lo+q}[r] * w'[r].  The window values and the next row group's extents are loaded
+// before the row's SpMV, so they are in flight together.  Returns the thread's largest exponent of w'.
+template <int NW, typename MT, typename VT, typename AT>
+__device__ __forceinline__ int spmv_dots_scalar(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                                const MT* __restrict__ val, const VT* __restrict__ Ub, int i, int lo,
+                                                int r0, int r1, AT* __restrict__ wblk, AT* __restrict__ W,
+                                                AT (&acc)[NW > 0 ? NW : 1]) {
+    const int lane = threadIdx.x & 31;
+    const VT* x = Ub + (int64_t)i * n;
+    int emax = 1;
+    int rw = r0 + (threadIdx.x & ~31);
+    int a = 0, len = 0;
+    if (rw + lane < r1) {
+        a = __ldg(rp + rw + lane);
+        len = __ldg(rp + rw + lane + 1) - a;
     }
+    for (; rw < r1; rw += blockDim.x) {  // warp-uniform loop
+        const int r = rw + lane;
+        const bool ok = r < r1;
+        AT uw[NW > 0 ? NW : 1];
+#pragma unroll
+        for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_plain(Ub + (int64_t)(lo + q) * n + r) : AT(0);
+        const int rn = r + (int)blockDim.x;
+        int an = 0, lenn = 0;
+        if (rn < r1) {
+            an = __ldg(rp + rn);
+            lenn = __ldg(rp + rn + 1) - an;
+        }
+        const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+        AT sum = AT(0);
+        for (int pk = 0; pk < maxlen; pk += 4) {
+            switch (min(maxlen - pk, 4)) {
+                case 1: row_chunk<1>(col, val, x, a, len, pk, sum); break;
+                case 2: row_chunk<2>(col, val, x, a, len, pk, sum); break;
+                case 3: row_chunk<3>(col, val, x, a, len, pk, sum); break;
+                default: row_chunk<4>(col, val, x, a, len, pk, sum); break;
+            }
+        }
+        if (ok) {
+            W[r] = sum;
+            wblk[r - r0] = sum;
+        }
+#pragma unroll
+        for (int q = 0; q < NW; ++q) acc[q] += uw[q] * sum;
+        emax = max(emax, exp_of(sum));
+        a = an;
+        len = lenn;
+    }
+    return emax;
 }
 
-// Stores the block of w' and forms its dot products with the NW window vectors u_lo.. (per-block partials into
-// hpart); returns the thread's largest FP64 exponent of w' (for the fixed-point sketch).
+// Phase 1 tail for the sub-warp path (w' already in shared memory): store w' and accumulate the window dots.
 template <int NW, typename VT, typename AT>
-__device__ __forceinline__ int dots_window(int n, int r0, int r1, const VT* __restrict__ Ub, int lo,
-                                           const AT* __restrict__ wblk, AT* __restrict__ W, AT* __restrict__ hpart,
-                                           int b, AT* red) {
-    AT acc[NW > 0 ? NW : 1];
-#pragma unroll
-    for (int q = 0; q < NW; ++q) acc[q] = AT(0);
+__device__ __forceinline__ int dots_pass(int n, int r0, int r1, const VT* __restrict__ Ub, int lo,
+                                         const AT* __restrict__ wblk, AT* __restrict__ W,
+                                         AT (&acc)[NW > 0 ? NW : 1]) {
     int emax = 1;
 #pragma unroll 2
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
         const AT w = wblk[r - r0];
         W[r] = w;
-        if constexpr (sizeof(AT) == 8) emax = max(emax, exp_of((double)w));
+        emax = max(emax, exp_of(w));
 #pragma unroll
         for (int q = 0; q < NW; ++q) acc[q] += ld_plain(Ub + (int64_t)(lo + q) * n + r) * w;
-    }
-#pragma unroll
-    for (int q = 0; q < NW; ++q) {
-        const AT v = block_sum_lean(acc[q], red);
-        if (threadIdx.x == 0) hpart[(int64_t)b * kMaxTrunc + q] = v;
     }
     return emax;
 }
@@ -127,13 +121,15 @@ __device__ __forceinline__ AT axpy_window(int n, int r0, int r1, VT* __restrict_
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-template <int V, int U, typename MT, typename VT, typename AT>
+// Shared memory: the block of w' (Bn + 1 slots of AT, slot Bn = 0 for the list padding).  FP64: the block is
+// converted in place to its 64-bit fixed-point image before the sketch sums.
+template <int V, int U, int NW, typename MT, typename VT, typename AT>
 __global__ void __launch_bounds__(512, 2)
-    k_inner_spmv(int n, int Bn, int s, int t, int i, int H, const int* __restrict__ rp, const int* __restrict__ col,
+    k_inner_spmv(int n, int Bn, int s, int i, int H, const int* __restrict__ rp, const int* __restrict__ col,
                  const MT* __restrict__ val, const VT* __restrict__ Ub, AT* __restrict__ W, AT* __restrict__ hpart,
                  AT* __restrict__ cpart, const int* __restrict__ seg, const uint16_t* __restrict__ ent,
                  const CycleState* __restrict__ cyc) {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     AT* wblk = reinterpret_cast<AT*>(smem_raw);
     __shared__ AT red[512];
     __shared__ int stop_sh, emax_sh[16];
@@ -143,40 +139,45 @@ __global__ void __launch_bounds__(512, 2)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int b = blockIdx.x;
     const int r0 = b * Bn, r1 = min(n, r0 + Bn);
-    spmv_rows_to_smem<V, U, MT, VT, AT>(rp, col, val, Ub + (int64_t)i * n, r0, r1, wblk);
-    __syncthreads();
-    // w' to global and the truncated-Arnoldi dots against u_lo..u_i (window size a compile-time count)
-    const int lo = (t > 0) ? max(0, i - t + 1) : i + 1;
-    const int nwin = i + 1 - lo;
-    int emax = 1;
-    switch (nwin) {
-        case 0: emax = dots_window<0>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
-        case 1: emax = dots_window<1>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
-        case 2: emax = dots_window<2>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
-        case 3: emax = dots_window<3>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
-        case 4: emax = dots_window<4>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
-        case 5: emax = dots_window<5>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
-        case 6: emax = dots_window<6>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
-        case 7: emax = dots_window<7>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
-        default: emax = dots_window<8>(n, r0, r1, Ub, lo, wblk, W, hpart, b, red); break;
+    const int lo = i - NW + 1;  // window u_lo..u_i (NW = min(t, i+1))
+    AT acc[NW > 0 ? NW : 1];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) acc[q] = AT(0);
+    int emax;
+    if constexpr (V == 1) {
+        emax = spmv_dots_scalar<NW>(n, rp, col, val, Ub, i, lo, r0, r1, wblk, W, acc);
+    } else {
+        spmv_rows_vector<V, U, MT, VT, AT>(rp, col, val, Ub + (int64_t)i * n, r0, r1, wblk);
+        __syncthreads();
+        emax = dots_pass<NW>(n, r0, r1, Ub, lo, wblk, W, acc);
     }
+    if (threadIdx.x == 0) wblk[Bn] = AT(0);
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const AT v = block_sum_lean(acc[q], red);
+        if (threadIdx.x == 0) hpart[(int64_t)b * kMaxTrunc + q] = v;
+    }
+    const int* sg = seg + (int64_t)b * s;
     if constexpr (sizeof(AT) == 8) {
-        // exact fixed-point sketch partials: block exponent, in-place conversion, integer gather sums
+        // exact fixed-point sketch sums (integer adds; the FP64 pipe stays with the SpMV)
         emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
         if (lane == 0) emax_sh[warp] = emax;
         __syncthreads();
         int Eb = 1;
         for (int q = 0; q < nw; ++q) Eb = max(Eb, emax_sh[q]);
         long long* qblk = reinterpret_cast<long long*>(wblk);
-        for (int r = threadIdx.x; r < r1 - r0; r += blockDim.x) qblk[r] = to_fixed((double)wblk[r], Eb, H);
+        for (int r = threadIdx.x; r <= Bn; r += blockDim.x) qblk[r] = (r < r1 - r0) ? to_fixed((double)wblk[r], Eb, H) : 0;
         __syncthreads();
-        const double scale_fx = ldexp(1.0, Eb + H - 1075);
-        gather_rows<long long>(b, s, seg, ent, qblk, [&](int rr, long long v) {
-            cpart[(int64_t)b * s + rr] = (Eb >= 2047) ? (AT)NAN : (AT)((double)v * scale_fx);
-        });
+        const double unit = fixed_unit(0.0, Eb, H);
+        const bool bad = exp_nonfinite(0.0, Eb);
+        for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
+            const long long v = sum_list(ent, sg[rr], sg[rr + 1], qblk);
+            cpart[(int64_t)b * s + rr] = bad ? (AT)NAN : (AT)((double)v * unit);
+        }
     } else {
         __syncthreads();
-        gather_rows<AT>(b, s, seg, ent, wblk, [&](int rr, AT v) { cpart[(int64_t)b * s + rr] = v; });
+        for (int rr = threadIdx.x; rr < s; rr += blockDim.x)
+            cpart[(int64_t)b * s + rr] = sum_list(ent, sg[rr], sg[rr + 1], wblk);
     }
 }
 
@@ -499,13 +500,36 @@ void launch_cycle_start(const Plan& p, int j, const double* v, const double* vsc
     ++g_launches;
 }
 
+template <int V, int U, int NW, typename MT, typename VT, typename AT>
+static void inner_spmv_v(const Plan& p, int i, const MT* val) {
+    const size_t sm = (size_t)(p.Bn + 1) * sizeof(AT);
+    set_smem((const void*)k_inner_spmv<V, U, NW, MT, VT, AT>, sm);
+    k_inner_spmv<V, U, NW, MT, VT, AT><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.s, i, p.sk_headroom, p.rp, p.col,
+                                                                 val, (const VT*)p.U, (AT*)p.W, (AT*)p.hpart,
+                                                                 (AT*)p.cpart, p.seg, p.ent, p.cyc);
+}
+
+template <int NW, typename MT, typename VT, typename AT>
+static void inner_spmv_nw(const Plan& p, int i, const MT* val) {
+    if (p.vec == 1) inner_spmv_v<1, 1, NW, MT, VT, AT>(p, i, val);
+    else if (p.vec <= 8) inner_spmv_v<8, 4, NW, MT, VT, AT>(p, i, val);
+    else inner_spmv_v<32, 2, NW, MT, VT, AT>(p, i, val);
+}
+
 template <typename MT, typename VT, typename AT>
 static void inner_spmv_t(const Plan& p, int i, const MT* val) {
-    const size_t sm = (size_t)p.Bn * sizeof(AT);
-    SFG_SPMV_DISPATCH(p.vec, (set_smem((const void*)k_inner_spmv<VV, UU, MT, VT, AT>, sm),
-                              k_inner_spmv<VV, UU, MT, VT, AT><<<p.nblk, 512, sm, p.st>>>(
-                                  p.n, p.Bn, p.s, p.t, i, p.sk_headroom, p.rp, p.col, val, (const VT*)p.U,
-                                  (AT*)p.W, (AT*)p.hpart, (AT*)p.cpart, p.seg, p.ent, p.cyc)));
+    const int nwin = (p.t > 0) ? std::min(p.t, i + 1) : 0;
+    switch (nwin) {
+        case 0: inner_spmv_nw<0, MT, VT, AT>(p, i, val); break;
+        case 1: inner_spmv_nw<1, MT, VT, AT>(p, i, val); break;
+        case 2: inner_spmv_nw<2, MT, VT, AT>(p, i, val); break;
+        case 3: inner_spmv_nw<3, MT, VT, AT>(p, i, val); break;
+        case 4: inner_spmv_nw<4, MT, VT, AT>(p, i, val); break;
+        case 5: inner_spmv_nw<5, MT, VT, AT>(p, i, val); break;
+        case 6: inner_spmv_nw<6, MT, VT, AT>(p, i, val); break;
+        case 7: inner_spmv_nw<7, MT, VT, AT>(p, i, val); break;
+        default: inner_spmv_nw<8, MT, VT, AT>(p, i, val); break;
+    }
 }
 
 void launch_inner_spmv(const Plan& p, int i) {

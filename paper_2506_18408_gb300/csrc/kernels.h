@@ -80,9 +80,13 @@ struct Plan {
 // ---- sketch (sketch.cu) ----
 void launch_sketch_pattern(const Plan& p, int n, int s, int zeta, int kind, uint64_t seed, int* rows, int8_t* neg,
                            cudaStream_t st);
-// counts: int[nblk*s + 1] zeroed by the caller; seg: int[nblk*s + 1]; ent: uint16[n*zeta]
-void launch_sketch_build(int n, int s, int zeta, int Bn, int nblk, const int* rows, const int8_t* neg, int* counts,
-                         int* seg, uint16_t* ent, cudaStream_t st);
+// Gather lists in two steps: counts (int[nblk*s], zeroed by the caller) and seg (int[nblk*s + 1], list starts with
+// lengths padded to multiples of 8); then, once the caller has read seg[nblk*s] = total and allocated
+// ent (uint16[total + 8]), the fill (padding entries point at the zero slot Bn of each block).
+void launch_sketch_count(int n, int s, int zeta, int Bn, int nblk, const int* rows, int* counts, int* seg,
+                         cudaStream_t st);
+void launch_sketch_fill(int n, int s, int zeta, int Bn, int nblk, const int* rows, const int8_t* neg,
+                        const int* seg, uint16_t* ent, int64_t total, cudaStream_t st);
 // part[nblk*s] = per-block sketch sums of (xscale * x), optionally storing (VT)(xscale*x) into dst
 void launch_sketch_partials(const Plan& p, const double* x, const double* xscale_dev, void* dst, void* part);
 // out[r] = sk_scale * sum_b part[b*s + r]; out2 (optional) gets the same values

@@ -7,6 +7,7 @@
 // summing each sketch row's list in a fixed order -- deterministic, no atomics on floating-point data.
 #include "kernels.h"
 
+#include <algorithm>
 #include <mutex>
 #include <unordered_map>
 
@@ -56,14 +57,15 @@ __global__ void k_seg_count(int n, int s, int zeta, int Bn, const int* __restric
     for (int l = 0; l < zeta; ++l) atomicAdd(counts + (int64_t)b * s + rows[j * zeta + l], 1);
 }
 
-// Exclusive prefix sum of counts[0..len) into seg[0..len] (single block; len up to a few million).
+// Exclusive prefix sum of the list lengths rounded up to multiples of 8 (counts[0..len)) into seg[0..len], so every
+// list starts on a 16-byte boundary (single block; len up to a few million).
 __global__ void k_scan_single(const int* __restrict__ counts, int* __restrict__ seg, int len) {
     __shared__ int sums[1024];
     const int tid = threadIdx.x, T = blockDim.x;
     const int chunk = (len + T - 1) / T;
     const int a = min(len, tid * chunk), bnd = min(len, a + chunk);
     int local = 0;
-    for (int i = a; i < bnd; ++i) local += counts[i];
+    for (int i = a; i < bnd; ++i) local += (counts[i] + 7) & ~7;
     sums[tid] = local;
     __syncthreads();
     for (int off = 1; off < T; off <<= 1) {  // Hillis-Steele inclusive scan of the per-thread totals
@@ -75,9 +77,14 @@ __global__ void k_scan_single(const int* __restrict__ counts, int* __restrict__ 
     int run = sums[tid] - local;
     for (int i = a; i < bnd; ++i) {
         seg[i] = run;
-        run += counts[i];
+        run += (counts[i] + 7) & ~7;
     }
     if (tid == T - 1) seg[len] = sums[T - 1];
+}
+
+__global__ void k_fill_u16(int64_t cnt, uint16_t v, uint16_t* __restrict__ o) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        o[i] = v;
 }
 
 // Fill the gather lists of block b (one warp per block).  Entries of a list appear in the order
@@ -109,63 +116,84 @@ __global__ void k_seg_fill(int n, int s, int zeta, int Bn, const int* __restrict
     }
 }
 
-void launch_sketch_build(int n, int s, int zeta, int Bn, int nblk, const int* rows, const int8_t* neg, int* counts,
-                         int* seg, uint16_t* ent, cudaStream_t st) {
+void launch_sketch_count(int n, int s, int zeta, int Bn, int nblk, const int* rows, int* counts, int* seg,
+                         cudaStream_t st) {
     k_seg_count<<<(n + 255) / 256, 256, 0, st>>>(n, s, zeta, Bn, rows, counts);
     k_scan_single<<<1, 1024, 0, st>>>(counts, seg, nblk * s);
+    g_launches += 2;
+}
+
+void launch_sketch_fill(int n, int s, int zeta, int Bn, int nblk, const int* rows, const int8_t* neg,
+                        const int* seg, uint16_t* ent, int64_t total, cudaStream_t st) {
+    k_fill_u16<<<(int)std::min<int64_t>((total + 8 + 255) / 256, 4096), 256, 0, st>>>(total + 8, (uint16_t)Bn,
+                                                                                        ent);
     k_seg_fill<<<nblk, 32, s * sizeof(int), st>>>(n, s, zeta, Bn, rows, neg, seg, ent);
-    g_launches += 3;
+    g_launches += 2;
 }
 
 // Per-block partial sketch of xs = xscale * x; optionally stores (VT)xs into dst.  The value fed to the sketch is
-// the stored (rounded) one, so S is applied to exactly the vector kept in the basis.
+// the stored (rounded) one, so S is applied to exactly the vector kept in the basis.  One thread per sketch row
+// walks its gather list; FP64 data are summed exactly in 64-bit fixed point, FP32 data in list order.
 template <typename VT, typename AT>
-__global__ void __launch_bounds__(512) k_sketch_partials(int n, int Bn, int s, const double* __restrict__ x,
+__global__ void __launch_bounds__(512) k_sketch_partials(int n, int Bn, int s, int H, const double* __restrict__ x,
                                                          const double* __restrict__ xscale, VT* __restrict__ dst,
                                                          const int* __restrict__ seg,
                                                          const uint16_t* __restrict__ ent, AT* __restrict__ part) {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     AT* xb = reinterpret_cast<AT*>(smem_raw);
+    __shared__ int emax_sh[32];
     const int b = blockIdx.x;
     const int r0 = b * Bn, r1 = min(n, r0 + Bn);
     const double sc = xscale ? *xscale : 1.0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        AT v = (AT)(sc * x[r]);
-        if (dst) {
-            store_as(dst + r, v);
-            v = ld_plain(dst + r);
+    int emax = 1;
+    for (int r = threadIdx.x; r <= Bn; r += blockDim.x) {
+        AT v = AT(0);
+        if (r < r1 - r0) {
+            v = (AT)(sc * x[r0 + r]);
+            if (dst) {
+                store_as(dst + r0 + r, v);
+                v = stored_value(v, dst);
+            }
         }
-        xb[r - r0] = v;
+        xb[r] = v;
+        emax = max(emax, exp_of(v));
     }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int rr = warp; rr < s; rr += nw) {
-        const int a = seg[(int64_t)b * s + rr], e = seg[(int64_t)b * s + rr + 1];
-        AT acc = AT(0);
-        for (int q = a + lane; q < e; q += 32) {
-            const unsigned en = ent[q];
-            const AT v = xb[en & 0x7fffu];
-            acc += (en & 0x8000u) ? -v : v;
+    const int* sg = seg + (int64_t)b * s;
+    if constexpr (sizeof(AT) == 8) {
+        emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
+        if ((threadIdx.x & 31) == 0) emax_sh[threadIdx.x >> 5] = emax;
+        __syncthreads();
+        int Eb = 1;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) Eb = max(Eb, emax_sh[q]);
+        long long* qb = reinterpret_cast<long long*>(xb);
+        for (int r = threadIdx.x; r <= Bn; r += blockDim.x) qb[r] = to_fixed((double)xb[r], Eb, H);
+        __syncthreads();
+        const double unit = fixed_unit(0.0, Eb, H);
+        const bool bad = exp_nonfinite(0.0, Eb);
+        for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
+            const long long v = sum_list(ent, sg[rr], sg[rr + 1], qb);
+            part[(int64_t)b * s + rr] = bad ? (AT)NAN : (AT)((double)v * unit);
         }
-        acc = warp_sum(acc);
-        if (lane == 0) part[(int64_t)b * s + rr] = acc;
+    } else {
+        __syncthreads();
+        for (int rr = threadIdx.x; rr < s; rr += blockDim.x) part[(int64_t)b * s + rr] = sum_list(ent, sg[rr], sg[rr + 1], xb);
     }
 }
 
 void launch_sketch_partials(const Plan& p, const double* x, const double* xscale_dev, void* dst, void* part) {
-    const size_t sm = (size_t)p.Bn * (p.prec == kFP64 ? 8 : 4);
+    const size_t sm = (size_t)(p.Bn + 1) * (p.prec == kFP64 ? 8 : 4);
     if (p.prec == kFP64) {
         set_smem((const void*)k_sketch_partials<double, double>, sm);
-        k_sketch_partials<double, double><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.s, x, xscale_dev, (double*)dst,
-                                                                    p.seg, p.ent, (double*)part);
+        k_sketch_partials<double, double><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.s, p.sk_headroom, x, xscale_dev,
+                                                                    (double*)dst, p.seg, p.ent, (double*)part);
     } else if (p.prec == kFP32) {
         set_smem((const void*)k_sketch_partials<float, float>, sm);
-        k_sketch_partials<float, float><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.s, x, xscale_dev, (float*)dst,
-                                                                  p.seg, p.ent, (float*)part);
+        k_sketch_partials<float, float><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.s, p.sk_headroom, x, xscale_dev,
+                                                                  (float*)dst, p.seg, p.ent, (float*)part);
     } else {
         set_smem((const void*)k_sketch_partials<__nv_bfloat16, float>, sm);
         k_sketch_partials<__nv_bfloat16, float><<<p.nblk, 512, sm, p.st>>>(
-            p.n, p.Bn, p.s, x, xscale_dev, (__nv_bfloat16*)dst, p.seg, p.ent, (float*)part);
+            p.n, p.Bn, p.s, p.sk_headroom, x, xscale_dev, (__nv_bfloat16*)dst, p.seg, p.ent, (float*)part);
     }
     ++g_launches;
 }
