@@ -34,7 +34,7 @@ template <int NW, typename MT, typename VT, typename AT>
 __device__ __forceinline__ int spmv_dots_scalar(int n, const int* __restrict__ rp, const int* __restrict__ col,
                                                 const MT* __restrict__ val, const VT* __restrict__ Ub, int i, int lo,
                                                 int r0, int r1, AT* __restrict__ wblk, AT* __restrict__ W,
-                                                AT (&acc)[NW > 0 ? NW : 1]) {
+                                                AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
     const int lane = threadIdx.x & 31;
     const VT* x = Ub + (int64_t)i * n;
     int emax = 1;
@@ -50,6 +50,9 @@ __device__ __forceinline__ int spmv_dots_scalar(int n, const int* __restrict__ r
         AT uw[NW > 0 ? NW : 1];
 #pragma unroll
         for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_plain(Ub + (int64_t)(lo + q) * n + r) : AT(0);
+        AT ui;  // u_i[r] (the last window vector when there is a window) for ||u_i||^2
+        if constexpr (NW > 0) ui = uw[NW - 1];
+        else ui = ok ? ld_plain(x + r) : AT(0);
         const int rn = r + (int)blockDim.x;
         int an = 0, lenn = 0;
         if (rn < r1) {
@@ -72,6 +75,7 @@ __device__ __forceinline__ int spmv_dots_scalar(int n, const int* __restrict__ r
         }
 #pragma unroll
         for (int q = 0; q < NW; ++q) acc[q] += uw[q] * sum;
+        nrm += ui * ui;
         emax = max(emax, exp_of(sum));
         a = an;
         len = lenn;
@@ -81,54 +85,34 @@ __device__ __forceinline__ int spmv_dots_scalar(int n, const int* __restrict__ r
 
 // Phase 1 tail for the sub-warp path (w' already in shared memory): store w' and accumulate the window dots.
 template <int NW, typename VT, typename AT>
-__device__ __forceinline__ int dots_pass(int n, int r0, int r1, const VT* __restrict__ Ub, int lo,
+__device__ __forceinline__ int dots_pass(int n, int r0, int r1, const VT* __restrict__ Ub, int lo, int i,
                                          const AT* __restrict__ wblk, AT* __restrict__ W,
-                                         AT (&acc)[NW > 0 ? NW : 1]) {
+                                         AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
     int emax = 1;
 #pragma unroll 2
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
         const AT w = wblk[r - r0];
         W[r] = w;
         emax = max(emax, exp_of(w));
+        const AT ui = ld_plain(Ub + (int64_t)i * n + r);
+        nrm += ui * ui;
 #pragma unroll
         for (int q = 0; q < NW; ++q) acc[q] += ld_plain(Ub + (int64_t)(lo + q) * n + r) * w;
     }
     return emax;
 }
 
-// u_{i+1} = 2^p2 (w' - sum_q coef_q u_{lo+q}) over rows [r0, r1), stored in VT; returns the thread's partial
-// squared norm of the stored values.
-template <int NW, typename VT, typename AT>
-__device__ __forceinline__ AT axpy_window(int n, int r0, int r1, VT* __restrict__ Ub, int lo, int i,
-                                          const AT* __restrict__ W, const AT* coef, int p2, AT sc2) {
-    AT cf[NW > 0 ? NW : 1];
-#pragma unroll
-    for (int q = 0; q < NW; ++q) cf[q] = coef[q];
-    VT* un = Ub + (int64_t)(i + 1) * n;
-    AT nacc = AT(0);
-#pragma unroll 2
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        AT u = W[r];
-#pragma unroll
-        for (int q = 0; q < NW; ++q) u -= cf[q] * ld_plain(Ub + (int64_t)(lo + q) * n + r);
-        if constexpr (sizeof(AT) == 8) u = mul_pow2((double)u, p2);
-        else u = u * sc2;
-        store_as(un + r, u);
-        const AT us = stored_value(u, un);  // the norm of the vector as stored
-        nacc += us * us;
-    }
-    return nacc;
-}
-
 // ---------------------------------------------------------------------------------------------------------------
 // Shared memory: the block of w' (Bn + 1 slots of AT, slot Bn = 0 for the list padding).  FP64: the block is
 // converted in place to its 64-bit fixed-point image before the sketch sums.
+// At most 56 registers per thread (registers are allocated in units of 8 per thread): two 512-thread CTAs per SM
+// then leave room for the sketched-QR cluster's CTAs to run beside them instead of displacing them.
 template <int V, int U, int NW, typename MT, typename VT, typename AT>
-__global__ void __launch_bounds__(512, 2)
+__global__ void __maxnreg__(56)
     k_inner_spmv(int n, int Bn, int s, int i, int H, const int* __restrict__ rp, const int* __restrict__ col,
                  const MT* __restrict__ val, const VT* __restrict__ Ub, AT* __restrict__ W, AT* __restrict__ hpart,
-                 AT* __restrict__ cpart, const int* __restrict__ seg, const uint16_t* __restrict__ ent,
-                 const CycleState* __restrict__ cyc) {
+                 AT* __restrict__ cpart, AT* __restrict__ normpart, const int* __restrict__ seg,
+                 const uint16_t* __restrict__ ent, const CycleState* __restrict__ cyc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AT* wblk = reinterpret_cast<AT*>(smem_raw);
     __shared__ AT red[512];
@@ -144,14 +128,19 @@ __global__ void __launch_bounds__(512, 2)
 #pragma unroll
     for (int q = 0; q < NW; ++q) acc[q] = AT(0);
     int emax;
+    AT nrm = AT(0);  // ||u_i||^2 over the block (the vector this step multiplies)
     if constexpr (V == 1) {
-        emax = spmv_dots_scalar<NW>(n, rp, col, val, Ub, i, lo, r0, r1, wblk, W, acc);
+        emax = spmv_dots_scalar<NW>(n, rp, col, val, Ub, i, lo, r0, r1, wblk, W, acc, nrm);
     } else {
         spmv_rows_vector<V, U, MT, VT, AT>(rp, col, val, Ub + (int64_t)i * n, r0, r1, wblk);
         __syncthreads();
-        emax = dots_pass<NW>(n, r0, r1, Ub, lo, wblk, W, acc);
+        emax = dots_pass<NW>(n, r0, r1, Ub, lo, i, wblk, W, acc, nrm);
     }
     if (threadIdx.x == 0) wblk[Bn] = AT(0);
+    {
+        const AT v = block_sum_lean(nrm, red);
+        if (threadIdx.x == 0) normpart[b] = v;
+    }
 #pragma unroll
     for (int q = 0; q < NW; ++q) {
         const AT v = block_sum_lean(acc[q], red);
@@ -182,22 +171,37 @@ __global__ void __launch_bounds__(512, 2)
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-template <typename VT, typename AT>
+// Truncated-Arnoldi update (NW = window size).  Each thread first loads its first PF rows of w' and of the window
+// vectors (they do not depend on the scalars), then forms sigma_i, the coefficients and its share of the sketched
+// column, so the row data are already in flight while the reductions run.
+template <int NW, typename VT, typename AT>
 __global__ void __launch_bounds__(512)
-    k_inner_axpy(int n, int Bn, int nblk, int s, int t, int i, int last, double sk_scale, VT* __restrict__ Ub,
-                 const AT* __restrict__ W, double* __restrict__ sigma, AT* __restrict__ normpart,
+    k_inner_axpy(int n, int Bn, int nblk, int s, int i, int last, double sk_scale, VT* __restrict__ Ub,
+                 const AT* __restrict__ W, double* __restrict__ sigma, const AT* __restrict__ normpart,
                  const AT* __restrict__ hpart, const AT* __restrict__ cpart, double* __restrict__ C,
                  double* __restrict__ hco, CycleState* __restrict__ cyc) {
-    __shared__ AT red[512];
+    constexpr int PF = 2;
     __shared__ AT coef_sh[kMaxTrunc];
     __shared__ double sig_sh;
     __shared__ int stop_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int b = blockIdx.x;
+    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
+    const int lo = i - NW + 1;
+    AT wv[PF], uv[PF][NW > 0 ? NW : 1];
+    if (!last) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int r = r0 + threadIdx.x + u * (int)blockDim.x;
+            wv[u] = (r < r1) ? W[r] : AT(0);
+#pragma unroll
+            for (int q = 0; q < NW; ++q) uv[u][q] = (r < r1) ? ld_plain(Ub + (int64_t)(lo + q) * n + r) : AT(0);
+        }
+    }
     if (threadIdx.x == 0) stop_sh = (cyc->stopped || cyc->brk_step <= i) ? 1 : 0;
     __syncthreads();
     if (stop_sh) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int b = blockIdx.x;
-    // sigma_i = 1/||u_i|| from the previous step's partials (double-buffered by step parity)
+    // sigma_i = 1/||u_i|| from the SpMV kernel's per-block partials
     if (warp == 0) {
         double sig = 1.0;
         bool bad = false;
@@ -206,8 +210,7 @@ __global__ void __launch_bounds__(512)
             sig = sigma[0];
         } else {
             AT a = AT(0);
-            const AT* np = normpart + (int64_t)(i & 1) * nblk;
-            for (int q = lane; q < nblk; q += 32) a += np[q];
+            for (int q = lane; q < nblk; q += 32) a += normpart[q];
             a = warp_sum(a);
             const double a2 = (double)a;
             bad = !(a2 > 0.0) || !isfinite(a2);
@@ -230,10 +233,8 @@ __global__ void __launch_bounds__(512)
     __syncthreads();
     if (stop_sh) return;
     const double sig_i = sig_sh;
-    const int lo = (t > 0) ? max(0, i - t + 1) : i + 1;
-    const int nwin = i + 1 - lo;
     // h_l = sigma_l sigma_i (u_l^T w'); the stored update uses sigma_l^2 (u_l^T w')
-    if (warp < nwin) {
+    if (warp < NW) {
         AT a = AT(0);
         for (int q = lane; q < nblk; q += 32) a += hpart[(int64_t)q * kMaxTrunc + warp];
         a = warp_sum(a);
@@ -254,32 +255,43 @@ __global__ void __launch_bounds__(512)
     }
     if (last) return;
     __syncthreads();
-    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
+    // u_{i+1} = 2^p2 (w' - sum_q coef_q u_{lo+q}), 2^p2 the power of two just below sigma_i
     int p2;
-    frexp(sig_i, &p2);  // sigma_i = f * 2^p2, f in [0.5, 1): rescale by 2^(p2-1)
+    frexp(sig_i, &p2);  // sigma_i = f * 2^p2, f in [0.5, 1)
     p2 -= 1;
     const AT sc2 = (AT)ldexp(1.0, p2);
-    AT nacc;
-    switch (nwin) {
-        case 0: nacc = axpy_window<0>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
-        case 1: nacc = axpy_window<1>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
-        case 2: nacc = axpy_window<2>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
-        case 3: nacc = axpy_window<3>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
-        case 4: nacc = axpy_window<4>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
-        case 5: nacc = axpy_window<5>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
-        case 6: nacc = axpy_window<6>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
-        case 7: nacc = axpy_window<7>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
-        default: nacc = axpy_window<8>(n, r0, r1, Ub, lo, i, W, coef_sh, p2, sc2); break;
+    AT cf[NW > 0 ? NW : 1];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) cf[q] = coef_sh[q];
+    VT* un = Ub + (int64_t)(i + 1) * n;
+    auto update = [&](int r, AT u, const AT (&uq)[NW > 0 ? NW : 1]) {
+#pragma unroll
+        for (int q = 0; q < NW; ++q) u -= cf[q] * uq[q];
+        if constexpr (sizeof(AT) == 8) u = mul_pow2((double)u, p2);
+        else u = u * sc2;
+        store_as(un + r, u);
+    };
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+        const int r = r0 + threadIdx.x + u * (int)blockDim.x;
+        if (r < r1) update(r, wv[u], uv[u]);
     }
-    nacc = block_sum_lean(nacc, red);
-    if (threadIdx.x == 0) normpart[(int64_t)((i + 1) & 1) * nblk + b] = nacc;
+#pragma unroll 2
+    for (int r = r0 + threadIdx.x + PF * (int)blockDim.x; r < r1; r += blockDim.x) {
+        AT uq[NW > 0 ? NW : 1];
+#pragma unroll
+        for (int q = 0; q < NW; ++q) uq[q] = ld_plain(Ub + (int64_t)(lo + q) * n + r);
+        update(r, W[r], uq);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------------------------
 // Sketched QR update of column i on a cluster of CTAs; CTA q of the cluster owns rows [s q / nq, s (q+1) / nq) of
 // Q and of the working vectors, and partial dot products are exchanged through distributed shared memory and summed
-// in rank order (deterministic).  Every early exit is decided from values all CTAs of the cluster share.
-__global__ void __launch_bounds__(256)
+// in rank order (deterministic).  Every early exit is decided from values all CTAs of the cluster share.  CTAs are
+// small (128 threads) so they fit beside the inner SpMV's CTAs, and every long FP64 dependency chain is split into
+// four independent accumulators (combined in a fixed order).
+__global__ void __launch_bounds__(128)
     k_inner_qr(int s, int m, int i, const double* __restrict__ C, double* __restrict__ Q, double* __restrict__ R,
                double* __restrict__ d, double* __restrict__ e, double* __restrict__ rho,
                CycleState* __restrict__ cyc) {
@@ -291,7 +303,7 @@ __global__ void __launch_bounds__(256)
     double* p = qsm;               // [nrmax] this CTA's rows of the working vector
     double* apart = qsm + nrmax;   // [m] partial projections over this CTA's rows
     double* a = apart + m;         // [m] full projections
-    __shared__ double red[256];
+    __shared__ double red[128];
     __shared__ double scal[4];
     __shared__ int code_sh;
     // state read by every CTA before the first cluster barrier (rank 0 writes it only after the last one)
@@ -312,9 +324,16 @@ __global__ void __launch_bounds__(256)
     for (int pass = 0; pass < 2; ++pass) {
         for (int l = threadIdx.x; l < i; l += blockDim.x) {
             const double* ql = Q + (int64_t)l * s + rlo;
-            double acc = 0.0;
-            for (int r = 0; r < nr; ++r) acc += ql[r] * p[r];
-            apart[l] = acc;
+            double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+            int r = 0;
+            for (; r + 4 <= nr; r += 4) {
+                c0 += ql[r] * p[r];
+                c1 += ql[r + 1] * p[r + 1];
+                c2 += ql[r + 2] * p[r + 2];
+                c3 += ql[r + 3] * p[r + 3];
+            }
+            for (; r < nr; ++r) c0 += ql[r] * p[r];
+            apart[l] = (c0 + c1) + (c2 + c3);
         }
         cl.sync();
         for (int l = threadIdx.x; l < i; l += blockDim.x) {
@@ -324,9 +343,17 @@ __global__ void __launch_bounds__(256)
         }
         cl.sync();  // every CTA has read the partials before the next pass overwrites them
         for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-            double v = p[r];
-            for (int l = 0; l < i; ++l) v -= a[l] * Q[(int64_t)l * s + rlo + r];
-            p[r] = v;
+            const double* qr = Q + rlo + r;
+            double v0 = p[r], v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            int l = 0;
+            for (; l + 4 <= i; l += 4) {
+                v0 -= a[l] * qr[(int64_t)l * s];
+                v1 -= a[l + 1] * qr[(int64_t)(l + 1) * s];
+                v2 -= a[l + 2] * qr[(int64_t)(l + 2) * s];
+                v3 -= a[l + 3] * qr[(int64_t)(l + 3) * s];
+            }
+            for (; l < i; ++l) v0 -= a[l] * qr[(int64_t)l * s];
+            p[r] = (v0 + v1) + (v2 + v3);
         }
         if (q == 0)
             for (int l = threadIdx.x; l < i; l += blockDim.x)
@@ -506,7 +533,7 @@ static void inner_spmv_v(const Plan& p, int i, const MT* val) {
     set_smem((const void*)k_inner_spmv<V, U, NW, MT, VT, AT>, sm);
     k_inner_spmv<V, U, NW, MT, VT, AT><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.s, i, p.sk_headroom, p.rp, p.col,
                                                                  val, (const VT*)p.U, (AT*)p.W, (AT*)p.hpart,
-                                                                 (AT*)p.cpart, p.seg, p.ent, p.cyc);
+                                                                 (AT*)p.cpart, (AT*)p.normpart, p.seg, p.ent, p.cyc);
 }
 
 template <int NW, typename MT, typename VT, typename AT>
@@ -539,11 +566,27 @@ void launch_inner_spmv(const Plan& p, int i) {
     ++g_launches;
 }
 
+template <int NW, typename VT, typename AT>
+static void inner_axpy_nw(const Plan& p, int i, bool last) {
+    k_inner_axpy<NW, VT, AT><<<p.nblk, 512, 0, p.st>>>(p.n, p.Bn, p.nblk, p.s, i, last ? 1 : 0, p.sk_scale,
+                                                       (VT*)p.U, (const AT*)p.W, p.sigma, (const AT*)p.normpart,
+                                                       (const AT*)p.hpart, (const AT*)p.cpart, p.C, p.hco, p.cyc);
+}
+
 template <typename VT, typename AT>
 static void inner_axpy_t(const Plan& p, int i, bool last) {
-    k_inner_axpy<VT, AT><<<p.nblk, 512, 0, p.st>>>(p.n, p.Bn, p.nblk, p.s, p.t, i, last ? 1 : 0, p.sk_scale,
-                                                   (VT*)p.U, (const AT*)p.W, p.sigma, (AT*)p.normpart,
-                                                   (const AT*)p.hpart, (const AT*)p.cpart, p.C, p.hco, p.cyc);
+    const int nwin = (p.t > 0) ? std::min(p.t, i + 1) : 0;
+    switch (nwin) {
+        case 0: inner_axpy_nw<0, VT, AT>(p, i, last); break;
+        case 1: inner_axpy_nw<1, VT, AT>(p, i, last); break;
+        case 2: inner_axpy_nw<2, VT, AT>(p, i, last); break;
+        case 3: inner_axpy_nw<3, VT, AT>(p, i, last); break;
+        case 4: inner_axpy_nw<4, VT, AT>(p, i, last); break;
+        case 5: inner_axpy_nw<5, VT, AT>(p, i, last); break;
+        case 6: inner_axpy_nw<6, VT, AT>(p, i, last); break;
+        case 7: inner_axpy_nw<7, VT, AT>(p, i, last); break;
+        default: inner_axpy_nw<8, VT, AT>(p, i, last); break;
+    }
 }
 
 void launch_inner_axpy(const Plan& p, int i, bool last) {
@@ -559,7 +602,7 @@ cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st) {
     set_smem((const void*)k_inner_qr, sm);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kQrCluster, 1, 1);
-    cfg.blockDim = dim3(256, 1, 1);
+    cfg.blockDim = dim3(128, 1, 1);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
