@@ -126,6 +126,21 @@ SFGMRES_API int sfgmres_get_option(sfgmres_t h, int32_t key, double* value);
 SFGMRES_API int sfgmres_solve(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m, int32_t s, int32_t k,
                   double tol, sfgmres_stats* st);
 
+/* Solve A^T x = b with the same method, parameters, options and sketch as sfgmres_solve (A^T is formed on the
+ * device on first use and kept).  This is the adjoint solve of the linear map b -> x = A^{-1} b: for a loss L(x),
+ * dL/db = A^{-T} dL/dx.  Arguments, special cases and return values as for sfgmres_solve. */
+SFGMRES_API int sfgmres_solve_transpose(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m,
+                                        int32_t s, int32_t k, double tol, sfgmres_stats* st);
+
+/* Replace the stored values of A (same sparsity pattern, same order as at sfgmres_create): vals is float64[nnz],
+ * host or device.  The FP32 copy and the transpose's values follow. */
+SFGMRES_API int sfgmres_update_values(sfgmres_t h, const double* vals);
+
+/* out[p] += alpha * u[row(p)] * v[col(p)] for every stored entry p of A (device pointers; u, v: float64[n],
+ * out: float64[nnz] in the stored order).  With u = A^{-T} dL/dx and v = x, alpha = -1 this accumulates the gradient
+ * of L with respect to the stored values of A (differentiating x = A^{-1} b on the sparsity pattern only). */
+SFGMRES_API int sfgmres_pattern_outer(sfgmres_t h, const double* u, const double* v, double alpha, double* out);
+
 /* One sGMRES preconditioner application z = B_k y_k ~ A^{-1} v (Eq. 3 with r0 = v, x0 = 0; Section 3), with rules
  * C1 and C2 only (C3 needs an outer iteration).  v must have unit 2-norm (it is the outer Arnoldi vector).
  *   v, z       n float64, device pointers

@@ -41,6 +41,13 @@ struct sfgmres_ctx {
     int* col = nullptr;
     double* val = nullptr;
     float* val32 = nullptr;
+    // transpose (built on first use): row pointers, columns, source positions in A, values, FP32 values
+    int* rpT = nullptr;
+    int* colT = nullptr;
+    int* srcT = nullptr;
+    double* valT = nullptr;
+    float* val32T = nullptr;
+    int maxlenT = 0, vecT = 8;
     uint64_t seed = 0;
     cudaStream_t st = nullptr;
     bool own_stream = false;
@@ -245,19 +252,46 @@ int build_sketch(sfgmres_ctx* h, int s) {
     return 0;
 }
 
-int ensure_f32(sfgmres_ctx* h) {
-    if (h->val32) return 0;
-    CK(cudaMalloc(&h->val32, std::max<int64_t>(h->nnz, 1) * sizeof(float)));
-    k_to_f32<<<grid_for(h->nnz), 256, 0, h->st>>>(h->nnz, h->val, h->val32);
+int ensure_f32(sfgmres_ctx* h, bool transpose) {
+    float*& v32 = transpose ? h->val32T : h->val32;
+    if (v32) return 0;
+    CK(cudaMalloc(&v32, std::max<int64_t>(h->nnz, 1) * sizeof(float)));
+    k_to_f32<<<grid_for(h->nnz), 256, 0, h->st>>>(h->nnz, transpose ? h->valT : h->val, v32);
     CK(cudaGetLastError());
     return 0;
 }
 
-// Allocates the workspaces of a solve and fills a Plan.
-int prepare(sfgmres_ctx* h, int m, int s, int t, int jmax, Plan* p) {
+// A^T in CSR form, built on first use (deterministic layout) and kept; values follow sfgmres_update_values.
+int ensure_transpose(sfgmres_ctx* h) {
+    if (h->rpT) return 0;
+    const int64_t nz = std::max<int64_t>(h->nnz, 1);
+    int* counts = nullptr;
+    int* mx = nullptr;
+    CK(cudaMalloc(&h->rpT, ((size_t)h->n + 1) * sizeof(int)));
+    CK(cudaMalloc(&h->colT, nz * sizeof(int)));
+    CK(cudaMalloc(&h->srcT, nz * sizeof(int)));
+    CK(cudaMalloc(&h->valT, nz * sizeof(double)));
+    CK(cudaMalloc(&counts, (size_t)h->n * sizeof(int)));
+    CK(cudaMalloc(&mx, sizeof(int)));
+    CK(cudaMemsetAsync(counts, 0, (size_t)h->n * sizeof(int), h->st));
+    CK(cudaMemsetAsync(mx, 0, sizeof(int), h->st));
+    launch_transpose(h->n, h->nnz, h->rp, h->col, counts, h->rpT, h->colT, h->srcT, mx, h->st);
+    launch_gather_vals(h->nnz, h->srcT, h->val, h->valT, h->st);
+    CK(cudaMemcpyAsync(&h->maxlenT, mx, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    cudaFree(counts);
+    cudaFree(mx);
+    h->vecT = choose_vec(h->nnz, h->n, h->maxlenT);
+    return 0;
+}
+
+// Allocates the workspaces of a solve and fills a Plan (for A, or for A^T when transpose is set).
+int prepare(sfgmres_ctx* h, int m, int s, int t, int jmax, Plan* p, bool transpose = false) {
     int rc;
     if ((rc = build_sketch(h, s))) return rc;
-    if (h->prec != kFP64 && (rc = ensure_f32(h))) return rc;
+    if (transpose && (rc = ensure_transpose(h))) return rc;
+    if (h->prec != kFP64 && (rc = ensure_f32(h, transpose))) return rc;
     const size_t vt = (h->prec == kFP64) ? 8 : (h->prec == kFP32 ? 4 : 2);
     const size_t at = (h->prec == kFP64) ? 8 : 4;
     const size_t n = (size_t)h->n;
@@ -305,11 +339,11 @@ int prepare(sfgmres_ctx* h, int m, int s, int t, int jmax, Plan* p) {
     Plan& P = *p;
     P.n = h->n;
     P.nnz = h->nnz;
-    P.rp = h->rp;
-    P.col = h->col;
-    P.val = h->val;
-    P.val32 = h->val32;
-    P.vec = h->vec;
+    P.rp = transpose ? h->rpT : h->rp;
+    P.col = transpose ? h->colT : h->col;
+    P.val = transpose ? h->valT : h->val;
+    P.val32 = transpose ? h->val32T : h->val32;
+    P.vec = transpose ? (h->vec_opt ? h->vec_opt : h->vecT) : h->vec;
     P.Bn = h->Bn;
     P.nblk = h->nblk;
     P.s = s;
@@ -525,6 +559,8 @@ int sfgmres_destroy(sfgmres_t h) {
     cudaFree(h->col);
     cudaFree(h->val);
     if (h->val32) cudaFree(h->val32);
+    for (void* q : {(void*)h->rpT, (void*)h->colT, (void*)h->srcT, (void*)h->valT, (void*)h->val32T})
+        if (q) cudaFree(q);
     if (h->seg) cudaFree(h->seg);
     if (h->ent) cudaFree(h->ent);
     DevBuf* bufs[] = {&h->U, &h->W, &h->sigma, &h->normpart, &h->hpart, &h->cpart, &h->C, &h->Q, &h->R, &h->d,
@@ -611,8 +647,8 @@ int sfgmres_get_option(sfgmres_t h, int32_t key, double* v) {
     }
 }
 
-int sfgmres_solve(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m, int32_t s, int32_t k,
-                  double tol, sfgmres_stats* st) {
+static int solve_impl(sfgmres_t h, bool transpose, const double* b, const double* x0, double* x, int32_t m,
+                      int32_t s, int32_t k, double tol, sfgmres_stats* st) {
     if (!h) return SFGMRES_ERR_INVALID_ARG;
     if (!b || !x) return fail(h, SFGMRES_ERR_INVALID_ARG, "b and x must not be NULL");
     if (!(tol > 0.0 && tol < 1.0)) return fail(h, SFGMRES_ERR_INVALID_ARG, "tol must be in (0, 1)");
@@ -622,7 +658,7 @@ int sfgmres_solve(sfgmres_t h, const double* b, const double* x0, double* x, int
     const int64_t launches0 = g_launches;
     const int jmax = h->max_outer;
     Plan P;
-    if ((rc = prepare(h, m, s, k, jmax, &P))) return rc;
+    if ((rc = prepare(h, m, s, k, jmax, &P, transpose))) return rc;
     const size_t nbytes = (size_t)h->n * sizeof(double);
     if ((rc = ensure(h, h->bst, nbytes))) return rc;
     if ((rc = ensure(h, h->xst, nbytes))) return rc;
@@ -760,6 +796,43 @@ int sfgmres_solve(sfgmres_t h, const double* b, const double* x0, double* x, int
         }
     }
     return status;
+}
+
+int sfgmres_solve(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m, int32_t s, int32_t k,
+                  double tol, sfgmres_stats* st) {
+    return solve_impl(h, false, b, x0, x, m, s, k, tol, st);
+}
+
+int sfgmres_solve_transpose(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m, int32_t s,
+                            int32_t k, double tol, sfgmres_stats* st) {
+    return solve_impl(h, true, b, x0, x, m, s, k, tol, st);
+}
+
+int sfgmres_update_values(sfgmres_t h, const double* vals) {
+    if (!h) return SFGMRES_ERR_INVALID_ARG;
+    if (!vals && h->nnz > 0) return fail(h, SFGMRES_ERR_INVALID_ARG, "vals must not be NULL");
+    CK(cudaSetDevice(h->dev));
+    if (h->nnz == 0) return SFGMRES_OK;
+    CK(cudaMemcpyAsync(h->val, vals, h->nnz * sizeof(double),
+                       is_device_ptr(vals) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    if (h->val32) k_to_f32<<<grid_for(h->nnz), 256, 0, h->st>>>(h->nnz, h->val, h->val32);
+    if (h->rpT) {
+        launch_gather_vals(h->nnz, h->srcT, h->val, h->valT, h->st);
+        if (h->val32T) k_to_f32<<<grid_for(h->nnz), 256, 0, h->st>>>(h->nnz, h->valT, h->val32T);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->st));
+    return SFGMRES_OK;
+}
+
+int sfgmres_pattern_outer(sfgmres_t h, const double* u, const double* v, double alpha, double* out) {
+    if (!h) return SFGMRES_ERR_INVALID_ARG;
+    if (!u || !v || (!out && h->nnz > 0)) return fail(h, SFGMRES_ERR_INVALID_ARG, "NULL pointer");
+    CK(cudaSetDevice(h->dev));
+    launch_pattern_outer(h->n, h->rp, h->col, u, v, alpha, out, h->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->st));
+    return SFGMRES_OK;
 }
 
 int sfgmres_inner_cycle(sfgmres_t h, const double* v, double* z, int32_t m, int32_t s, int32_t k, double* basis,

@@ -113,6 +113,14 @@ void launch_spmv_f64(const Plan& p, const double* x, double* y);
 // Raise the dynamic shared-memory limit of kernel `func` to at least `bytes` (cached per kernel).
 void set_smem(const void* func, size_t bytes);
 
+// ---- transpose and pattern gradient (transpose.cu) ----
+// counts: int[n] zeroed by the caller; rpT int[n+1]; colT, srcT int[nnz]; maxlen int (zeroed) gets the longest row
+void launch_transpose(int n, int64_t nnz, const int* rp, const int* col, int* counts, int* rpT, int* colT,
+                      int* srcT, int* maxlen, cudaStream_t st);
+void launch_gather_vals(int64_t nnz, const int* src, const double* val, double* out, cudaStream_t st);
+void launch_pattern_outer(int n, const int* rp, const int* col, const double* u, const double* v, double alpha,
+                          double* out, cudaStream_t st);
+
 // launch counter (incremented by every launcher)
 extern thread_local int64_t g_launches;
 

@@ -1,0 +1,114 @@
+// Transpose of the CSR matrix (for the adjoint solve A^T x = b) and the pattern gradient used by differentiation.
+//
+// The transpose is built once on the device: column counts, their prefix sum, a counting fill, then a sort of each
+// transposed row by original row index (ties by source position), so the layout -- and hence every sum formed from
+// it -- is deterministic.  The source position of every transposed entry is kept, so new values of A are carried
+// over by a gather without rebuilding the structure.
+#include "kernels.h"
+
+#include <algorithm>
+
+namespace sfg {
+
+__global__ void k_count_cols(int64_t nnz, const int* __restrict__ col, int* __restrict__ counts) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(counts + col[p], 1);
+}
+
+// Exclusive prefix sum of counts[0..len) into out[0..len] (single block).
+__global__ void k_scan_plain(const int* __restrict__ counts, int* __restrict__ out, int len) {
+    __shared__ int sums[1024];
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int chunk = (len + T - 1) / T;
+    const int a = min(len, tid * chunk), bnd = min(len, a + chunk);
+    int local = 0;
+    for (int i = a; i < bnd; ++i) local += counts[i];
+    sums[tid] = local;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        int v = (tid >= off) ? sums[tid - off] : 0;
+        __syncthreads();
+        sums[tid] += v;
+        __syncthreads();
+    }
+    int run = sums[tid] - local;
+    for (int i = a; i < bnd; ++i) {
+        out[i] = run;
+        run += counts[i];
+    }
+    if (tid == T - 1) out[len] = sums[T - 1];
+}
+
+__global__ void k_fill_transpose(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                 const int* __restrict__ rpT, int* __restrict__ cursor, int* __restrict__ colT,
+                                 int* __restrict__ srcT) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    for (int p = rp[r]; p < rp[r + 1]; ++p) {
+        const int c = col[p];
+        const int pos = rpT[c] + atomicAdd(cursor + c, 1);
+        colT[pos] = r;
+        srcT[pos] = p;
+    }
+}
+
+// Insertion sort of each transposed row by (original row, source position); rows are short.
+__global__ void k_sort_rows(int n, const int* __restrict__ rpT, int* __restrict__ colT, int* __restrict__ srcT,
+                            int* __restrict__ maxlen) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int a = rpT[r], e = rpT[r + 1];
+    for (int i = a + 1; i < e; ++i) {
+        const int c = colT[i], sidx = srcT[i];
+        int j = i - 1;
+        while (j >= a && (colT[j] > c || (colT[j] == c && srcT[j] > sidx))) {
+            colT[j + 1] = colT[j];
+            srcT[j + 1] = srcT[j];
+            --j;
+        }
+        colT[j + 1] = c;
+        srcT[j + 1] = sidx;
+    }
+    atomicMax(maxlen, e - a);
+}
+
+__global__ void k_gather_vals(int64_t nnz, const int* __restrict__ src, const double* __restrict__ val,
+                              double* __restrict__ out) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = val[src[q]];
+}
+
+void launch_transpose(int n, int64_t nnz, const int* rp, const int* col, int* counts, int* rpT, int* colT,
+                      int* srcT, int* maxlen, cudaStream_t st) {
+    const int g = (int)std::min<int64_t>((nnz + 255) / 256, 152 * 16);
+    k_count_cols<<<std::max(g, 1), 256, 0, st>>>(nnz, col, counts);
+    k_scan_plain<<<1, 1024, 0, st>>>(counts, rpT, n);
+    cudaMemsetAsync(counts, 0, (size_t)n * sizeof(int), st);
+    k_fill_transpose<<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, rpT, counts, colT, srcT);
+    k_sort_rows<<<(n + 255) / 256, 256, 0, st>>>(n, rpT, colT, srcT, maxlen);
+    g_launches += 4;
+}
+
+void launch_gather_vals(int64_t nnz, const int* src, const double* val, double* out, cudaStream_t st) {
+    const int g = (int)std::min<int64_t>((nnz + 255) / 256, 152 * 16);
+    k_gather_vals<<<std::max(g, 1), 256, 0, st>>>(nnz, src, val, out);
+    ++g_launches;
+}
+
+// out[p] += alpha * u[row(p)] * v[col(p)] over the stored entries (one thread per row, entries in order).
+__global__ void k_pattern_outer(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                const double* __restrict__ u, const double* __restrict__ v, double alpha,
+                                double* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const double ur = alpha * u[r];
+    for (int p = rp[r]; p < rp[r + 1]; ++p) out[p] += ur * v[col[p]];
+}
+
+void launch_pattern_outer(int n, const int* rp, const int* col, const double* u, const double* v, double alpha,
+                          double* out, cudaStream_t st) {
+    k_pattern_outer<<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, u, v, alpha, out);
+    ++g_launches;
+}
+
+}  // namespace sfg

@@ -27,7 +27,8 @@ OPT_PRECISION, OPT_ZETA, OPT_COND_THRESHOLD, OPT_C3, OPT_MAX_OUTER, OPT_SKETCH_K
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SKETCH_KIND = {"sparse_sign": 0, "identity": 1}
 
-EXPORTED = ["sfgmres_create", "sfgmres_set_option", "sfgmres_get_option", "sfgmres_solve", "sfgmres_inner_cycle",
+EXPORTED = ["sfgmres_create", "sfgmres_set_option", "sfgmres_get_option", "sfgmres_solve",
+            "sfgmres_solve_transpose", "sfgmres_update_values", "sfgmres_pattern_outer", "sfgmres_inner_cycle",
             "sfgmres_sketch_apply", "sfgmres_sketch_apply_noalloc", "sfgmres_sketch_pattern", "sfgmres_spmv",
             "sfgmres_destroy", "sfgmres_last_error", "sfgmres_version"]
 
@@ -58,6 +59,9 @@ def load():
     lib.sfgmres_set_option.argtypes = [vp, i32, f64]
     lib.sfgmres_get_option.argtypes = [vp, i32, C.POINTER(f64)]
     lib.sfgmres_solve.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, C.POINTER(Stats)]
+    lib.sfgmres_solve_transpose.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, C.POINTER(Stats)]
+    lib.sfgmres_update_values.argtypes = [vp, vp]
+    lib.sfgmres_pattern_outer.argtypes = [vp, vp, vp, f64, vp]
     lib.sfgmres_inner_cycle.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, C.POINTER(i32), C.POINTER(i32)]
     lib.sfgmres_sketch_apply.argtypes = [vp, i32, vp, vp]
     lib.sfgmres_sketch_apply_noalloc.argtypes = [i64, i32, i32, u64, vp, vp, vp]
@@ -133,6 +137,20 @@ def sfgmres_get_option(h: int, key: int) -> float:
 def sfgmres_solve(h: int, b, x0, x, m: int, s: int, k: int, tol: float, stats: Optional[Stats] = None) -> int:
     return _check(h, load().sfgmres_solve(h, _ptr(b), _ptr(x0), _ptr(x), m, s, k, tol,
                                           C.byref(stats) if stats is not None else None))
+
+
+def sfgmres_solve_transpose(h: int, b, x0, x, m: int, s: int, k: int, tol: float,
+                            stats: Optional[Stats] = None) -> int:
+    return _check(h, load().sfgmres_solve_transpose(h, _ptr(b), _ptr(x0), _ptr(x), m, s, k, tol,
+                                                    C.byref(stats) if stats is not None else None))
+
+
+def sfgmres_update_values(h: int, vals) -> None:
+    _check(h, load().sfgmres_update_values(h, _ptr(vals)), allow_positive=False)
+
+
+def sfgmres_pattern_outer(h: int, u, v, alpha: float, out) -> None:
+    _check(h, load().sfgmres_pattern_outer(h, _ptr(u), _ptr(v), float(alpha), _ptr(out)), allow_positive=False)
 
 
 def sfgmres_inner_cycle(h: int, v, z, m: int, s: int, k: int, basis=None, y=None):
@@ -212,8 +230,10 @@ class Solver:
     def get(self, key: str) -> float:
         return sfgmres_get_option(self.h, self._KEYS[key])
 
-    def solve(self, b, x0=None, *, m: int, s: int, k: int, tol: float = 1e-8, out=None, hist_cap: int = 1000):
-        """Solve ``A x = b``; ``b``/``x0``/``out`` are float64 CUDA tensors or NumPy arrays.  Returns ``(x, info)``."""
+    def solve(self, b, x0=None, *, m: int, s: int, k: int, tol: float = 1e-8, out=None, hist_cap: int = 1000,
+              transpose: bool = False):
+        """Solve ``A x = b`` (``A^T x = b`` with ``transpose``); ``b``/``x0``/``out`` are float64 CUDA tensors or NumPy
+        arrays.  Returns ``(x, info)``."""
         import torch
 
         if out is None:
@@ -228,7 +248,7 @@ class Solver:
         st.inner_reason = C.cast(rh, C.POINTER(C.c_int32))
         st.res_est = C.cast(eh, C.POINTER(C.c_double))
         st.ffom_res = C.cast(fh, C.POINTER(C.c_double))
-        rc = sfgmres_solve(self.h, b, x0, out, m, s, k, tol, st)
+        rc = (sfgmres_solve_transpose if transpose else sfgmres_solve)(self.h, b, x0, out, m, s, k, tol, st)
         J = st.outer_iters
         cnt = min(J + (1 if rc == BREAKDOWN else 0), hist_cap)
         info = {"status": rc, "outer_iters": J, "total_inner": st.total_inner, "rel_res_true": st.rel_res_true,
@@ -239,6 +259,14 @@ class Solver:
                 "t_inner_axpy_ms": st.t_inner_axpy_ms, "n_inner_axpy": st.n_inner_axpy, "t_qr_ms": st.t_qr_ms,
                 "n_qr": st.n_qr}
         return out, info
+
+    def update_values(self, vals) -> None:
+        """Replace the stored values of A (same pattern and order)."""
+        sfgmres_update_values(self.h, vals)
+
+    def pattern_outer(self, u, v, alpha: float, out) -> None:
+        """out[p] += alpha * u[row(p)] * v[col(p)] over the stored entries of A."""
+        sfgmres_pattern_outer(self.h, u, v, alpha, out)
 
     def inner_cycle(self, v, *, m: int, s: int, k: int, basis: bool = True):
         """One sGMRES cycle on the unit CUDA vector ``v``; returns ``(z, k, reason, basis[(m+1), n] or None, y)``."""
