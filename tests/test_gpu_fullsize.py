@@ -1,0 +1,111 @@
+"""GPU parity at the full workload sizes (the sizes bench.py times), in the same launch configuration.
+
+* 3D convection-diffusion 128^3 (n = 2,097,152): first-cycle basis vectors against the oracle's first cycle to 1e-10,
+  the FP64 solve against the oracle's full solve (outer iterations within +-1, both at <= 1e-8 recomputed relative
+  residual, the first outer estimate agreeing to 1e-6), and the FP32-inner and BF16-basis solves reaching 1e-8.
+* Random Zipf matrix, n = 2,000,000 (t = 4, s = 240): first-cycle basis vectors to 1e-10, the first outer step
+  against the oracle's, and FP64 / FP32-inner solves reaching 1e-8 (the residual recomputed on the CPU).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import fgmres as ofg
+from oracle import sgmres as osg
+from oracle import sketch as osk
+
+from gpu_common import dev_vec, need_gpu, rel_err, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _check_first_cycle(sv, A, b, m, s, t, steps):
+    v = b / np.linalg.norm(b)
+    _, k, reason, B, _ = sv.inner_cycle(dev_vec(v), m=steps, s=s, k=t)
+    S = osk.sketch_matrix(A.n, s, 8, 1)
+    ref = osg.sgmres_cycle(A.to_scipy(), v, S, steps, t, record=True)
+    assert (k, reason) == (ref.k, ref.reason)
+    B = B.cpu().numpy()
+    for l in range(len(ref.basis)):
+        assert rel_err(B[l], ref.basis[l]) <= 1e-10, (l, rel_err(B[l], ref.basis[l]))
+
+
+def _rel_res(As, b, x):
+    return float(np.linalg.norm(b - As @ x) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def cd3d():
+    cfg = workloads.CONFIGS["cd3d_128"]
+    A = cfg.build_matrix()
+    return cfg, A, cfg.build_rhs(A.n)
+
+
+def test_cd3d_128_first_cycle(cd3d):
+    from paper_2506_18408_gb300 import Solver
+
+    cfg, A, b = cd3d
+    sv = Solver(A.n, A.row_ptr, A.col, A.val, sketch_seed=cfg.sketch_seed)
+    _check_first_cycle(sv, A, b, cfg.m, cfg.s, cfg.t, steps=12)
+
+
+def test_cd3d_128_fp64_solve_against_oracle(cd3d):
+    from paper_2506_18408_gb300 import Solver
+
+    cfg, A, b = cd3d
+    As = A.to_scipy()
+    sv = Solver(A.n, A.row_ptr, A.col, A.val, sketch_seed=cfg.sketch_seed, max_outer=cfg.max_outer)
+    x, info = sv.solve(dev_vec(b), m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
+    ref = ofg.fgmres(As, b, m=cfg.m, s=cfg.s, t=cfg.t, tol=cfg.tol, max_outer=cfg.max_outer)
+    assert info["status"] == 0 and ref.status == ofg.CONVERGED
+    assert _rel_res(As, b, x.cpu().numpy()) <= cfg.tol and ref.rel_res_true <= cfg.tol
+    assert abs(info["outer_iters"] - ref.outer_iters) <= 1
+    assert abs(info["res_est"][0] - ref.est_hist[0]) <= 1e-6 * ref.est_hist[0]
+    est = info["res_est"]
+    assert all(b2 <= a2 * (1 + 1e-12) for a2, b2 in zip(est, est[1:]))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_cd3d_128_low_precision_inner_reaches_tol(cd3d, prec):
+    from paper_2506_18408_gb300 import Solver
+
+    cfg, A, b = cd3d
+    sv = Solver(A.n, A.row_ptr, A.col, A.val, sketch_seed=cfg.sketch_seed, max_outer=cfg.max_outer, precision=prec)
+    x, info = sv.solve(dev_vec(b), m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
+    assert info["status"] == 0
+    assert _rel_res(A.to_scipy(), b, x.cpu().numpy()) <= cfg.tol
+
+
+@pytest.fixture(scope="module")
+def zipf():
+    cfg = workloads.CONFIGS["zipf_2m"]
+    A = cfg.build_matrix()
+    return cfg, A, cfg.build_rhs(A.n)
+
+
+def test_zipf_2m_first_cycle_and_first_outer_step(zipf):
+    from paper_2506_18408_gb300 import Solver
+
+    cfg, A, b = zipf
+    sv = Solver(A.n, A.row_ptr, A.col, A.val, sketch_seed=cfg.sketch_seed, max_outer=1)
+    _check_first_cycle(sv, A, b, cfg.m, cfg.s, cfg.t, steps=8)
+    _, info = sv.solve(dev_vec(b), m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
+    ref = ofg.fgmres(A.to_scipy(), b, m=cfg.m, s=cfg.s, t=cfg.t, tol=cfg.tol, max_outer=1)
+    assert info["inner_k"][0] == ref.inner_k[0]
+    assert abs(info["res_est"][0] - ref.est_hist[0]) <= 1e-6 * ref.est_hist[0]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_zipf_2m_solve_reaches_tol(zipf, prec):
+    from paper_2506_18408_gb300 import Solver
+
+    cfg, A, b = zipf
+    sv = Solver(A.n, A.row_ptr, A.col, A.val, sketch_seed=cfg.sketch_seed, max_outer=cfg.max_outer, precision=prec)
+    x, info = sv.solve(dev_vec(b), m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
+    assert info["status"] == 0
+    assert _rel_res(A.to_scipy(), b, x.cpu().numpy()) <= cfg.tol
