@@ -63,6 +63,18 @@ extern "C" {
 #define SFGMRES_OPT_SKETCH_KIND 6    /* 0 = sparse-sign (default), 1 = identity (requires s == n; tests) */
 #define SFGMRES_OPT_PROFILE 7        /* 1 = time the kernels with CUDA events (see sfgmres_stats), default 0 */
 #define SFGMRES_OPT_SPMV_VECTOR 8    /* lanes per CSR row in the SpMV (2,4,8,16,32); 0 = chosen from nnz/n */
+#define SFGMRES_OPT_BLOCK_ROWS 9     /* rows per row block of the fused inner kernels: a multiple of 32 in
+                                        [32, 8192], or 0 (default) = chosen by the library (one system: about a
+                                        multiple of the SM count of blocks; several systems: 4096).  Reading it
+                                        returns the size in use. */
+#define SFGMRES_OPT_GRAPH 10         /* 1 (default): each outer step (one inner cycle for every problem and the outer
+                                        FGMRES update) is captured once into a CUDA graph and replayed; the graphs
+                                        are kept while the solve's parameters and workspaces stay the same.  0: the
+                                        kernels are launched one by one.  Results are identical either way.
+                                        SFGMRES_OPT_PROFILE = 1 launches one by one. */
+
+/* ---- sfgmres_solve_batch flags ---------------------------------------------------------------------------- */
+#define SFGMRES_SOLVE_TRANSPOSE 1    /* solve A_q^T x = b for every problem (see sfgmres_solve_transpose) */
 
 /* ---- solve statistics ------------------------------------------------------------------------------------- */
 /* Filled by sfgmres_solve when a non-NULL pointer is passed.  The array members are caller-owned host arrays of
@@ -90,6 +102,20 @@ typedef struct {
     double t_total_ms;       /* device time of the whole solve (first to last kernel) */
 } sfgmres_stats;
 
+/* Filled by sfgmres_solve_batch when a non-NULL pointer is passed.  The arrays are caller-owned host arrays of
+ * length problems = nsys * nrhs (or NULL), indexed by problem p = q * nrhs + r (system q, right-hand side r). */
+typedef struct {
+    int32_t problems;        /* set by the library: nsys * nrhs */
+    int32_t lockstep_outer;  /* outer steps the batch ran (the largest per-problem count) */
+    int64_t total_inner;     /* sum over problems and cycles of the inner basis size k */
+    int32_t* status;         /* per-problem status: SFGMRES_OK, _NOT_CONVERGED, _BREAKDOWN or _ERR_NAN */
+    int32_t* outer_iters;    /* per-problem FGMRES iterations */
+    double* rel_res_true;    /* per-problem recomputed ||b - A x|| / ||b|| */
+    double* rel_res_est;     /* per-problem last Givens estimate */
+    int64_t kernel_launches; /* kernels this call launched */
+    double t_total_ms;       /* device time of the whole solve (first to last kernel) */
+} sfgmres_batch_stats;
+
 typedef struct sfgmres_ctx* sfgmres_t;
 
 /* Create a solver handle for the n x n matrix A given in CSR form (Section 1: A x = b, A large, sparse,
@@ -107,6 +133,20 @@ typedef struct sfgmres_ctx* sfgmres_t;
 SFGMRES_API int sfgmres_create(sfgmres_t* out, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                    const double* vals, uint64_t sketch_seed, int32_t flags, void* stream);
 
+/* Create a handle for a batch of nsys independent systems A_q x = b (q = 0 .. nsys-1) of uneven orders sys_n[q],
+ * given as the block-diagonal matrix diag(A_0, ..., A_{nsys-1}) in one CSR: system q owns rows and columns
+ * off_q .. off_q + sys_n[q] - 1 with off_q = sys_n[0] + ... + sys_n[q-1], and every stored entry of a row must lie
+ * in its system's column range.  Every system is solved independently by the method of sfgmres_solve (its own
+ * inner cycles, outer FGMRES, stop rules and convergence test); the systems share the handle's options and sketch
+ * seed (system q's embedding is the one sfgmres_create would draw for order sys_n[q]).  sfgmres_create(n, ...) is
+ * sfgmres_create_batch(1, &n, ...).
+ *   nsys, sys_n    number of systems >= 1 and their orders (host int64[nsys], each >= 1, sum < 2^31 - 1)
+ *   nnz, row_ptr, col_idx, vals, flags, stream    as for sfgmres_create, for the block-diagonal matrix
+ * Returns SFGMRES_ERR_INVALID_ARG for an entry outside its system's block (in addition to the CSR rules). */
+SFGMRES_API int sfgmres_create_batch(sfgmres_t* out, int32_t nsys, const int64_t* sys_n, int64_t nnz,
+                                     const int64_t* row_ptr, const int32_t* col_idx, const double* vals,
+                                     uint64_t sketch_seed, int32_t flags, void* stream);
+
 /* Set / read an option (SFGMRES_OPT_*).  Values are passed as double.  Unknown keys or out-of-range values return
  * SFGMRES_ERR_INVALID_ARG and leave the option unchanged. */
 SFGMRES_API int sfgmres_set_option(sfgmres_t h, int32_t key, double value);
@@ -122,7 +162,8 @@ SFGMRES_API int sfgmres_get_option(sfgmres_t h, int32_t key, double* value);
  *   st         optional statistics (may be NULL)
  * Special cases: ||b|| = 0 gives x = 0 and SFGMRES_OK; if ||b - A x0|| <= tol ||b|| then x = x0, 0 iterations.
  * The outer loop stops when the Givens estimate meets tol and the recomputed residual confirms it; otherwise it
- * continues until SFGMRES_OPT_MAX_OUTER iterations (SFGMRES_NOT_CONVERGED).  Returns a status code. */
+ * continues until SFGMRES_OPT_MAX_OUTER iterations (SFGMRES_NOT_CONVERGED).  Returns a status code.  The handle
+ * must hold a single system (sfgmres_create); batches use sfgmres_solve_batch. */
 SFGMRES_API int sfgmres_solve(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m, int32_t s, int32_t k,
                   double tol, sfgmres_stats* st);
 
@@ -131,6 +172,23 @@ SFGMRES_API int sfgmres_solve(sfgmres_t h, const double* b, const double* x0, do
  * dL/db = A^{-T} dL/dx.  Arguments, special cases and return values as for sfgmres_solve. */
 SFGMRES_API int sfgmres_solve_transpose(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m,
                                         int32_t s, int32_t k, double tol, sfgmres_stats* st);
+
+/* Solve every system of the handle for nrhs right-hand sides each: P = nsys * nrhs independent problems, all
+ * advanced together (one inner step or one outer step of every unfinished problem per kernel launch; a problem
+ * that has converged, broken down or failed is skipped from then on).
+ *   nrhs       right-hand sides per system, >= 1 (nrhs * n < 2^31 - 1)
+ *   b, x0, x   float64[nrhs * n] in problem order: problem p = q * nrhs + r (system q, right-hand side r) occupies
+ *              the sys_n[q] entries starting at nrhs * off_q + r * sys_n[q].  Device or host pointers; x0 may be
+ *              NULL and may alias x.  x is written on every non-error return.
+ *   m, s, k, tol    as for sfgmres_solve (the same for every problem)
+ *   flags      0, or SFGMRES_SOLVE_TRANSPOSE for A_q^T x = b
+ *   st         optional per-problem statistics (may be NULL)
+ * Returns SFGMRES_ERR_NAN if any problem met a non-finite value (that problem's x is x0; the others are valid),
+ * else SFGMRES_NOT_CONVERGED if any problem did not converge, else SFGMRES_BREAKDOWN if any broke down, else
+ * SFGMRES_OK; the per-problem outcomes are in st->status. */
+SFGMRES_API int sfgmres_solve_batch(sfgmres_t h, int32_t nrhs, const double* b, const double* x0, double* x,
+                                    int32_t m, int32_t s, int32_t k, double tol, int32_t flags,
+                                    sfgmres_batch_stats* st);
 
 /* Replace the stored values of A (same sparsity pattern, same order as at sfgmres_create): vals is float64[nnz],
  * host or device.  The FP32 copy and the transpose's values follow. */
@@ -142,7 +200,7 @@ SFGMRES_API int sfgmres_update_values(sfgmres_t h, const double* vals);
 SFGMRES_API int sfgmres_pattern_outer(sfgmres_t h, const double* u, const double* v, double alpha, double* out);
 
 /* One sGMRES preconditioner application z = B_k y_k ~ A^{-1} v (Eq. 3 with r0 = v, x0 = 0; Section 3), with rules
- * C1 and C2 only (C3 needs an outer iteration).  v must have unit 2-norm (it is the outer Arnoldi vector).
+ * C1 and C2 only (C3 needs an outer iteration).  Single-system handles only.  v must have unit 2-norm (it is the outer Arnoldi vector).
  *   v, z       n float64, device pointers
  *   m, s, k    as for sfgmres_solve
  *   basis      optional device float64[(m+1) * n], column-major: receives the normalised basis vectors b_1..b_kb
@@ -153,14 +211,16 @@ SFGMRES_API int sfgmres_pattern_outer(sfgmres_t h, const double* u, const double
 SFGMRES_API int sfgmres_inner_cycle(sfgmres_t h, const double* v, double* z, int32_t m, int32_t s, int32_t k, double* basis,
                         double* y, int32_t* k_out, int32_t* reason_out);
 
-/* c = S v for the handle's embedding with s rows (Eq. 1).  v: device float64[n], c: device float64[s]. */
+/* c = S v for the handle's embedding with s rows (Eq. 1).  v: device float64[n], c: device float64[s].
+ * Single-system handles only. */
 SFGMRES_API int sfgmres_sketch_apply(sfgmres_t h, int32_t s, const double* v, double* c);
 
 /* The nonzero pattern of S with s rows: for column j and slot l < zeta, rows[j*zeta + l] in [0, s) and
  * signs[j*zeta + l] in {+1, -1} (the value is sign / sqrt(zeta)).  rows: device int32[n*zeta],
  * signs: device int8[n*zeta].  Draw rule (SplitMix64, counter-based): slot q = j*zeta + l draws its row from
  * outputs 128q + 2a (attempt a = 0..63, first row not used by slots 0..l-1 of the column; cyclic probe after 64
- * collisions; row = ((h >> 32) * s) >> 32) and its sign from bit 63 of output 128q + 1. */
+ * collisions; row = ((h >> 32) * s) >> 32) and its sign from bit 63 of output 128q + 1.  Single-system handles
+ * only. */
 SFGMRES_API int sfgmres_sketch_pattern(sfgmres_t h, int32_t s, int32_t* rows, int8_t* signs);
 
 /* c = S v without allocating anything, for callers that cannot call cudaMalloc (code whose device-memory plan is
@@ -183,7 +243,7 @@ SFGMRES_API int sfgmres_sketch_pattern(sfgmres_t h, int32_t s, int32_t* rows, in
 SFGMRES_API int sfgmres_sketch_apply_noalloc(int64_t n, int32_t s, int32_t zeta, uint64_t sketch_seed,
                                              const double* v, double* c, void* stream);
 
-/* y = A x in FP64 (device pointers, n each). */
+/* y = A x in FP64 (device pointers, n each; for a batch handle A is the block-diagonal matrix). */
 SFGMRES_API int sfgmres_spmv(sfgmres_t h, const double* x, double* y);
 
 /* Release the handle and everything it owns.  NULL is accepted. */

@@ -4,13 +4,29 @@ The derivative is implicit (not back-propagation through the iterations): for a 
 lambda = A^{-T} g solves the adjoint system, dL/db = lambda and dL/dA_ij = -lambda_i x_j on the stored entries of A
 only.  Both the forward solves and the adjoint solves run in the CUDA library (sfgmres_solve, sfgmres_solve_transpose
 with the same sketch and parameters), and the pattern gradient is accumulated by sfgmres_pattern_outer.  Several
-right-hand sides (rows of b) are solved one after another with the same handle.
+right-hand sides (rows of b) are solved together as one batch (sfgmres_solve_batch, nrhs = rows of b): every row is
+still its own FGMRES problem with its own stop rules, and gets the result a separate solve would give.
 """
 from __future__ import annotations
 
 import torch
 
 from .sfgmres import BREAKDOWN, NOT_CONVERGED
+
+
+def _solve_rows(solver, B, X, m, s, k, tol, transpose):
+    """X[r] = A^{-1} B[r] (A^{-T} with ``transpose``) for every row, as one batch; raises if a row fails."""
+    what = "adjoint" if transpose else "forward"
+    if B.shape[0] == 1:
+        _, info = solver.solve(B[0], m=m, s=s, k=k, tol=tol, out=X[0], transpose=transpose)
+        if info["status"] in (NOT_CONVERGED, BREAKDOWN):
+            raise RuntimeError(f"sfgmres {what} solve did not converge: {info['rel_res_true']:.3e}")
+        return
+    _, info = solver.solve_batch(B.reshape(-1), nrhs=B.shape[0], m=m, s=s, k=k, tol=tol, out=X.reshape(-1),
+                                 transpose=transpose)
+    for r, st in enumerate(info["status_p"]):
+        if st in (NOT_CONVERGED, BREAKDOWN):
+            raise RuntimeError(f"sfgmres {what} solve {r} did not converge: {info['rel_res_true_p'][r]:.3e}")
 
 
 class SFGMRESSolve(torch.autograd.Function):
@@ -26,10 +42,7 @@ class SFGMRESSolve(torch.autograd.Function):
         solver.update_values(vals.detach().contiguous())
         B = b.detach().reshape(-1, solver.n).contiguous()
         X = torch.empty_like(B)
-        for r in range(B.shape[0]):
-            _, info = solver.solve(B[r], m=m, s=s, k=k, tol=tol, out=X[r])
-            if info["status"] in (NOT_CONVERGED, BREAKDOWN):
-                raise RuntimeError(f"sfgmres forward solve {r} did not converge: {info['rel_res_true']:.3e}")
+        _solve_rows(solver, B, X, m, s, k, tol, transpose=False)
         ctx.solver = solver
         ctx.params = (m, s, k, tol)
         ctx.bshape = b.shape
@@ -44,13 +57,7 @@ class SFGMRESSolve(torch.autograd.Function):
         solver.update_values(vals.detach().contiguous())
         G = gx.reshape(-1, solver.n).contiguous().to(torch.float64)
         Lam = torch.empty_like(G)
-        for r in range(G.shape[0]):
-            if not torch.any(G[r] != 0):
-                Lam[r].zero_()
-                continue
-            _, info = solver.solve(G[r], m=m, s=s, k=k, tol=tol, out=Lam[r], transpose=True)
-            if info["status"] in (NOT_CONVERGED, BREAKDOWN):
-                raise RuntimeError(f"sfgmres adjoint solve {r} did not converge: {info['rel_res_true']:.3e}")
+        _solve_rows(solver, G, Lam, m, s, k, tol, transpose=True)
         gvals = None
         if ctx.needs_input_grad[1]:
             gvals = torch.zeros_like(vals)

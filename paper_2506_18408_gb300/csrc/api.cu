@@ -1,7 +1,10 @@
 // C ABI of the sketched-FGMRES library: handle management, validation, workspaces and the host-side driver loop.
 //
-// The driver enqueues every step on the handle's stream; the device state (CycleState / OuterState) carries the
-// decisions of the stop rules, so the host synchronises once per outer FGMRES step to read the convergence flags.
+// A handle holds Q >= 1 systems as one block-diagonal CSR matrix (sfgmres_create: Q = 1).  A solve with R right-hand
+// sides per system runs the P = Q * R problems (system q, right-hand side r; problem p = q * R + r) in lockstep: every
+// kernel covers all problems and skips the row blocks of problems that are done.  The device state
+// (CycleState / OuterState per problem) carries the decisions of the stop rules, so the host synchronises once per
+// outer FGMRES step to read every problem's convergence flags and to mark the problems to finalise or retire.
 #include "../../include/sfgmres.h"
 #include "kernels.h"
 
@@ -9,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -23,9 +27,24 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+struct HostBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
 struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
 };
+
+// Row-block geometry of a solve with `nrhs` right-hand sides per system (device tables in one allocation).
+struct Geo {
+    int nrhs = -1, ver = -1;
+    int P = 0, N = 0, nblk = 0;
+    DevBuf tab;  // int: blk_v0, blk_len, blk_cs, blk_list, blk_prob [nblk each], prob_b0 [P+1], pflag [P]
+    uint64_t used = 0;
+};
+
+constexpr int kGeoCache = 4;
 
 }  // namespace
 
@@ -35,8 +54,11 @@ void set_global_error(const std::string& msg) { g_create_error = msg; }
 
 struct sfgmres_ctx {
     int dev = 0;
-    int n = 0;
+    int nsys = 1;
+    int n = 0;                  // rows of the block-diagonal matrix (sum over systems)
     int64_t nnz = 0;
+    std::vector<int> sys_n;     // rows of each system
+    std::vector<int> sys_moff;  // first row of each system (nsys + 1 entries)
     int* rp = nullptr;
     int* col = nullptr;
     double* val = nullptr;
@@ -51,21 +73,27 @@ struct sfgmres_ctx {
     uint64_t seed = 0;
     cudaStream_t st = nullptr;
     bool own_stream = false;
-    cudaStream_t qst = nullptr;       // side stream of the sketched-QR cluster kernel
+    cudaStream_t qst = nullptr;       // side stream of the sketched-QR kernel
     cudaEvent_t ev_c = nullptr;       // "sketched column ready" (main -> side)
     cudaEvent_t ev_q = nullptr;       // "cycle's QR updates done" (side -> main)
     int sms = 152;
     int maxlen = 0;                   // longest CSR row
 
     // options
-    int prec = kFP64, zeta = 8, c3 = 1, max_outer = 50, kind = 0, profile = 0, vec_opt = 0;
+    int prec = kFP64, zeta = 8, c3 = 1, max_outer = 50, kind = 0, profile = 0, vec_opt = 0, block_rows = 0;
+    int use_graph = 1;
     double cond_thr = 1e15;
 
-    // geometry
-    int Bn = 0, nblk = 0, vec = 8;
+    // list-block geometry (depends on the systems and the block-rows option; version bumps on change)
+    int Bn = 0, vec = 8, nl = 0, geo_ver = 0;
+    std::vector<int> sys_Bq, sys_l0;
 
-    // sketch gather lists (cached for one (s, zeta, kind))
-    int sk_s = -1, sk_zeta = -1, sk_kind = -1, sk_headroom = 0;
+    // vector-block geometries, cached per number of right-hand sides
+    Geo geos[kGeoCache];
+    uint64_t geo_clock = 0;
+
+    // sketch gather lists (cached for one (s, zeta, kind, geometry version))
+    int sk_s = -1, sk_zeta = -1, sk_kind = -1, sk_ver = -1, sk_headroom = 0;
     int* seg = nullptr;
     uint16_t* ent = nullptr;
 
@@ -75,9 +103,14 @@ struct sfgmres_ctx {
         ost;
     DevBuf bst, xst, x0st;  // staging / internal copies
 
-    // pinned host mirrors of the device state
-    OuterState* h_ost = nullptr;
-    CycleState* h_cyc = nullptr;
+    // pinned host mirrors of the per-problem device state
+    HostBuf h_ost, h_cyc, h_pflag;
+
+    // executable graphs of outer steps j = 0, 1, ... (one inner cycle + one outer FGMRES step each), valid for the
+    // plan they were captured with
+    std::vector<uint64_t> graph_key;
+    std::vector<cudaGraphExec_t> graph_exec;
+    std::vector<int64_t> graph_launches;
 
     // profiling
     std::vector<EventPair> ev_spmv, ev_axpy, ev_qr;
@@ -119,8 +152,29 @@ int ensure(sfgmres_ctx* h, DevBuf& b, size_t bytes) {
     return 0;
 }
 
+int ensure_host(sfgmres_ctx* h, HostBuf& b, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 16);
+    if (b.bytes >= bytes) return 0;
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMallocHost(&b.p, bytes) != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return fail(h, SFGMRES_ERR_OOM, "cudaMallocHost of " + std::to_string(bytes) + " bytes failed");
+    }
+    b.bytes = bytes;
+    return 0;
+}
+
 void release(DevBuf& b) {
     if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+void release_host(HostBuf& b) {
+    if (b.p) cudaFreeHost(b.p);
     b.p = nullptr;
     b.bytes = 0;
 }
@@ -145,8 +199,8 @@ int choose_vec(int64_t nnz, int n, int maxlen) {
     return 32;
 }
 
-// Row blocks: nblk a multiple of the SM count where possible, Bn a multiple of 32 and <= kBlockRowsMax.
-void choose_blocks(int n, int sms, int* Bn, int* nblk) {
+// Row blocks of one system: nblk a multiple of the SM count where possible, Bn a multiple of 32, <= kBlockRowsMax.
+int single_block_rows(int n, int sms) {
     int q = 1, b = 32;
     for (;;) {
         const int64_t per = ((int64_t)n + (int64_t)sms * q - 1) / ((int64_t)sms * q);
@@ -154,14 +208,48 @@ void choose_blocks(int n, int sms, int* Bn, int* nblk) {
         if (b <= kBlockRowsMax) break;
         q *= 2;
     }
-    b = std::max(b, 32);
-    *Bn = b;
-    *nblk = (int)(((int64_t)n + b - 1) / b);
+    return std::max(b, 32);
+}
+
+// Rows per block of a batch of systems (every system is cut into blocks of this size; the last block of a system
+// is ragged).  4096 rows = 8 rows per thread of a 512-thread CTA: enough independent rows per thread to hide the
+// gather latency, and the shared-memory block (32 KiB in FP64) leaves room for two CTAs per SM.
+constexpr int kBatchBlockRows = 4096;
+
+void set_list_geometry(sfgmres_ctx* h) {
+    h->sys_Bq.assign(h->nsys, 0);
+    h->sys_l0.assign(h->nsys + 1, 0);
+    int Bq;
+    if (h->block_rows) Bq = h->block_rows;
+    else if (h->nsys == 1) Bq = single_block_rows(h->n, h->sms);
+    else Bq = kBatchBlockRows;
+    int Bn = 32, nl = 0;
+    for (int q = 0; q < h->nsys; ++q) {
+        const int nq = h->sys_n[q];
+        h->sys_Bq[q] = Bq;
+        h->sys_l0[q] = nl;
+        nl += (nq + Bq - 1) / Bq;
+        Bn = std::max(Bn, std::min(Bq, ((nq + 31) / 32) * 32));
+    }
+    h->sys_l0[h->nsys] = nl;
+    h->nl = nl;
+    h->Bn = Bn;
+    ++h->geo_ver;
+}
+
+int qr_cluster_for(int P) {
+    if (P <= 16) return kQrCluster;
+    if (P <= 32) return 4;
+    if (P <= 64) return 2;
+    return 1;
 }
 
 // ---- CSR validation on the device ----
+// bad[0] |= 1 range, 2 row_ptr[0] != 0, 4 row_ptr[n] != nnz, 8 decreasing, 16 column out of range, 32 column
+// outside the row's system; bad[1] = longest row.
 __global__ void k_validate_csr(int n, int64_t nnz, const int64_t* __restrict__ rp64, const int* __restrict__ col,
-                               int* __restrict__ rp32, int* __restrict__ bad) {
+                               int* __restrict__ rp32, int* __restrict__ bad, const int* __restrict__ moff,
+                               int nsys) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i <= n) {
         const int64_t v = rp64[i];
@@ -170,8 +258,25 @@ __global__ void k_validate_csr(int n, int64_t nnz, const int64_t* __restrict__ r
         if (i == n && v != nnz) atomicOr(bad, 4);
         if (i < n && rp64[i + 1] < v) atomicOr(bad, 8);
         if (i < n) {
-            const int64_t len = rp64[i + 1] - v;
+            const int64_t e = rp64[i + 1];
+            const int64_t len = e - v;
             if (len > 0) atomicMax(bad + 1, (int)min(len, (int64_t)INT32_MAX));
+            if (nsys > 1 && v >= 0 && e <= nnz && v <= e) {
+                int lo = 0, hi = nsys;  // system of row i: moff[lo] <= i < moff[lo + 1]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (moff[mid] <= i) lo = mid;
+                    else hi = mid;
+                }
+                const int c0 = moff[lo], c1 = moff[lo + 1];
+                for (int64_t q = v; q < e; ++q) {
+                    const int c = col[q];
+                    if (c < c0 || c >= c1) {
+                        atomicOr(bad, 32);
+                        break;
+                    }
+                }
+            }
         }
         rp32[i] = (int)v;
     }
@@ -186,14 +291,21 @@ __global__ void k_to_f32(int64_t nnz, const double* __restrict__ v, float* __res
         o[i] = (float)v[i];
 }
 
-__global__ void k_copy(int n, const double* __restrict__ a, double* __restrict__ b) {
+__global__ void k_copy(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = a[i];
 }
 
-__global__ void k_fill(int n, double v, double* __restrict__ b) {
+__global__ void k_fill(int64_t n, double v, double* __restrict__ b) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = v;
+}
+
+// x = 0 over the rows of the problems whose flag has bit 2 set (right-hand side zero).
+__global__ void k_zero_flagged(const Plan P, double* __restrict__ x) {
+    const BlockInfo bi = block_info(P, blockIdx.x);
+    if (!(P.pflag[bi.prob] & 4)) return;
+    for (int k = threadIdx.x; k < bi.len; k += blockDim.x) x[bi.v0 + k] = 0.0;
 }
 
 __global__ void k_neg_to_sign(int64_t cnt, const int8_t* __restrict__ a, int8_t* __restrict__ o) {
@@ -201,37 +313,49 @@ __global__ void k_neg_to_sign(int64_t cnt, const int8_t* __restrict__ a, int8_t*
         o[i] = a[i] ? (int8_t)-1 : (int8_t)1;
 }
 
-int grid_for(int64_t n, int th = 256) { return (int)std::min<int64_t>((n + th - 1) / th, 152 * 16); }
+int grid_for(int64_t n, int th = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + th - 1) / th, 152 * 16)); }
 
+// Gather lists of every system's sketch for s rows (one pattern per system, all drawn from the handle's seed).
 int build_sketch(sfgmres_ctx* h, int s) {
     const int zeta = (h->kind == 1) ? 1 : h->zeta;
-    if (h->seg && h->sk_s == s && h->sk_zeta == zeta && h->sk_kind == h->kind) return 0;
+    if (h->seg && h->sk_s == s && h->sk_zeta == zeta && h->sk_kind == h->kind && h->sk_ver == h->geo_ver) return 0;
     if (h->seg) cudaFree(h->seg);
     if (h->ent) cudaFree(h->ent);
     h->seg = nullptr;
     h->ent = nullptr;
     h->sk_s = -1;
+    int maxn = 0;
+    for (int q = 0; q < h->nsys; ++q) maxn = std::max(maxn, h->sys_n[q]);
     const int64_t tot = (int64_t)h->n * zeta;
-    const int64_t nseg = (int64_t)h->nblk * s + 1;
+    const int64_t nseg = (int64_t)h->nl * s + 1;
     if (nseg > INT32_MAX || tot + 8 * nseg >= INT32_MAX)
         return fail(h, SFGMRES_ERR_INVALID_ARG, "sketch too large for 32-bit gather lists");
     int* rows = nullptr;
     int8_t* neg = nullptr;
     int* counts = nullptr;
-    CK(cudaMalloc(&rows, tot * sizeof(int)));
-    CK(cudaMalloc(&neg, tot));
+    const int64_t tq = (int64_t)maxn * zeta;
+    CK(cudaMalloc(&rows, tq * sizeof(int)));
+    CK(cudaMalloc(&neg, tq));
     CK(cudaMalloc(&counts, nseg * sizeof(int)));
     CK(cudaMalloc(&h->seg, nseg * sizeof(int)));
     CK(cudaMemsetAsync(counts, 0, nseg * sizeof(int), h->st));
-    Plan dummy;
-    launch_sketch_pattern(dummy, h->n, s, zeta, h->kind, h->seed, rows, neg, h->st);
-    launch_sketch_count(h->n, s, zeta, h->Bn, h->nblk, rows, counts, h->seg, h->st);
+    for (int q = 0; q < h->nsys; ++q) {
+        launch_sketch_pattern(h->sys_n[q], s, zeta, h->kind, h->seed, rows, neg, h->st);
+        launch_sketch_count(h->sys_n[q], s, zeta, h->sys_Bq[q], rows, counts + (int64_t)h->sys_l0[q] * s, h->st);
+    }
+    launch_list_scan(counts, h->seg, (int)(nseg - 1), h->st);
     std::vector<int> hs(nseg);
     CK(cudaMemcpyAsync(hs.data(), h->seg, nseg * sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     const int64_t total = hs[nseg - 1];
-    CK(cudaMalloc(&h->ent, (total + 8) * sizeof(uint16_t)));  // +8: room for one padding group
-    launch_sketch_fill(h->n, s, zeta, h->Bn, h->nblk, rows, neg, h->seg, h->ent, total, h->st);
+    // +8: the gather loop may read one 16-byte group past the end of the last list
+    CK(cudaMalloc(&h->ent, (total + 8) * sizeof(uint16_t)));
+    launch_fill_u16(total + 8, (uint16_t)h->Bn, h->ent, h->st);  // padding points at the zero slot
+    for (int q = 0; q < h->nsys; ++q) {
+        launch_sketch_pattern(h->sys_n[q], s, zeta, h->kind, h->seed, rows, neg, h->st);
+        launch_sketch_fill(h->sys_n[q], s, zeta, h->sys_Bq[q], rows, neg, h->seg + (int64_t)h->sys_l0[q] * s,
+                           h->ent, h->st);
+    }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->st));
     cudaFree(rows);
@@ -249,6 +373,59 @@ int build_sketch(sfgmres_ctx* h, int s) {
     h->sk_s = s;
     h->sk_zeta = zeta;
     h->sk_kind = h->kind;
+    h->sk_ver = h->geo_ver;
+    return 0;
+}
+
+// Vector-block geometry for nrhs right-hand sides per system (cached; the least recently used entry is replaced).
+int get_geometry(sfgmres_ctx* h, int nrhs, Geo** out) {
+    Geo* g = nullptr;
+    for (Geo& c : h->geos)
+        if (c.nrhs == nrhs && c.ver == h->geo_ver) g = &c;
+    if (!g) {
+        const int64_t N64 = (int64_t)nrhs * h->n;
+        if (N64 > INT32_MAX - 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "nrhs * n must be below 2^31 - 1");
+        g = &h->geos[0];
+        for (Geo& c : h->geos)
+            if (c.used < g->used) g = &c;
+        const int P = h->nsys * nrhs;
+        std::vector<int> v0, len, cs, lst, prob, pb0(P + 1);
+        for (int q = 0; q < h->nsys; ++q) {
+            const int nq = h->sys_n[q], Bq = h->sys_Bq[q], mo = h->sys_moff[q];
+            const int nlq = (nq + Bq - 1) / Bq;
+            for (int r = 0; r < nrhs; ++r) {
+                const int p = q * nrhs + r;
+                const int pv0 = nrhs * mo + r * nq;
+                pb0[p] = (int)v0.size();
+                for (int k = 0; k < nlq; ++k) {
+                    v0.push_back(pv0 + k * Bq);
+                    len.push_back(std::min(Bq, nq - k * Bq));
+                    cs.push_back(pv0 - mo);
+                    lst.push_back(h->sys_l0[q] + k);
+                    prob.push_back(p);
+                }
+            }
+        }
+        const int nblk = (int)v0.size();
+        pb0[P] = nblk;
+        std::vector<int> tab;
+        tab.reserve((size_t)5 * nblk + 2 * P + 1);
+        for (auto* vv : {&v0, &len, &cs, &lst, &prob}) tab.insert(tab.end(), vv->begin(), vv->end());
+        tab.insert(tab.end(), pb0.begin(), pb0.end());
+        tab.resize(tab.size() + P, 0);  // pflag
+        g->nrhs = -1;
+        int rc = ensure(h, g->tab, tab.size() * sizeof(int));
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(g->tab.p, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        g->nrhs = nrhs;
+        g->ver = h->geo_ver;
+        g->P = P;
+        g->N = (int)N64;
+        g->nblk = nblk;
+    }
+    g->used = ++h->geo_clock;
+    *out = g;
     return 0;
 }
 
@@ -261,7 +438,9 @@ int ensure_f32(sfgmres_ctx* h, bool transpose) {
     return 0;
 }
 
-// A^T in CSR form, built on first use (deterministic layout) and kept; values follow sfgmres_update_values.
+// A^T in CSR form, built on first use (deterministic layout) and kept; values follow sfgmres_update_values.  The
+// transpose of the block-diagonal matrix is block-diagonal with the same blocks, so the row-block geometry and the
+// sketch lists serve both.
 int ensure_transpose(sfgmres_ctx* h) {
     if (h->rpT) return 0;
     const int64_t nz = std::max<int64_t>(h->nnz, 1);
@@ -286,66 +465,94 @@ int ensure_transpose(sfgmres_ctx* h) {
     return 0;
 }
 
-// Allocates the workspaces of a solve and fills a Plan (for A, or for A^T when transpose is set).
-int prepare(sfgmres_ctx* h, int m, int s, int t, int jmax, Plan* p, bool transpose = false) {
-    int rc;
-    if ((rc = build_sketch(h, s))) return rc;
-    if (transpose && (rc = ensure_transpose(h))) return rc;
-    if (h->prec != kFP64 && (rc = ensure_f32(h, transpose))) return rc;
-    const size_t vt = (h->prec == kFP64) ? 8 : (h->prec == kFP32 ? 4 : 2);
-    const size_t at = (h->prec == kFP64) ? 8 : 4;
-    const size_t n = (size_t)h->n;
-    const size_t nb = (size_t)h->nblk;
-    if ((rc = ensure(h, h->U, (size_t)(m + 1) * n * vt))) return rc;
-    if ((rc = ensure(h, h->W, n * at))) return rc;
-    if ((rc = ensure(h, h->sigma, (m + 1) * 8))) return rc;
-    if ((rc = ensure(h, h->normpart, 2 * nb * at))) return rc;
-    if ((rc = ensure(h, h->hpart, nb * kMaxTrunc * at))) return rc;
-    if ((rc = ensure(h, h->cpart, nb * s * at))) return rc;
-    if ((rc = ensure(h, h->C, (size_t)m * s * 8))) return rc;
-    if ((rc = ensure(h, h->Q, (size_t)m * s * 8))) return rc;
-    if ((rc = ensure(h, h->R, (size_t)m * m * 8))) return rc;
-    if ((rc = ensure(h, h->d, m * 8))) return rc;
-    if ((rc = ensure(h, h->e, s * 8))) return rc;
-    if ((rc = ensure(h, h->c0, s * 8))) return rc;
-    if ((rc = ensure(h, h->rho, m * 8))) return rc;
-    if ((rc = ensure(h, h->y, m * 8))) return rc;
-    if ((rc = ensure(h, h->coef, m * 8))) return rc;
-    if ((rc = ensure(h, h->hco, (size_t)m * kMaxTrunc * 8))) return rc;
-    if ((rc = ensure(h, h->cyc, sizeof(CycleState)))) return rc;
-    if (jmax > 0) {
-        const size_t J = (size_t)jmax;
-        if ((rc = ensure(h, h->Vb, (J + 1) * n * 8))) return rc;
-        if ((rc = ensure(h, h->Z, J * n * 8))) return rc;
-        if ((rc = ensure(h, h->nu, (J + 1) * 8))) return rc;
-        if ((rc = ensure(h, h->Wo, n * 8))) return rc;
-        if ((rc = ensure(h, h->opart, nb * (J + 1) * 8))) return rc;
-        if ((rc = ensure(h, h->h1, (J + 1) * 8))) return rc;
-        if ((rc = ensure(h, h->h2, (J + 1) * 8))) return rc;
-        if ((rc = ensure(h, h->H, (J + 1) * J * 8))) return rc;
-        if ((rc = ensure(h, h->cs, J * 8))) return rc;
-        if ((rc = ensure(h, h->sn, J * 8))) return rc;
-        if ((rc = ensure(h, h->g, (J + 1) * 8))) return rc;
-        if ((rc = ensure(h, h->yo, J * 8))) return rc;
-        if ((rc = ensure(h, h->est_hist, J * 8))) return rc;
-        if ((rc = ensure(h, h->ffom_hist, J * 8))) return rc;
-        if ((rc = ensure(h, h->k_hist, J * 4))) return rc;
-        if ((rc = ensure(h, h->reason_hist, J * 4))) return rc;
-    }
-    if ((rc = ensure(h, h->npart, nb * 8))) return rc;
-    if ((rc = ensure(h, h->npart2, nb * 8))) return rc;
-    if ((rc = ensure(h, h->ost, sizeof(OuterState)))) return rc;
-
-    Plan& P = *p;
-    P.n = h->n;
+// Matrix and geometry fields of a Plan (enough for the SpMV and the per-block helpers).
+void plan_geometry(sfgmres_ctx* h, const Geo* g, bool transpose, Plan& P) {
     P.nnz = h->nnz;
     P.rp = transpose ? h->rpT : h->rp;
     P.col = transpose ? h->colT : h->col;
     P.val = transpose ? h->valT : h->val;
     P.val32 = transpose ? h->val32T : h->val32;
     P.vec = transpose ? (h->vec_opt ? h->vec_opt : h->vecT) : h->vec;
+    P.N = g->N;
+    P.P = g->P;
+    P.nblk = g->nblk;
     P.Bn = h->Bn;
-    P.nblk = h->nblk;
+    const int* t = (const int*)g->tab.p;
+    const int nb = g->nblk;
+    P.blk_v0 = t;
+    P.blk_len = t + nb;
+    P.blk_cs = t + 2 * (int64_t)nb;
+    P.blk_list = t + 3 * (int64_t)nb;
+    P.blk_prob = t + 4 * (int64_t)nb;
+    P.prob_b0 = t + 5 * (int64_t)nb;
+    P.pflag = t + 5 * (int64_t)nb + g->P + 1;
+    P.st = h->st;
+}
+
+int* pflag_of(const Geo* g) { return (int*)g->tab.p + 5 * (int64_t)g->nblk + g->P + 1; }
+
+// Allocates the workspaces of a solve with nrhs right-hand sides per system and fills a Plan (for A, or for A^T
+// when transpose is set).  Every problem's flag is reset to "active".
+int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Geo** geo_out, bool transpose = false) {
+    int rc;
+    Geo* g = nullptr;
+    if ((rc = get_geometry(h, nrhs, &g))) return rc;
+    if ((rc = build_sketch(h, s))) return rc;
+    if (transpose && (rc = ensure_transpose(h))) return rc;
+    if (h->prec != kFP64 && (rc = ensure_f32(h, transpose))) return rc;
+    const size_t vt = (h->prec == kFP64) ? 8 : (h->prec == kFP32 ? 4 : 2);
+    const size_t at = (h->prec == kFP64) ? 8 : 4;
+    const size_t N = (size_t)g->N;
+    const size_t nb = (size_t)g->nblk;
+    const size_t Pn = (size_t)g->P;
+    const size_t M = (size_t)m, S = (size_t)s;
+    if ((rc = ensure(h, h->U, (M + 1) * N * vt))) return rc;
+    if ((rc = ensure(h, h->W, N * at))) return rc;
+    if ((rc = ensure(h, h->sigma, Pn * (M + 1) * 8))) return rc;
+    if ((rc = ensure(h, h->normpart, 2 * nb * at))) return rc;
+    if ((rc = ensure(h, h->hpart, nb * kMaxTrunc * at))) return rc;
+    if ((rc = ensure(h, h->cpart, nb * S * at))) return rc;
+    if ((rc = ensure(h, h->C, Pn * M * S * 8))) return rc;
+    if ((rc = ensure(h, h->Q, Pn * M * S * 8))) return rc;
+    if ((rc = ensure(h, h->R, Pn * M * M * 8))) return rc;
+    if ((rc = ensure(h, h->d, Pn * M * 8))) return rc;
+    if ((rc = ensure(h, h->e, Pn * S * 8))) return rc;
+    if ((rc = ensure(h, h->c0, Pn * S * 8))) return rc;
+    if ((rc = ensure(h, h->rho, Pn * M * 8))) return rc;
+    if ((rc = ensure(h, h->y, Pn * M * 8))) return rc;
+    if ((rc = ensure(h, h->coef, Pn * M * 8))) return rc;
+    if ((rc = ensure(h, h->hco, Pn * M * kMaxTrunc * 8))) return rc;
+    if ((rc = ensure(h, h->cyc, Pn * sizeof(CycleState)))) return rc;
+    if (jmax > 0) {
+        const size_t J = (size_t)jmax;
+        if ((rc = ensure(h, h->Vb, (J + 1) * N * 8))) return rc;
+        if ((rc = ensure(h, h->Z, J * N * 8))) return rc;
+        if ((rc = ensure(h, h->nu, Pn * (J + 1) * 8))) return rc;
+        if ((rc = ensure(h, h->Wo, N * 8))) return rc;
+        if ((rc = ensure(h, h->opart, nb * (J + 1) * 8))) return rc;
+        if ((rc = ensure(h, h->h1, Pn * (J + 1) * 8))) return rc;
+        if ((rc = ensure(h, h->h2, Pn * (J + 1) * 8))) return rc;
+        if ((rc = ensure(h, h->H, Pn * (J + 1) * J * 8))) return rc;
+        if ((rc = ensure(h, h->cs, Pn * J * 8))) return rc;
+        if ((rc = ensure(h, h->sn, Pn * J * 8))) return rc;
+        if ((rc = ensure(h, h->g, Pn * (J + 1) * 8))) return rc;
+        if ((rc = ensure(h, h->yo, Pn * J * 8))) return rc;
+        if ((rc = ensure(h, h->est_hist, Pn * J * 8))) return rc;
+        if ((rc = ensure(h, h->ffom_hist, Pn * J * 8))) return rc;
+        if ((rc = ensure(h, h->k_hist, Pn * J * 4))) return rc;
+        if ((rc = ensure(h, h->reason_hist, Pn * J * 4))) return rc;
+    }
+    if ((rc = ensure(h, h->npart, nb * 8))) return rc;
+    if ((rc = ensure(h, h->npart2, nb * 8))) return rc;
+    if ((rc = ensure(h, h->ost, Pn * sizeof(OuterState)))) return rc;
+    if ((rc = ensure_host(h, h->h_ost, Pn * sizeof(OuterState)))) return rc;
+    if ((rc = ensure_host(h, h->h_cyc, Pn * sizeof(CycleState)))) return rc;
+    if ((rc = ensure_host(h, h->h_pflag, Pn * sizeof(int)))) return rc;
+    std::memset(h->h_pflag.p, 0, Pn * sizeof(int));
+    CK(cudaMemsetAsync(pflag_of(g), 0, Pn * sizeof(int), h->st));
+
+    Plan& P = *p;
+    plan_geometry(h, g, transpose, P);
     P.s = s;
     P.zeta = h->sk_zeta;
     P.kind = h->kind;
@@ -373,6 +580,7 @@ int prepare(sfgmres_ctx* h, int m, int s, int t, int jmax, Plan* p, bool transpo
     P.coef = (double*)h->coef.p;
     P.hco = (double*)h->hco.p;
     P.cyc = (CycleState*)h->cyc.p;
+    P.qr_cluster = qr_cluster_for(g->P);
     P.jmax = jmax;
     P.Vb = (double*)h->Vb.p;
     P.Z = (double*)h->Z.p;
@@ -393,7 +601,7 @@ int prepare(sfgmres_ctx* h, int m, int s, int t, int jmax, Plan* p, bool transpo
     P.k_hist = (int*)h->k_hist.p;
     P.reason_hist = (int*)h->reason_hist.p;
     P.ost = (OuterState*)h->ost.p;
-    P.st = h->st;
+    if (geo_out) *geo_out = g;
     return 0;
 }
 
@@ -401,6 +609,7 @@ int check_params(sfgmres_ctx* h, int m, int s, int t) {
     if (m < 1 || m > kMaxM) return fail(h, SFGMRES_ERR_INVALID_ARG, "m must be in [1, 1024]");
     if (t < 0 || t > kMaxTrunc) return fail(h, SFGMRES_ERR_INVALID_ARG, "k (truncation) must be in [0, 8]");
     if (h->kind == 1) {
+        if (h->nsys != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "identity sketch needs a single-system handle");
         if (s != h->n) return fail(h, SFGMRES_ERR_INVALID_ARG, "identity sketch needs s == n");
         if (s > kMaxS) return fail(h, SFGMRES_ERR_INVALID_ARG, "identity sketch needs n <= 4096");
     } else {
@@ -432,11 +641,13 @@ double ev_sum(const std::vector<EventPair>& pool, size_t count) {
     return tot;
 }
 
-// One inner cycle (Section 3) on u_0 = vscale * v; j >= 0 inside a solve (C3 as configured), j < 0 standalone.
-// The sketched-QR update of step i runs on the side stream after step i's sketch column is ready, overlapping the
-// next step's SpMV; the main stream waits for the last QR update before the least-squares solve.
-int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const double* vscale, int c3, double* z) {
-    launch_cycle_start(P, j, v, vscale, c3, h->cond_thr);
+// One inner cycle (Section 3) for every active problem on u_0 = vscale_p * v; j >= 0 inside a solve (C3 as
+// configured), j < 0 standalone.  The sketched-QR update of step i runs on the side stream after step i's sketch
+// column is ready, overlapping the next step's SpMV; the main stream waits for the last QR update before the
+// least-squares solve.
+int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const double* vscale, int vstride, int c3,
+              double* z) {
+    launch_cycle_start(P, j, v, vscale, vstride, c3, h->cond_thr);
     for (int i = 0; i < P.m; ++i) {
         const bool last = (i == P.m - 1);
         if (h->profile) ev_begin(h, h->ev_spmv, h->n_spmv, h->st);
@@ -457,28 +668,357 @@ int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const doubl
     return 0;
 }
 
+// Everything a captured outer step depends on: the plan's pointers and sizes and the cycle options.
+std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
+    std::vector<uint64_t> k;
+    auto u = [&](const void* p) { k.push_back((uint64_t)(uintptr_t)p); };
+    for (const void* p : std::initializer_list<const void*>{(const void*)P.rp, (const void*)P.col, (const void*)P.val, (const void*)P.val32,
+                          (const void*)P.blk_v0, (const void*)P.seg, (const void*)P.ent, P.U, P.W,
+                          (const void*)P.sigma, P.normpart, P.hpart, P.cpart, (const void*)P.C, (const void*)P.Q,
+                          (const void*)P.R, (const void*)P.d, (const void*)P.e, (const void*)P.c0,
+                          (const void*)P.rho, (const void*)P.y, (const void*)P.coef, (const void*)P.hco,
+                          (const void*)P.cyc, (const void*)P.Vb, (const void*)P.Z, (const void*)P.nu,
+                          (const void*)P.Wo, (const void*)P.opart, (const void*)P.npart, (const void*)P.npart2,
+                          (const void*)P.h1, (const void*)P.h2, (const void*)P.H, (const void*)P.cs,
+                          (const void*)P.sn, (const void*)P.g, (const void*)P.yo, (const void*)P.est_hist,
+                          (const void*)P.ffom_hist, (const void*)P.k_hist, (const void*)P.reason_hist,
+                          (const void*)P.ost, (const void*)P.st, (const void*)h->qst})
+        u(p);
+    for (int64_t v : std::initializer_list<int64_t>{(int64_t)P.nnz, (int64_t)P.vec, (int64_t)P.N, (int64_t)P.P, (int64_t)P.nblk, (int64_t)P.Bn,
+                      (int64_t)P.s, (int64_t)P.zeta, (int64_t)P.kind, (int64_t)P.sk_headroom, (int64_t)P.prec,
+                      (int64_t)P.m, (int64_t)P.t, (int64_t)P.qr_cluster, (int64_t)P.jmax, (int64_t)h->c3})
+        k.push_back((uint64_t)v);
+    uint64_t bits;
+    std::memcpy(&bits, &P.sk_scale, 8);
+    k.push_back(bits);
+    std::memcpy(&bits, &h->cond_thr, 8);
+    k.push_back(bits);
+    return k;
+}
+
+void drop_graphs(sfgmres_ctx* h) {
+    for (cudaGraphExec_t g : h->graph_exec)
+        if (g) cudaGraphExecDestroy(g);
+    h->graph_exec.clear();
+    h->graph_launches.clear();
+    h->graph_key.clear();
+}
+
+// One outer step j (inner cycle j and the outer FGMRES update) for every active problem.  With graphs on, the step
+// is captured from the handle's streams once per plan and j, then replayed as a single graph launch.
+int outer_step(sfgmres_ctx* h, const Plan& P, int j) {
+    auto enqueue = [&]() -> int {
+        int rc = run_cycle(h, P, j, P.Vb + (int64_t)j * P.N, P.nu + j, P.jmax + 1, h->c3, P.Z + (int64_t)j * P.N);
+        if (rc) return rc;
+        launch_outer_step(P, j);
+        return 0;
+    };
+    if (!h->use_graph || h->profile) return enqueue();
+    std::vector<uint64_t> key = plan_key(h, P);
+    if (key != h->graph_key) {
+        drop_graphs(h);
+        h->graph_key = key;
+    }
+    if ((int)h->graph_exec.size() <= j) {
+        h->graph_exec.resize(j + 1, nullptr);
+        h->graph_launches.resize(j + 1, 0);
+    }
+    if (!h->graph_exec[j]) {
+        const int64_t l0 = g_launches;
+        CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
+        int rc = enqueue();
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->st, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        CK(e);
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        h->graph_exec[j] = ex;
+        h->graph_launches[j] = g_launches - l0;
+        g_launches = l0;
+    }
+    CK(cudaGraphLaunch(h->graph_exec[j], h->st));
+    g_launches += h->graph_launches[j];
+    return 0;
+}
+
+// Per-problem outcome of a solve.
+struct ProbOut {
+    int status = SFGMRES_NOT_CONVERGED;
+    int outer = 0;
+    double rel_true = 0.0, rel_est = 0.0;
+    bool done = false, brk = false, nan_init = false;
+};
+
+struct SolveOut {
+    std::vector<ProbOut> pr;
+    int jmax = 0;
+    Plan P;
+};
+
+int status_of(const std::vector<ProbOut>& pr) {
+    bool nc = false, brk = false, nan = false;
+    for (const ProbOut& o : pr) {
+        nan |= (o.status == SFGMRES_ERR_NAN);
+        nc |= (o.status == SFGMRES_NOT_CONVERGED);
+        brk |= (o.status == SFGMRES_BREAKDOWN);
+    }
+    if (nan) return SFGMRES_ERR_NAN;
+    if (nc) return SFGMRES_NOT_CONVERGED;
+    if (brk) return SFGMRES_BREAKDOWN;
+    return SFGMRES_OK;
+}
+
+// The solve of every problem of the batch: b, x0, x hold nrhs * n values in problem order.
+int solve_core(sfgmres_t h, bool transpose, int nrhs, const double* b, const double* x0, double* x, int m, int s,
+               int k, double tol, SolveOut* so) {
+    const int jmax = h->max_outer;
+    Plan P;
+    Geo* g = nullptr;
+    int rc;
+    if ((rc = prepare(h, nrhs, m, s, k, jmax, &P, &g, transpose))) return rc;
+    const int NP = P.P;
+    const size_t nbytes = (size_t)P.N * sizeof(double);
+    if ((rc = ensure(h, h->bst, nbytes))) return rc;
+    if ((rc = ensure(h, h->xst, nbytes))) return rc;
+    if ((rc = ensure(h, h->x0st, nbytes))) return rc;
+    double* db = (double*)h->bst.p;
+    double* dx = (double*)h->xst.p;
+    double* dx0 = (double*)h->x0st.p;
+    int* hflag = (int*)h->h_pflag.p;
+    int* dflag = pflag_of(g);
+    OuterState* host_ost = (OuterState*)h->h_ost.p;
+    const bool x_dev = is_device_ptr(x);
+    h->n_spmv = h->n_axpy = h->n_qr = 0;
+    CK(cudaEventRecord(h->ev_t0, h->st));
+    // private copies of b and x0 (x may alias x0, and host inputs are staged)
+    CK(cudaMemcpyAsync(db, b, nbytes, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    if (x0) {
+        CK(cudaMemcpyAsync(dx0, x0, nbytes, is_device_ptr(x0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           h->st));
+    }
+    const double* px0 = x0 ? dx0 : nullptr;
+    // every problem's iterate starts at x0; finalisation overwrites the problems it covers
+    if (x0) k_copy<<<grid_for(P.N), 256, 0, h->st>>>(P.N, dx0, dx);
+    else k_fill<<<grid_for(P.N), 256, 0, h->st>>>(P.N, 0.0, dx);
+    ++g_launches;
+    // r0 = b - A x0 into v_0; beta, ||b||
+    launch_residual(P, db, px0, P.Vb, false);
+    launch_init_state(P, tol);
+    CK(cudaMemcpyAsync(host_ost, P.ost, NP * sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    so->pr.assign(NP, ProbOut());
+    so->jmax = jmax;
+    std::vector<ProbOut>& pr = so->pr;
+    int active = 0;
+    bool any_zero = false;
+    for (int p = 0; p < NP; ++p) {
+        const OuterState& os = host_ost[p];
+        ProbOut& o = pr[p];
+        if (!std::isfinite(os.beta) || !std::isfinite(os.bnorm) || os.nan) {
+            o.status = SFGMRES_ERR_NAN;
+            o.nan_init = true;
+            o.done = true;
+        } else if (os.bnorm == 0.0) {  // x = 0
+            o.status = SFGMRES_OK;
+            o.done = true;
+            hflag[p] |= 4;
+            any_zero = true;
+        } else if (os.beta <= os.tol_abs) {  // x0 already meets the tolerance
+            o.status = SFGMRES_OK;
+            o.done = true;
+            o.rel_true = o.rel_est = os.beta / os.bnorm;
+        } else {
+            ++active;
+        }
+        if (o.done) hflag[p] |= 1;
+    }
+    if (active < NP) {
+        CK(cudaMemcpyAsync(dflag, hflag, NP * sizeof(int), cudaMemcpyHostToDevice, h->st));
+        if (any_zero) {
+            k_zero_flagged<<<P.nblk, 256, 0, h->st>>>(P, dx);
+            ++g_launches;
+        }
+    }
+    std::vector<int> fin;
+    for (int j = 0; j < jmax && active > 0; ++j) {
+        if ((rc = outer_step(h, P, j))) return rc;
+        CK(cudaMemcpyAsync(host_ost, P.ost, NP * sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        CK(cudaGetLastError());
+        const bool last = (j + 1 == jmax);
+        fin.clear();
+        bool changed = false;
+        for (int p = 0; p < NP; ++p) {
+            ProbOut& o = pr[p];
+            if (o.done) continue;
+            const OuterState& os = host_ost[p];
+            if (os.nan) {
+                o.status = SFGMRES_ERR_NAN;
+                o.done = true;
+                hflag[p] |= 1;
+                changed = true;
+                --active;
+                continue;
+            }
+            if (os.breakdown == 2) {  // the inner cycle accepted no column: keep the iterate of step j
+                o.brk = true;
+                o.outer = j;
+                fin.push_back(p);
+                continue;
+            }
+            o.outer = j + 1;
+            o.rel_est = os.est / os.bnorm;
+            if (os.conv_est || os.breakdown == 1 || last) fin.push_back(p);
+        }
+        if (!fin.empty()) {
+            for (int p : fin) hflag[p] |= 2;
+            CK(cudaMemcpyAsync(dflag, hflag, NP * sizeof(int), cudaMemcpyHostToDevice, h->st));
+            launch_final_x(P, jmax, px0, dx);
+            launch_residual(P, db, dx, nullptr, true);
+            launch_true_residual_reduce(P);
+            CK(cudaMemcpyAsync(host_ost, P.ost, NP * sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
+            CK(cudaStreamSynchronize(h->st));
+            CK(cudaGetLastError());
+            for (int p : fin) {
+                ProbOut& o = pr[p];
+                const OuterState& os = host_ost[p];
+                o.rel_true = std::sqrt(os.true_res2) / os.bnorm;
+                hflag[p] &= ~2;
+                if (o.brk) o.status = SFGMRES_BREAKDOWN;
+                else if (o.rel_true <= tol || os.breakdown == 1) o.status = SFGMRES_OK;
+                else if (last) o.status = SFGMRES_NOT_CONVERGED;
+                else continue;
+                o.done = true;
+                hflag[p] |= 1;
+                --active;
+            }
+            changed = true;
+        }
+        if (changed) CK(cudaMemcpyAsync(dflag, hflag, NP * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    }
+    CK(cudaMemcpyAsync(x, dx, nbytes, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    CK(cudaEventRecord(h->ev_t1, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    so->P = P;
+    return 0;
+}
+
+int check_solve_args(sfgmres_t h, const double* b, double* x, int m, int s, int k, double tol) {
+    if (!b || !x) return fail(h, SFGMRES_ERR_INVALID_ARG, "b and x must not be NULL");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(h, SFGMRES_ERR_INVALID_ARG, "tol must be in (0, 1)");
+    return check_params(h, m, s, k);
+}
+
+int solve_single(sfgmres_t h, bool transpose, const double* b, const double* x0, double* x, int32_t m, int32_t s,
+                 int32_t k, double tol, sfgmres_stats* st) {
+    if (!h) return SFGMRES_ERR_INVALID_ARG;
+    if (h->nsys != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "this handle holds several systems: use sfgmres_solve_batch");
+    int rc = check_solve_args(h, b, x, m, s, k, tol);
+    if (rc) return rc;
+    CK(cudaSetDevice(h->dev));
+    const int64_t launches0 = g_launches;
+    SolveOut so;
+    if ((rc = solve_core(h, transpose, 1, b, x0, x, m, s, k, tol, &so))) return rc;
+    const ProbOut& o = so.pr[0];
+    const int status = o.status;
+    if (status == SFGMRES_ERR_NAN) {
+        return fail(h, SFGMRES_ERR_NAN, o.nan_init ? "non-finite value in b or x0 (or in A x0)"
+                                                   : "non-finite value during the iteration");
+    }
+    if (st) {
+        const Plan& P = so.P;
+        const int jmax = so.jmax;
+        st->status = status;
+        st->outer_iters = o.outer;
+        st->rel_res_true = o.rel_true;
+        st->rel_res_est = o.rel_est;
+        const int cnt = std::min(o.outer + (status == SFGMRES_BREAKDOWN ? 1 : 0), jmax);
+        std::vector<int> kh(std::max(cnt, 1)), rh(std::max(cnt, 1));
+        std::vector<double> eh(std::max(cnt, 1)), fh(std::max(cnt, 1));
+        if (cnt > 0) {
+            CK(cudaMemcpy(kh.data(), P.k_hist, cnt * sizeof(int), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(rh.data(), P.reason_hist, cnt * sizeof(int), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(eh.data(), P.est_hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(fh.data(), P.ffom_hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+        int tot = 0;
+        for (int q = 0; q < cnt; ++q) tot += kh[q];
+        st->total_inner = tot;
+        const int cap = std::min(cnt, st->hist_cap);
+        for (int q = 0; q < cap; ++q) {
+            if (st->inner_k) st->inner_k[q] = kh[q];
+            if (st->inner_reason) st->inner_reason[q] = rh[q];
+            if (st->res_est && q < o.outer) st->res_est[q] = eh[q];
+            if (st->ffom_res && q < o.outer) st->ffom_res[q] = fh[q];
+        }
+        st->kernel_launches = g_launches - launches0;
+        float tms = 0.f;
+        cudaEventElapsedTime(&tms, h->ev_t0, h->ev_t1);
+        st->t_total_ms = tms;
+        if (h->profile) {
+            st->t_inner_spmv_ms = ev_sum(h->ev_spmv, h->n_spmv);
+            st->n_inner_spmv = (int64_t)h->n_spmv;
+            st->t_inner_axpy_ms = ev_sum(h->ev_axpy, h->n_axpy);
+            st->n_inner_axpy = (int64_t)h->n_axpy;
+            st->t_qr_ms = ev_sum(h->ev_qr, h->n_qr);
+            st->n_qr = (int64_t)h->n_qr;
+        } else {
+            st->t_inner_spmv_ms = st->t_inner_axpy_ms = st->t_qr_ms = 0.0;
+            st->n_inner_spmv = st->n_inner_axpy = st->n_qr = 0;
+        }
+    }
+    return status;
+}
+
 }  // namespace
 
 // =====================================================================================================================
 extern "C" {
 
-const char* sfgmres_version(void) { return "sfgmres-gb300 0.1 (sm_103a)"; }
+const char* sfgmres_version(void) { return "sfgmres-gb300 0.2 (sm_103a)"; }
 
 const char* sfgmres_last_error(sfgmres_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
-int sfgmres_create(sfgmres_t* out, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
-                   const double* vals, uint64_t sketch_seed, int32_t flags, void* stream) {
+int sfgmres_create_batch(sfgmres_t* out, int32_t nsys, const int64_t* sys_n, int64_t nnz, const int64_t* row_ptr,
+                         const int32_t* col_idx, const double* vals, uint64_t sketch_seed, int32_t flags,
+                         void* stream) {
     sfgmres_ctx* h = nullptr;
     if (!out) return fail(nullptr, SFGMRES_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (n < 1 || n > INT32_MAX - 1) return fail(nullptr, SFGMRES_ERR_INVALID_ARG, "n must be in [1, 2^31-2]");
+    if (nsys < 1 || !sys_n) return fail(nullptr, SFGMRES_ERR_INVALID_ARG, "nsys must be >= 1 and sys_n not NULL");
+    int64_t n = 0;
+    for (int q = 0; q < nsys; ++q) {
+        if (sys_n[q] < 1) return fail(nullptr, SFGMRES_ERR_INVALID_ARG, "every system needs at least one row");
+        n += sys_n[q];
+        if (n > INT32_MAX - 1) return fail(nullptr, SFGMRES_ERR_INVALID_ARG, "total rows must be below 2^31 - 1");
+    }
     if (nnz < 0 || nnz > INT32_MAX) return fail(nullptr, SFGMRES_ERR_INVALID_ARG, "nnz must be in [0, 2^31-1]");
     if (!row_ptr || (nnz > 0 && (!col_idx || !vals)))
         return fail(nullptr, SFGMRES_ERR_INVALID_ARG, "NULL CSR array");
     h = new sfgmres_ctx();
+    h->nsys = nsys;
     h->n = (int)n;
     h->nnz = nnz;
     h->seed = sketch_seed;
+    h->sys_n.resize(nsys);
+    h->sys_moff.resize(nsys + 1);
+    {
+        int off = 0;
+        for (int q = 0; q < nsys; ++q) {
+            h->sys_n[q] = (int)sys_n[q];
+            h->sys_moff[q] = off;
+            off += (int)sys_n[q];
+        }
+        h->sys_moff[nsys] = off;
+    }
     cudaError_t ce = cudaGetDevice(&h->dev);
     if (ce != cudaSuccess) {
         delete h;
@@ -499,13 +1039,16 @@ int sfgmres_create(sfgmres_t* out, int64_t n, int64_t nnz, const int64_t* row_pt
     const bool host = (flags & SFGMRES_CSR_HOST) != 0;
     int64_t* rp64 = nullptr;
     int* bad = nullptr;
+    int* dmoff = nullptr;
     if (cudaMalloc(&h->rp, (n + 1) * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&h->col, std::max<int64_t>(nnz, 1) * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&h->val, std::max<int64_t>(nnz, 1) * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&rp64, (n + 1) * sizeof(int64_t)) != cudaSuccess || cudaMalloc(&bad, 2 * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&rp64, (n + 1) * sizeof(int64_t)) != cudaSuccess || cudaMalloc(&bad, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&dmoff, (nsys + 1) * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         if (rp64) cudaFree(rp64);
         if (bad) cudaFree(bad);
+        if (dmoff) cudaFree(dmoff);
         return bail(SFGMRES_ERR_OOM, "out of device memory for the CSR copy");
     }
     const cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -514,30 +1057,28 @@ int sfgmres_create(sfgmres_t* out, int64_t n, int64_t nnz, const int64_t* row_pt
         cudaMemcpyAsync(h->col, col_idx, nnz * sizeof(int), kind, h->st);
         cudaMemcpyAsync(h->val, vals, nnz * sizeof(double), kind, h->st);
     }
+    cudaMemcpyAsync(dmoff, h->sys_moff.data(), (nsys + 1) * sizeof(int), cudaMemcpyHostToDevice, h->st);
     cudaMemsetAsync(bad, 0, 2 * sizeof(int), h->st);
     const int64_t cover = std::max<int64_t>(n + 1, nnz);
-    k_validate_csr<<<(int)((cover + 255) / 256), 256, 0, h->st>>>((int)n, nnz, rp64, h->col, h->rp, bad);
+    k_validate_csr<<<(int)((cover + 255) / 256), 256, 0, h->st>>>((int)n, nnz, rp64, h->col, h->rp, bad, dmoff,
+                                                                  nsys);
     int hbad2[2] = {0, 0};
     cudaMemcpyAsync(hbad2, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st);
     ce = cudaStreamSynchronize(h->st);
     cudaFree(rp64);
     cudaFree(bad);
+    cudaFree(dmoff);
     if (ce != cudaSuccess) return bail(SFGMRES_ERR_CUDA, std::string("CSR upload: ") + cudaGetErrorString(ce));
     const int hbad = hbad2[0];
     h->maxlen = hbad2[1];
     if (hbad) {
-        char buf[160];
+        char buf[200];
         snprintf(buf, sizeof buf, "invalid CSR (code %d: 1 range, 2 row_ptr[0]!=0, 4 row_ptr[n]!=nnz, "
-                 "8 decreasing row_ptr, 16 column out of range)", hbad);
+                 "8 decreasing row_ptr, 16 column out of range, 32 column outside the row's system)", hbad);
         return bail(SFGMRES_ERR_INVALID_ARG, buf);
     }
-    choose_blocks(h->n, h->sms, &h->Bn, &h->nblk);
+    set_list_geometry(h);
     h->vec = choose_vec(nnz, h->n, h->maxlen);
-    if (cudaMallocHost(&h->h_ost, sizeof(OuterState)) != cudaSuccess ||
-        cudaMallocHost(&h->h_cyc, sizeof(CycleState)) != cudaSuccess) {
-        cudaGetLastError();
-        return bail(SFGMRES_ERR_OOM, "cudaMallocHost failed");
-    }
     cudaEventCreate(&h->ev_t0);
     cudaEventCreate(&h->ev_t1);
     int lo_prio = 0, hi_prio = 0;
@@ -550,6 +1091,13 @@ int sfgmres_create(sfgmres_t* out, int64_t n, int64_t nnz, const int64_t* row_pt
     }
     *out = h;
     return SFGMRES_OK;
+}
+
+int sfgmres_create(sfgmres_t* out, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                   const double* vals, uint64_t sketch_seed, int32_t flags, void* stream) {
+    if (out) *out = nullptr;
+    if (n < 1 || n > INT32_MAX - 1) return fail(nullptr, SFGMRES_ERR_INVALID_ARG, "n must be in [1, 2^31-2]");
+    return sfgmres_create_batch(out, 1, &n, nnz, row_ptr, col_idx, vals, sketch_seed, flags, stream);
 }
 
 int sfgmres_destroy(sfgmres_t h) {
@@ -569,8 +1117,11 @@ int sfgmres_destroy(sfgmres_t h) {
                       &h->est_hist, &h->ffom_hist, &h->k_hist, &h->reason_hist, &h->ost, &h->bst, &h->xst,
                       &h->x0st};
     for (DevBuf* b : bufs) release(*b);
-    if (h->h_ost) cudaFreeHost(h->h_ost);
-    if (h->h_cyc) cudaFreeHost(h->h_cyc);
+    for (Geo& g : h->geos) release(g.tab);
+    drop_graphs(h);
+    release_host(h->h_ost);
+    release_host(h->h_cyc);
+    release_host(h->h_pflag);
     for (auto* pool : {&h->ev_spmv, &h->ev_axpy, &h->ev_qr})
         for (auto& e : *pool) {
             cudaEventDestroy(e.a);
@@ -627,6 +1178,18 @@ int sfgmres_set_option(sfgmres_t h, int32_t key, double v) {
             h->vec_opt = iv;
             h->vec = iv ? iv : choose_vec(h->nnz, h->n, h->maxlen);
             return 0;
+        case SFGMRES_OPT_GRAPH:
+            if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "graph must be 0 or 1");
+            h->use_graph = iv;
+            return 0;
+        case SFGMRES_OPT_BLOCK_ROWS:
+            if (iv != v || !(iv == 0 || (iv >= 32 && iv <= kBlockRowsMax && iv % 32 == 0)))
+                return fail(h, SFGMRES_ERR_INVALID_ARG, "block rows must be 0 or a multiple of 32 in [32, 8192]");
+            if (iv != h->block_rows) {
+                h->block_rows = iv;
+                set_list_geometry(h);
+            }
+            return 0;
         default:
             return fail(h, SFGMRES_ERR_INVALID_ARG, "unknown option key");
     }
@@ -643,169 +1206,68 @@ int sfgmres_get_option(sfgmres_t h, int32_t key, double* v) {
         case SFGMRES_OPT_SKETCH_KIND: *v = h->kind; return 0;
         case SFGMRES_OPT_PROFILE: *v = h->profile; return 0;
         case SFGMRES_OPT_SPMV_VECTOR: *v = h->vec; return 0;
+        case SFGMRES_OPT_BLOCK_ROWS: *v = h->sys_Bq.empty() ? 0 : h->sys_Bq[0]; return 0;
+        case SFGMRES_OPT_GRAPH: *v = h->use_graph; return 0;
         default: return fail(h, SFGMRES_ERR_INVALID_ARG, "unknown option key");
     }
 }
 
-static int solve_impl(sfgmres_t h, bool transpose, const double* b, const double* x0, double* x, int32_t m,
-                      int32_t s, int32_t k, double tol, sfgmres_stats* st) {
-    if (!h) return SFGMRES_ERR_INVALID_ARG;
-    if (!b || !x) return fail(h, SFGMRES_ERR_INVALID_ARG, "b and x must not be NULL");
-    if (!(tol > 0.0 && tol < 1.0)) return fail(h, SFGMRES_ERR_INVALID_ARG, "tol must be in (0, 1)");
-    int rc = check_params(h, m, s, k);
-    if (rc) return rc;
-    CK(cudaSetDevice(h->dev));
-    const int64_t launches0 = g_launches;
-    const int jmax = h->max_outer;
-    Plan P;
-    if ((rc = prepare(h, m, s, k, jmax, &P, transpose))) return rc;
-    const size_t nbytes = (size_t)h->n * sizeof(double);
-    if ((rc = ensure(h, h->bst, nbytes))) return rc;
-    if ((rc = ensure(h, h->xst, nbytes))) return rc;
-    if ((rc = ensure(h, h->x0st, nbytes))) return rc;
-    double* db = (double*)h->bst.p;
-    double* dx = (double*)h->xst.p;
-    double* dx0 = (double*)h->x0st.p;
-    const bool x_dev = is_device_ptr(x);
-    h->n_spmv = h->n_axpy = h->n_qr = 0;
-    CK(cudaEventRecord(h->ev_t0, h->st));
-    // private copies of b and x0 (x may alias x0, and host inputs are staged)
-    CK(cudaMemcpyAsync(db, b, nbytes, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
-    if (x0) {
-        CK(cudaMemcpyAsync(dx0, x0, nbytes, is_device_ptr(x0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                           h->st));
-    }
-    const double* px0 = x0 ? dx0 : nullptr;
-    // r0 = b - A x0 into v_0; beta, ||b||
-    launch_residual(P, db, px0, P.Vb);
-    launch_init_state(P, tol, jmax);
-    CK(cudaMemcpyAsync(h->h_ost, P.ost, sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    CK(cudaGetLastError());
-    OuterState os = *h->h_ost;
-    int status = SFGMRES_OK;
-    int outer = 0;
-    double rel_true = 0.0, rel_est = 0.0;
-    bool have_x = false;
-    if (!std::isfinite(os.beta) || !std::isfinite(os.bnorm) || os.nan) {
-        return fail(h, SFGMRES_ERR_NAN, "non-finite value in b or x0 (or in A x0)");
-    }
-    if (os.bnorm == 0.0) {  // x = 0
-        k_fill<<<grid_for(h->n), 256, 0, h->st>>>(h->n, 0.0, dx);
-        ++g_launches;
-        have_x = true;
-    } else if (os.beta <= os.tol_abs) {  // x0 already meets the tolerance
-        if (x0) k_copy<<<grid_for(h->n), 256, 0, h->st>>>(h->n, dx0, dx);
-        else k_fill<<<grid_for(h->n), 256, 0, h->st>>>(h->n, 0.0, dx);
-        ++g_launches;
-        have_x = true;
-        rel_true = os.beta / os.bnorm;
-        rel_est = rel_true;
-    } else {
-        status = SFGMRES_NOT_CONVERGED;
-        for (int j = 0; j < jmax; ++j) {
-            if ((rc = run_cycle(h, P, j, P.Vb + (int64_t)j * h->n, P.nu + j, h->c3, P.Z + (int64_t)j * h->n)))
-                return rc;
-            launch_outer_step(P, j);
-            CK(cudaMemcpyAsync(h->h_ost, P.ost, sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
-            CK(cudaStreamSynchronize(h->st));
-            CK(cudaGetLastError());
-            os = *h->h_ost;
-            if (os.nan) return fail(h, SFGMRES_ERR_NAN, "non-finite value during the iteration");
-            if (os.breakdown == 2) {  // the inner cycle accepted no column: keep the iterate of step j
-                status = SFGMRES_BREAKDOWN;
-                if (j > 0) {
-                    launch_final_x(P, j, px0, dx);
-                    launch_residual(P, db, dx, nullptr);
-                    launch_true_residual_reduce(P);
-                } else {
-                    if (x0) k_copy<<<grid_for(h->n), 256, 0, h->st>>>(h->n, dx0, dx);
-                    else k_fill<<<grid_for(h->n), 256, 0, h->st>>>(h->n, 0.0, dx);
-                    ++g_launches;
-                    launch_residual(P, db, px0, nullptr);
-                    launch_true_residual_reduce(P);
-                }
-                outer = j;
-                have_x = true;
-                break;
-            }
-            outer = j + 1;
-            rel_est = os.est / os.bnorm;
-            const bool last = (j + 1 == jmax);
-            if (os.conv_est || os.breakdown == 1 || last) {
-                launch_final_x(P, j + 1, px0, dx);
-                launch_residual(P, db, dx, nullptr);
-                launch_true_residual_reduce(P);
-                CK(cudaMemcpyAsync(h->h_ost, P.ost, sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
-                CK(cudaStreamSynchronize(h->st));
-                os = *h->h_ost;
-                rel_true = std::sqrt(os.true_res2) / os.bnorm;
-                have_x = true;
-                if (rel_true <= tol || os.breakdown == 1) {
-                    status = SFGMRES_OK;
-                    break;
-                }
-            }
-        }
-    }
-    if (!have_x) return fail(h, SFGMRES_ERR_CUDA, "internal: no iterate formed");
-    CK(cudaMemcpyAsync(x, dx, nbytes, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(h->h_ost, P.ost, sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaEventRecord(h->ev_t1, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    CK(cudaGetLastError());
-    if (status == SFGMRES_BREAKDOWN) rel_true = std::sqrt(h->h_ost->true_res2) / h->h_ost->bnorm;
-    if (st) {
-        st->status = status;
-        st->outer_iters = outer;
-        st->rel_res_true = rel_true;
-        st->rel_res_est = rel_est;
-        const int cnt = std::min(outer + (status == SFGMRES_BREAKDOWN ? 1 : 0), jmax);
-        std::vector<int> kh(std::max(cnt, 1)), rh(std::max(cnt, 1));
-        std::vector<double> eh(std::max(cnt, 1)), fh(std::max(cnt, 1));
-        if (cnt > 0) {
-            CK(cudaMemcpy(kh.data(), P.k_hist, cnt * sizeof(int), cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(rh.data(), P.reason_hist, cnt * sizeof(int), cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(eh.data(), P.est_hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(fh.data(), P.ffom_hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));
-        }
-        int tot = 0;
-        for (int q = 0; q < cnt; ++q) tot += kh[q];
-        st->total_inner = tot;
-        const int cap = std::min(cnt, st->hist_cap);
-        for (int q = 0; q < cap; ++q) {
-            if (st->inner_k) st->inner_k[q] = kh[q];
-            if (st->inner_reason) st->inner_reason[q] = rh[q];
-            if (st->res_est && q < outer) st->res_est[q] = eh[q];
-            if (st->ffom_res && q < outer) st->ffom_res[q] = fh[q];
-        }
-        st->kernel_launches = g_launches - launches0;
-        float tms = 0.f;
-        cudaEventElapsedTime(&tms, h->ev_t0, h->ev_t1);
-        st->t_total_ms = tms;
-        if (h->profile) {
-            st->t_inner_spmv_ms = ev_sum(h->ev_spmv, h->n_spmv);
-            st->n_inner_spmv = (int64_t)h->n_spmv;
-            st->t_inner_axpy_ms = ev_sum(h->ev_axpy, h->n_axpy);
-            st->n_inner_axpy = (int64_t)h->n_axpy;
-            st->t_qr_ms = ev_sum(h->ev_qr, h->n_qr);
-            st->n_qr = (int64_t)h->n_qr;
-        } else {
-            st->t_inner_spmv_ms = st->t_inner_axpy_ms = st->t_qr_ms = 0.0;
-            st->n_inner_spmv = st->n_inner_axpy = st->n_qr = 0;
-        }
-    }
-    return status;
-}
-
 int sfgmres_solve(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m, int32_t s, int32_t k,
                   double tol, sfgmres_stats* st) {
-    return solve_impl(h, false, b, x0, x, m, s, k, tol, st);
+    return solve_single(h, false, b, x0, x, m, s, k, tol, st);
 }
 
 int sfgmres_solve_transpose(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m, int32_t s,
                             int32_t k, double tol, sfgmres_stats* st) {
-    return solve_impl(h, true, b, x0, x, m, s, k, tol, st);
+    return solve_single(h, true, b, x0, x, m, s, k, tol, st);
+}
+
+int sfgmres_solve_batch(sfgmres_t h, int32_t nrhs, const double* b, const double* x0, double* x, int32_t m,
+                        int32_t s, int32_t k, double tol, int32_t flags, sfgmres_batch_stats* st) {
+    if (!h) return SFGMRES_ERR_INVALID_ARG;
+    if (nrhs < 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "nrhs must be >= 1");
+    if (flags & ~SFGMRES_SOLVE_TRANSPOSE) return fail(h, SFGMRES_ERR_INVALID_ARG, "unknown solve flag");
+    int rc = check_solve_args(h, b, x, m, s, k, tol);
+    if (rc) return rc;
+    CK(cudaSetDevice(h->dev));
+    const int64_t launches0 = g_launches;
+    SolveOut so;
+    if ((rc = solve_core(h, (flags & SFGMRES_SOLVE_TRANSPOSE) != 0, nrhs, b, x0, x, m, s, k, tol, &so))) return rc;
+    const int status = status_of(so.pr);
+    if (status == SFGMRES_ERR_NAN) {
+        int first = 0;
+        while (so.pr[first].status != SFGMRES_ERR_NAN) ++first;
+        fail(h, SFGMRES_ERR_NAN, "non-finite value in problem " + std::to_string(first) +
+                                     " (its x is x0; the other problems' results are valid)");
+    }
+    if (st) {
+        const int NP = (int)so.pr.size();
+        st->problems = NP;
+        int lock = 0;
+        int64_t ninner = 0;
+        std::vector<int> kh;
+        if (so.jmax > 0 && NP > 0) {
+            kh.resize((size_t)NP * so.jmax);
+            CK(cudaMemcpy(kh.data(), so.P.k_hist, kh.size() * sizeof(int), cudaMemcpyDeviceToHost));
+        }
+        for (int p = 0; p < NP; ++p) {
+            const ProbOut& o = so.pr[p];
+            lock = std::max(lock, o.outer + (o.brk ? 1 : 0));
+            const int cnt = std::min(o.outer + (o.brk ? 1 : 0), so.jmax);
+            for (int q = 0; q < cnt; ++q) ninner += kh[(size_t)p * so.jmax + q];
+            if (st->status) st->status[p] = o.status;
+            if (st->outer_iters) st->outer_iters[p] = o.outer;
+            if (st->rel_res_true) st->rel_res_true[p] = o.rel_true;
+            if (st->rel_res_est) st->rel_res_est[p] = o.rel_est;
+        }
+        st->lockstep_outer = lock;
+        st->total_inner = ninner;
+        st->kernel_launches = g_launches - launches0;
+        float tms = 0.f;
+        cudaEventElapsedTime(&tms, h->ev_t0, h->ev_t1);
+        st->t_total_ms = tms;
+    }
+    return status;
 }
 
 int sfgmres_update_values(sfgmres_t h, const double* vals) {
@@ -839,16 +1301,18 @@ int sfgmres_inner_cycle(sfgmres_t h, const double* v, double* z, int32_t m, int3
                         double* y, int32_t* k_out, int32_t* reason_out) {
     if (!h) return SFGMRES_ERR_INVALID_ARG;
     if (!v || !z || !k_out) return fail(h, SFGMRES_ERR_INVALID_ARG, "v, z and k_out must not be NULL");
+    if (h->nsys != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "sfgmres_inner_cycle needs a single-system handle");
     int rc = check_params(h, m, s, k);
     if (rc) return rc;
     CK(cudaSetDevice(h->dev));
     Plan P;
-    if ((rc = prepare(h, m, s, k, 0, &P))) return rc;
-    if ((rc = run_cycle(h, P, -1, v, nullptr, 0, z))) return rc;
-    CK(cudaMemcpyAsync(h->h_cyc, P.cyc, sizeof(CycleState), cudaMemcpyDeviceToHost, h->st));
+    if ((rc = prepare(h, 1, m, s, k, 0, &P, nullptr))) return rc;
+    if ((rc = run_cycle(h, P, -1, v, nullptr, 0, 0, z))) return rc;
+    CycleState* hc = (CycleState*)h->h_cyc.p;
+    CK(cudaMemcpyAsync(hc, P.cyc, sizeof(CycleState), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
-    const CycleState cs = *h->h_cyc;
+    const CycleState cs = *hc;
     *k_out = cs.k;
     if (reason_out) *reason_out = cs.reason;
     if (cs.reason == 6) return fail(h, SFGMRES_ERR_NAN, "non-finite value in the inner cycle");
@@ -867,17 +1331,17 @@ int sfgmres_inner_cycle(sfgmres_t h, const double* v, double* z, int32_t m, int3
 int sfgmres_sketch_apply(sfgmres_t h, int32_t s, const double* v, double* c) {
     if (!h) return SFGMRES_ERR_INVALID_ARG;
     if (!v || !c) return fail(h, SFGMRES_ERR_INVALID_ARG, "NULL pointer");
+    if (h->nsys != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "sfgmres_sketch_apply needs a single-system handle");
     int rc = check_params(h, 1, s, 0);
     if (rc) return rc;
     CK(cudaSetDevice(h->dev));
-    if ((rc = build_sketch(h, s))) return rc;
     Plan P;
     const int save = h->prec;
     h->prec = kFP64;
-    rc = prepare(h, 1, s, 0, 0, &P);
+    rc = prepare(h, 1, 1, s, 0, 0, &P, nullptr);
     h->prec = save;
     if (rc) return rc;
-    launch_sketch_partials(P, v, nullptr, nullptr, P.cpart);
+    launch_sketch_partials(P, v, nullptr, 0, nullptr, P.cpart);
     launch_sketch_reduce(P, P.cpart, c, nullptr);
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
@@ -887,14 +1351,14 @@ int sfgmres_sketch_apply(sfgmres_t h, int32_t s, const double* v, double* c) {
 int sfgmres_sketch_pattern(sfgmres_t h, int32_t s, int32_t* rows, int8_t* signs) {
     if (!h) return SFGMRES_ERR_INVALID_ARG;
     if (!rows || !signs) return fail(h, SFGMRES_ERR_INVALID_ARG, "NULL pointer");
+    if (h->nsys != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "sfgmres_sketch_pattern needs a single-system handle");
     int rc = check_params(h, 1, s, 0);
     if (rc) return rc;
     CK(cudaSetDevice(h->dev));
     const int zeta = (h->kind == 1) ? 1 : h->zeta;
     int8_t* neg = nullptr;
     CK(cudaMalloc(&neg, (size_t)h->n * zeta));
-    Plan dummy;
-    launch_sketch_pattern(dummy, h->n, s, zeta, h->kind, h->seed, rows, neg, h->st);
+    launch_sketch_pattern(h->n, s, zeta, h->kind, h->seed, rows, neg, h->st);
     const int64_t cnt = (int64_t)h->n * zeta;
     k_neg_to_sign<<<grid_for(cnt), 256, 0, h->st>>>(cnt, neg, signs);
     ++g_launches;
@@ -909,15 +1373,11 @@ int sfgmres_spmv(sfgmres_t h, const double* xv, double* yv) {
     if (!h) return SFGMRES_ERR_INVALID_ARG;
     if (!xv || !yv) return fail(h, SFGMRES_ERR_INVALID_ARG, "NULL pointer");
     CK(cudaSetDevice(h->dev));
+    Geo* g = nullptr;
+    int rc = get_geometry(h, 1, &g);
+    if (rc) return rc;
     Plan P;
-    P.n = h->n;
-    P.rp = h->rp;
-    P.col = h->col;
-    P.val = h->val;
-    P.vec = h->vec;
-    P.Bn = h->Bn;
-    P.nblk = h->nblk;
-    P.st = h->st;
+    plan_geometry(h, g, false, P);
     launch_spmv_f64(P, xv, yv);
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());

@@ -1,19 +1,20 @@
-// One sketched-GMRES cycle on the device (Section 3; Eq. 3 with r0 = v_j and zero initial guess).
+// One sketched-GMRES cycle on the device for every problem of a batch (Section 3; Eq. 3 with r0 = v_j and zero
+// initial guess).
 //
 // Storage: the basis vectors are kept unnormalised, b_l = sigma_l u_l; scale factors live in scalars and a stored
 // vector is only ever rescaled by a power of two.  Per inner step i (0-based; the paper's i+1):
 //   k_inner_spmv  w' = A u_i, the truncated-Arnoldi dot products u_l^T w' for the last t basis vectors
-//                 (Section 4.1), and the per-block partial sketch S w' -- one pass over A; the row block of w' stays
-//                 in shared memory for the sketch gather lists.  In FP64 the sketch partials are accumulated exactly
-//                 in 64-bit fixed point (integer adds), which keeps the scarce FP64 pipe for the SpMV.
+//                 (Section 4.1), ||u_i||^2, and the per-block partial sketch S w' -- one pass over A; the row block of
+//                 w' stays in shared memory for the sketch gather lists.  In FP64 the sketch partials are accumulated
+//                 exactly in 64-bit fixed point (integer adds), which keeps the scarce FP64 pipe for the SpMV.
 //   k_inner_axpy  sigma_i = 1/||u_i||, h_l = b_l^T A b_i, the sketched column S A b_i = sigma_i S w', and the next
 //                 stored vector u_{i+1} = 2^p_i (w' - sum_l sigma_l^2 (u_l^T w') u_l), with 2^p_i the power of two
-//                 nearest below sigma_i (an exact rescaling that keeps stored norms O(||A||) instead of growing like
-//                 ||A||^i), and its per-block norm partials.
-//   k_inner_qr    a cluster of CTAs: Gram-Schmidt with one reorthogonalisation pass of S A b_i against Q
+//                 just below sigma_i (an exact rescaling that keeps stored norms O(||A||) instead of growing like
+//                 ||A||^i).
+//   k_inner_qr    per problem a cluster of CTAs: Gram-Schmidt with one reorthogonalisation pass of S A b_i against Q
 //                 (Section 3, C2), the condition proxy max|r_ll|/min|r_ll| (rule C2), the running sketched residual
 //                 (rule C3) and C1.  It runs on a second stream, overlapping the next step's SpMV; a step that runs
-//                 past the end of the cycle is discarded.
+//                 past the end of a problem's cycle is discarded.
 // After the cycle: k_inner_ls solves R_k y = (Q^T S v)_k and k_inner_gemv forms z_j = B_k y_k (FP64 output).
 #include "kernels.h"
 #include "spmv.cuh"
@@ -26,78 +27,89 @@ namespace cg = cooperative_groups;
 
 namespace sfg {
 
+__device__ __forceinline__ bool cycle_idle(const Plan& P, int p, int i) {
+    const CycleState* c = P.cyc + p;
+    return c->stopped || c->brk_step <= i || (P.pflag[p] & 1);
+}
+
 // ---------------------------------------------------------------------------------------------------------------
-// Phase 1, one thread per row: w' = A u_i fused with storing w' (global W and the shared block copy) and the
-// window dot products acc_q += u_{lo+q}[r] * w'[r].  The window values and the next row group's extents are loaded
-// before the row's SpMV, so they are in flight together.  Returns the thread's largest exponent of w'.
+// Phase 1, one thread per row: w' = A u_i over the block (vector rows v0 .. v0+len = matrix rows v0-cs ..) fused
+// with storing w' (global W and the shared block copy), the window dot products acc_q += u_{lo+q}[r] * w'[r] and
+// ||u_i||^2.  The window values and the next row group's extents are loaded before the row's SpMV, so they are in
+// flight together.  Returns the thread's largest exponent of w'.
 template <int NW, typename MT, typename VT, typename AT>
-__device__ __forceinline__ int spmv_dots_scalar(int n, const int* __restrict__ rp, const int* __restrict__ col,
+__device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ rp, const int* __restrict__ col,
                                                 const MT* __restrict__ val, const VT* __restrict__ Ub, int i, int lo,
-                                                int r0, int r1, AT* __restrict__ wblk, AT* __restrict__ W,
+                                                int v0, int len, int cs, AT* __restrict__ wblk, AT* __restrict__ W,
                                                 AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
     const int lane = threadIdx.x & 31;
-    const VT* x = Ub + (int64_t)i * n;
+    const VT* x = Ub + (int64_t)i * N;
+    const VT* xs = x + cs;                // gather base: vector index of matrix column c is c + cs
+    const int* rpm = rp + (v0 - cs);      // row pointers of the block's matrix rows
     int emax = 1;
-    int rw = r0 + (threadIdx.x & ~31);
-    int a = 0, len = 0;
-    if (rw + lane < r1) {
-        a = __ldg(rp + rw + lane);
-        len = __ldg(rp + rw + lane + 1) - a;
+    int kw = threadIdx.x & ~31;
+    int a = 0, rl = 0;
+    if (kw + lane < len) {
+        a = __ldg(rpm + kw + lane);
+        rl = __ldg(rpm + kw + lane + 1) - a;
     }
-    for (; rw < r1; rw += blockDim.x) {  // warp-uniform loop
-        const int r = rw + lane;
-        const bool ok = r < r1;
+    for (; kw < len; kw += blockDim.x) {  // warp-uniform loop over the block's rows
+        const int k = kw + lane;
+        const bool ok = k < len;
+        const int r = v0 + k;
         AT uw[NW > 0 ? NW : 1];
 #pragma unroll
-        for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_plain(Ub + (int64_t)(lo + q) * n + r) : AT(0);
+        for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
         AT ui;  // u_i[r] (the last window vector when there is a window) for ||u_i||^2
         if constexpr (NW > 0) ui = uw[NW - 1];
         else ui = ok ? ld_plain(x + r) : AT(0);
-        const int rn = r + (int)blockDim.x;
-        int an = 0, lenn = 0;
-        if (rn < r1) {
-            an = __ldg(rp + rn);
-            lenn = __ldg(rp + rn + 1) - an;
+        const int kn = k + (int)blockDim.x;
+        int an = 0, rln = 0;
+        if (kn < len) {
+            an = __ldg(rpm + kn);
+            rln = __ldg(rpm + kn + 1) - an;
         }
-        const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+        const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)rl);
         AT sum = AT(0);
         for (int pk = 0; pk < maxlen; pk += 4) {
             switch (min(maxlen - pk, 4)) {
-                case 1: row_chunk<1>(col, val, x, a, len, pk, sum); break;
-                case 2: row_chunk<2>(col, val, x, a, len, pk, sum); break;
-                case 3: row_chunk<3>(col, val, x, a, len, pk, sum); break;
-                default: row_chunk<4>(col, val, x, a, len, pk, sum); break;
+                case 1: row_chunk<1>(col, val, xs, a, rl, pk, sum); break;
+                case 2: row_chunk<2>(col, val, xs, a, rl, pk, sum); break;
+                case 3: row_chunk<3>(col, val, xs, a, rl, pk, sum); break;
+                default: row_chunk<4>(col, val, xs, a, rl, pk, sum); break;
             }
         }
         if (ok) {
             W[r] = sum;
-            wblk[r - r0] = sum;
+            wblk[k] = sum;
         }
 #pragma unroll
         for (int q = 0; q < NW; ++q) acc[q] += uw[q] * sum;
         nrm += ui * ui;
         emax = max(emax, exp_of(sum));
         a = an;
-        len = lenn;
+        rl = rln;
     }
     return emax;
 }
 
-// Phase 1 tail for the sub-warp path (w' already in shared memory): store w' and accumulate the window dots.
+// Phase 1 tail for the sub-warp path (w' already in shared memory): store w', accumulate the window dots and
+// ||u_i||^2.
 template <int NW, typename VT, typename AT>
-__device__ __forceinline__ int dots_pass(int n, int r0, int r1, const VT* __restrict__ Ub, int lo, int i,
+__device__ __forceinline__ int dots_pass(int N, int v0, int len, const VT* __restrict__ Ub, int lo, int i,
                                          const AT* __restrict__ wblk, AT* __restrict__ W,
                                          AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
     int emax = 1;
 #pragma unroll 2
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        const AT w = wblk[r - r0];
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+        const int r = v0 + k;
+        const AT w = wblk[k];
         W[r] = w;
         emax = max(emax, exp_of(w));
-        const AT ui = ld_plain(Ub + (int64_t)i * n + r);
+        const AT ui = ld_plain(Ub + (int64_t)i * N + r);
         nrm += ui * ui;
 #pragma unroll
-        for (int q = 0; q < NW; ++q) acc[q] += ld_plain(Ub + (int64_t)(lo + q) * n + r) * w;
+        for (int q = 0; q < NW; ++q) acc[q] += ld_plain(Ub + (int64_t)(lo + q) * N + r) * w;
     }
     return emax;
 }
@@ -108,21 +120,20 @@ __device__ __forceinline__ int dots_pass(int n, int r0, int r1, const VT* __rest
 // At most 56 registers per thread (registers are allocated in units of 8 per thread): two 512-thread CTAs per SM
 // then leave room for the sketched-QR cluster's CTAs to run beside them instead of displacing them.
 template <int V, int U, int NW, typename MT, typename VT, typename AT>
-__global__ void __maxnreg__(56)
-    k_inner_spmv(int n, int Bn, int s, int i, int H, const int* __restrict__ rp, const int* __restrict__ col,
-                 const MT* __restrict__ val, const VT* __restrict__ Ub, AT* __restrict__ W, AT* __restrict__ hpart,
-                 AT* __restrict__ cpart, AT* __restrict__ normpart, const int* __restrict__ seg,
-                 const uint16_t* __restrict__ ent, const CycleState* __restrict__ cyc) {
+__global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __restrict__ val) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AT* wblk = reinterpret_cast<AT*>(smem_raw);
     __shared__ AT red[512];
     __shared__ int stop_sh, emax_sh[16];
-    if (threadIdx.x == 0) stop_sh = (cyc->stopped || cyc->brk_step <= i) ? 1 : 0;
+    const int b = blockIdx.x;
+    const BlockInfo bi = block_info(P, b);
+    if (threadIdx.x == 0) stop_sh = cycle_idle(P, bi.prob, i) ? 1 : 0;
     __syncthreads();
     if (stop_sh) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int b = blockIdx.x;
-    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
+    const int s = P.s, Bn = P.Bn, N = P.N;
+    const VT* Ub = (const VT*)P.U;
+    AT* W = (AT*)P.W;
     const int lo = i - NW + 1;  // window u_lo..u_i (NW = min(t, i+1))
     AT acc[NW > 0 ? NW : 1];
 #pragma unroll
@@ -130,23 +141,25 @@ __global__ void __maxnreg__(56)
     int emax;
     AT nrm = AT(0);  // ||u_i||^2 over the block (the vector this step multiplies)
     if constexpr (V == 1) {
-        emax = spmv_dots_scalar<NW>(n, rp, col, val, Ub, i, lo, r0, r1, wblk, W, acc, nrm);
+        emax = spmv_dots_scalar<NW>(N, P.rp, P.col, val, Ub, i, lo, bi.v0, bi.len, bi.cs, wblk, W, acc, nrm);
     } else {
-        spmv_rows_vector<V, U, MT, VT, AT>(rp, col, val, Ub + (int64_t)i * n, r0, r1, wblk);
+        const int m0 = bi.v0 - bi.cs;
+        spmv_rows_vector<V, U, MT, VT, AT>(P.rp, P.col, val, Ub + (int64_t)i * N + bi.cs, m0, m0 + bi.len, wblk);
         __syncthreads();
-        emax = dots_pass<NW>(n, r0, r1, Ub, lo, i, wblk, W, acc, nrm);
+        emax = dots_pass<NW>(N, bi.v0, bi.len, Ub, lo, i, wblk, W, acc, nrm);
     }
     if (threadIdx.x == 0) wblk[Bn] = AT(0);
     {
         const AT v = block_sum_lean(nrm, red);
-        if (threadIdx.x == 0) normpart[b] = v;
+        if (threadIdx.x == 0) ((AT*)P.normpart)[b] = v;
     }
 #pragma unroll
     for (int q = 0; q < NW; ++q) {
         const AT v = block_sum_lean(acc[q], red);
-        if (threadIdx.x == 0) hpart[(int64_t)b * kMaxTrunc + q] = v;
+        if (threadIdx.x == 0) ((AT*)P.hpart)[(int64_t)b * kMaxTrunc + q] = v;
     }
-    const int* sg = seg + (int64_t)b * s;
+    const int* sg = P.seg + (int64_t)bi.list * s;
+    AT* cpart = (AT*)P.cpart;
     if constexpr (sizeof(AT) == 8) {
         // exact fixed-point sketch sums (integer adds; the FP64 pipe stays with the SpMV)
         emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
@@ -154,53 +167,61 @@ __global__ void __maxnreg__(56)
         __syncthreads();
         int Eb = 1;
         for (int q = 0; q < nw; ++q) Eb = max(Eb, emax_sh[q]);
+        const int H = P.sk_headroom;
         long long* qblk = reinterpret_cast<long long*>(wblk);
-        for (int r = threadIdx.x; r <= Bn; r += blockDim.x) qblk[r] = (r < r1 - r0) ? to_fixed((double)wblk[r], Eb, H) : 0;
+        for (int r = threadIdx.x; r <= Bn; r += blockDim.x)
+            qblk[r] = (r < bi.len) ? to_fixed((double)wblk[r], Eb, H) : 0;
         __syncthreads();
         const double unit = fixed_unit(0.0, Eb, H);
         const bool bad = exp_nonfinite(0.0, Eb);
         for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
-            const long long v = sum_list(ent, sg[rr], sg[rr + 1], qblk);
+            const long long v = sum_list(P.ent, sg[rr], sg[rr + 1], qblk);
             cpart[(int64_t)b * s + rr] = bad ? (AT)NAN : (AT)((double)v * unit);
         }
     } else {
         __syncthreads();
         for (int rr = threadIdx.x; rr < s; rr += blockDim.x)
-            cpart[(int64_t)b * s + rr] = sum_list(ent, sg[rr], sg[rr + 1], wblk);
+            cpart[(int64_t)b * s + rr] = sum_list(P.ent, sg[rr], sg[rr + 1], wblk);
     }
 }
 
 // ---------------------------------------------------------------------------------------------------------------
 // Truncated-Arnoldi update (NW = window size).  Each thread first loads its first PF rows of w' and of the window
 // vectors (they do not depend on the scalars), then forms sigma_i, the coefficients and its share of the sketched
-// column, so the row data are already in flight while the reductions run.
+// column of its problem, so the row data are already in flight while the reductions run.
 template <int NW, typename VT, typename AT>
-__global__ void __launch_bounds__(512)
-    k_inner_axpy(int n, int Bn, int nblk, int s, int i, int last, double sk_scale, VT* __restrict__ Ub,
-                 const AT* __restrict__ W, double* __restrict__ sigma, const AT* __restrict__ normpart,
-                 const AT* __restrict__ hpart, const AT* __restrict__ cpart, double* __restrict__ C,
-                 double* __restrict__ hco, CycleState* __restrict__ cyc) {
+__global__ void __launch_bounds__(512) k_inner_axpy(const Plan P, int i, int last) {
     constexpr int PF = 2;
     __shared__ AT coef_sh[kMaxTrunc];
     __shared__ double sig_sh;
     __shared__ int stop_sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int b = blockIdx.x;
-    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
+    const BlockInfo bi = block_info(P, b);
+    const int p = bi.prob;
+    const int N = P.N, s = P.s, m = P.m;
+    VT* Ub = (VT*)P.U;
+    const AT* W = (const AT*)P.W;
     const int lo = i - NW + 1;
     AT wv[PF], uv[PF][NW > 0 ? NW : 1];
     if (!last) {
 #pragma unroll
         for (int u = 0; u < PF; ++u) {
-            const int r = r0 + threadIdx.x + u * (int)blockDim.x;
-            wv[u] = (r < r1) ? W[r] : AT(0);
+            const int k = threadIdx.x + u * (int)blockDim.x;
+            const int r = bi.v0 + k;
+            wv[u] = (k < bi.len) ? W[r] : AT(0);
 #pragma unroll
-            for (int q = 0; q < NW; ++q) uv[u][q] = (r < r1) ? ld_plain(Ub + (int64_t)(lo + q) * n + r) : AT(0);
+            for (int q = 0; q < NW; ++q)
+                uv[u][q] = (k < bi.len) ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
         }
     }
-    if (threadIdx.x == 0) stop_sh = (cyc->stopped || cyc->brk_step <= i) ? 1 : 0;
+    if (threadIdx.x == 0) stop_sh = cycle_idle(P, p, i) ? 1 : 0;
     __syncthreads();
     if (stop_sh) return;
+    const int b0 = P.prob_b0[p], b1 = P.prob_b0[p + 1];
+    const bool lead = (b == b0);  // the problem's first block writes its scalars
+    double* sigma = P.sigma + (int64_t)p * (m + 1);
+    CycleState* cyc = P.cyc + p;
     // sigma_i = 1/||u_i|| from the SpMV kernel's per-block partials
     if (warp == 0) {
         double sig = 1.0;
@@ -210,7 +231,8 @@ __global__ void __launch_bounds__(512)
             sig = sigma[0];
         } else {
             AT a = AT(0);
-            for (int q = lane; q < nblk; q += 32) a += normpart[q];
+            const AT* np = (const AT*)P.normpart;
+            for (int q = b0 + lane; q < b1; q += 32) a += np[q];
             a = warp_sum(a);
             const double a2 = (double)a;
             bad = !(a2 > 0.0) || !isfinite(a2);
@@ -221,11 +243,11 @@ __global__ void __launch_bounds__(512)
             sig_sh = sig;
             if (bad) {
                 stop_sh = 1;
-                if (b == 0) {
+                if (lead) {
                     cyc->brk_reason = why;
                     atomicMin(&cyc->brk_step, i);
                 }
-            } else if (b == 0) {
+            } else if (lead) {
                 sigma[i] = sig;
             }
         }
@@ -236,22 +258,24 @@ __global__ void __launch_bounds__(512)
     // h_l = sigma_l sigma_i (u_l^T w'); the stored update uses sigma_l^2 (u_l^T w')
     if (warp < NW) {
         AT a = AT(0);
-        for (int q = lane; q < nblk; q += 32) a += hpart[(int64_t)q * kMaxTrunc + warp];
+        const AT* hp = (const AT*)P.hpart;
+        for (int q = b0 + lane; q < b1; q += 32) a += hp[(int64_t)q * kMaxTrunc + warp];
         a = warp_sum(a);
         if (lane == 0) {
             const int l = lo + warp;
             const double sl = (l == i) ? sig_i : sigma[l];
             coef_sh[warp] = (AT)(sl * sl * (double)a);
-            if (b == 0) hco[(int64_t)i * kMaxTrunc + warp] = sl * sig_i * (double)a;
+            if (lead) P.hco[((int64_t)p * m + i) * kMaxTrunc + warp] = sl * sig_i * (double)a;
         }
     }
-    // sketched column S A b_i = sigma_i S w': one warp per sketch row across the grid
-    const double csc = sk_scale * sig_i;
-    for (int rr = b * nw + warp; rr < s; rr += nblk * nw) {
+    // sketched column S A b_i = sigma_i S w': one warp per sketch row across the problem's blocks
+    const double csc = P.sk_scale * sig_i;
+    const AT* cp = (const AT*)P.cpart;
+    for (int rr = (b - b0) * nw + warp; rr < s; rr += (b1 - b0) * nw) {
         AT a = AT(0);
-        for (int q = lane; q < nblk; q += 32) a += cpart[(int64_t)q * s + rr];
+        for (int q = b0 + lane; q < b1; q += 32) a += cp[(int64_t)q * s + rr];
         a = warp_sum(a);
-        if (lane == 0) C[(int64_t)i * s + rr] = csc * (double)a;
+        if (lane == 0) P.C[((int64_t)p * m + i) * s + rr] = csc * (double)a;
     }
     if (last) return;
     __syncthreads();
@@ -263,7 +287,7 @@ __global__ void __launch_bounds__(512)
     AT cf[NW > 0 ? NW : 1];
 #pragma unroll
     for (int q = 0; q < NW; ++q) cf[q] = coef_sh[q];
-    VT* un = Ub + (int64_t)(i + 1) * n;
+    VT* un = Ub + (int64_t)(i + 1) * N;
     auto update = [&](int r, AT u, const AT (&uq)[NW > 0 ? NW : 1]) {
 #pragma unroll
         for (int q = 0; q < NW; ++q) u -= cf[q] * uq[q];
@@ -273,30 +297,37 @@ __global__ void __launch_bounds__(512)
     };
 #pragma unroll
     for (int u = 0; u < PF; ++u) {
-        const int r = r0 + threadIdx.x + u * (int)blockDim.x;
-        if (r < r1) update(r, wv[u], uv[u]);
+        const int k = threadIdx.x + u * (int)blockDim.x;
+        if (k < bi.len) update(bi.v0 + k, wv[u], uv[u]);
     }
 #pragma unroll 2
-    for (int r = r0 + threadIdx.x + PF * (int)blockDim.x; r < r1; r += blockDim.x) {
+    for (int k = threadIdx.x + PF * (int)blockDim.x; k < bi.len; k += blockDim.x) {
+        const int r = bi.v0 + k;
         AT uq[NW > 0 ? NW : 1];
 #pragma unroll
-        for (int q = 0; q < NW; ++q) uq[q] = ld_plain(Ub + (int64_t)(lo + q) * n + r);
+        for (int q = 0; q < NW; ++q) uq[q] = ld_plain(Ub + (int64_t)(lo + q) * N + r);
         update(r, W[r], uq);
     }
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// Sketched QR update of column i on a cluster of CTAs; CTA q of the cluster owns rows [s q / nq, s (q+1) / nq) of
-// Q and of the working vectors, and partial dot products are exchanged through distributed shared memory and summed
-// in rank order (deterministic).  Every early exit is decided from values all CTAs of the cluster share.  CTAs are
-// small (128 threads) so they fit beside the inner SpMV's CTAs, and every long FP64 dependency chain is split into
-// four independent accumulators (combined in a fixed order).
-__global__ void __launch_bounds__(128)
-    k_inner_qr(int s, int m, int i, const double* __restrict__ C, double* __restrict__ Q, double* __restrict__ R,
-               double* __restrict__ d, double* __restrict__ e, double* __restrict__ rho,
-               CycleState* __restrict__ cyc) {
+// Sketched QR update of column i, one cluster of nq CTAs per problem (cluster index = problem); CTA q of a cluster
+// owns rows [s q / nq, s (q+1) / nq) of Q and of the working vectors, and partial dot products are exchanged
+// through distributed shared memory and summed in rank order (deterministic).  Every early exit is decided from
+// values all CTAs of the cluster share.  CTAs are small (128 threads) so they fit beside the inner SpMV's CTAs, and
+// every long FP64 dependency chain is split into four independent accumulators (combined in a fixed order).
+__global__ void __launch_bounds__(128) k_inner_qr(const Plan P, int i) {
     cg::cluster_group cl = cg::this_cluster();
     const int q = (int)cl.block_rank(), nq = (int)cl.num_blocks();
+    const int prob = blockIdx.x / nq;
+    const int s = P.s, m = P.m;
+    const double* __restrict__ C = P.C + (int64_t)prob * m * s;
+    double* __restrict__ Q = P.Q + (int64_t)prob * m * s;
+    double* __restrict__ R = P.R + (int64_t)prob * m * m;
+    double* __restrict__ d = P.d + (int64_t)prob * m;
+    double* __restrict__ e = P.e + (int64_t)prob * s;
+    double* __restrict__ rho = P.rho + (int64_t)prob * m;
+    CycleState* cyc = P.cyc + prob;
     const int rlo = (int)((int64_t)s * q / nq), rhi = (int)((int64_t)s * (q + 1) / nq), nr = rhi - rlo;
     const int nrmax = (s + nq - 1) / nq;
     extern __shared__ double qsm[];
@@ -308,7 +339,8 @@ __global__ void __launch_bounds__(128)
     __shared__ int code_sh;
     // state read by every CTA before the first cluster barrier (rank 0 writes it only after the last one)
     const double dmax0 = cyc->dmax, dmin0 = cyc->dmin, thr = cyc->cond_thr;
-    if (q == 0 && threadIdx.x == 0) code_sh = cyc->stopped ? 1 : (cyc->brk_step <= i ? 2 : 0);
+    if (q == 0 && threadIdx.x == 0)
+        code_sh = (cyc->stopped || (P.pflag[prob] & 1)) ? 1 : (cyc->brk_step <= i ? 2 : 0);
     cl.sync();
     const int code = *cl.map_shared_rank(&code_sh, 0);
     cl.sync();
@@ -425,12 +457,17 @@ __global__ void __launch_bounds__(128)
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// y = R_k^{-1} d (back substitution, one warp), coef_l = y_l * sigma_l.
-__global__ void k_inner_ls(int m, const double* __restrict__ R, const double* __restrict__ d,
-                           const double* __restrict__ sigma, double* __restrict__ y, double* __restrict__ coef,
-                           const CycleState* __restrict__ cyc) {
+// Per problem (one warp each): y = R_k^{-1} d by back substitution, coef_l = y_l * sigma_l.
+__global__ void k_inner_ls(const Plan P) {
     extern __shared__ double rhs[];
-    const int k = cyc->k;
+    const int p = blockIdx.x, m = P.m;
+    if (P.pflag[p] & 1) return;
+    const double* R = P.R + (int64_t)p * m * m;
+    const double* d = P.d + (int64_t)p * m;
+    const double* sigma = P.sigma + (int64_t)p * (m + 1);
+    double* y = P.y + (int64_t)p * m;
+    double* coef = P.coef + (int64_t)p * m;
+    const int k = P.cyc[p].k;
     const int lane = threadIdx.x;
     for (int l = lane; l < k; l += 32) rhs[l] = d[l];
     __syncwarp();
@@ -445,15 +482,19 @@ __global__ void k_inner_ls(int m, const double* __restrict__ R, const double* __
     }
 }
 
-// z = sum_{l<k} coef_l u_l, FP64 output.  FP64 basis: FP64 FMAs.  FP32/BF16 basis: the FP64 coefficients are
-// split into two FP32 parts and the sum is carried as an unevaluated FP32 pair (TwoSum, and FMA for the exact
-// product error), close to FP64 accuracy on the FP32 pipe.
+// z = sum_{l<k} coef_l u_l over each block's rows, FP64 output.  FP64 basis: FP64 FMAs.  FP32/BF16 basis: the FP64
+// coefficients are split into two FP32 parts and the sum is carried as an unevaluated FP32 pair (TwoSum, and FMA
+// for the exact product error), close to FP64 accuracy on the FP32 pipe.
 template <typename VT>
-__global__ void __launch_bounds__(256) k_inner_gemv(int n, const VT* __restrict__ Ub, const double* __restrict__ coef,
-                                                    const CycleState* __restrict__ cyc, double* __restrict__ z) {
+__global__ void __launch_bounds__(256) k_inner_gemv(const Plan P, double* __restrict__ z) {
     __shared__ double cf[kMaxM];
     __shared__ float ch[kMaxM], clo[kMaxM];
-    const int k = cyc->k;
+    const BlockInfo bi = block_info(P, blockIdx.x);
+    const int p = bi.prob;
+    if (P.pflag[p] & 1) return;
+    const int k = P.cyc[p].k, N = P.N;
+    const VT* Ub = (const VT*)P.U;
+    const double* coef = P.coef + (int64_t)p * P.m;
     for (int l = threadIdx.x; l < k; l += blockDim.x) {
         const double c = coef[l];
         cf[l] = c;
@@ -462,20 +503,21 @@ __global__ void __launch_bounds__(256) k_inner_gemv(int n, const VT* __restrict_
         clo[l] = (float)(c - (double)hi);
     }
     __syncthreads();
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    for (int kk = threadIdx.x; kk < bi.len; kk += blockDim.x) {
+        const int64_t r = bi.v0 + kk;
         if constexpr (sizeof(VT) == 8) {
             double acc = 0.0;
-            for (int l = 0; l < k; ++l) acc += cf[l] * (double)ld_plain(Ub + (int64_t)l * n + r);
+            for (int l = 0; l < k; ++l) acc += cf[l] * (double)ld_plain(Ub + (int64_t)l * N + r);
             z[r] = acc;
         } else {
             float sh = 0.f, sl = 0.f;
             for (int l = 0; l < k; ++l) {
-                const float u = ld_plain(Ub + (int64_t)l * n + r);
-                const float p = ch[l] * u;
-                const float pe = fmaf(ch[l], u, -p) + clo[l] * u;  // exact product error + low-part term
-                const float t1 = sh + p;                             // TwoSum(sh, p)
+                const float u = ld_plain(Ub + (int64_t)l * N + r);
+                const float pr = ch[l] * u;
+                const float pe = fmaf(ch[l], u, -pr) + clo[l] * u;  // exact product error + low-part term
+                const float t1 = sh + pr;                            // TwoSum(sh, pr)
                 const float bv = t1 - sh;
-                const float err = (sh - (t1 - bv)) + (p - bv);
+                const float err = (sh - (t1 - bv)) + (pr - bv);
                 sh = t1;
                 sl += err + pe;
             }
@@ -485,19 +527,25 @@ __global__ void __launch_bounds__(256) k_inner_gemv(int n, const VT* __restrict_
 }
 
 template <typename VT>
-__global__ void k_export_basis(int n, int count, const VT* __restrict__ Ub, const double* __restrict__ sigma,
-                               double* __restrict__ out) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-        for (int l = 0; l < count; ++l) out[(int64_t)l * n + r] = sigma[l] * (double)ld_plain(Ub + (int64_t)l * n + r);
+__global__ void k_export_basis(const Plan P, int count, double* __restrict__ out) {
+    const BlockInfo bi = block_info(P, blockIdx.x);
+    const double* sigma = P.sigma + (int64_t)bi.prob * (P.m + 1);
+    const VT* Ub = (const VT*)P.U;
+    for (int kk = threadIdx.x; kk < bi.len; kk += blockDim.x) {
+        const int64_t r = bi.v0 + kk;
+        for (int l = 0; l < count; ++l)
+            out[(int64_t)l * P.N + r] = sigma[l] * (double)ld_plain(Ub + (int64_t)l * P.N + r);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// Start of inner cycle j: reset the cycle state (C3 scale = FFOM residual of the previous outer step, beta at the
-// first, Eq. 5), u_0 = v_j (copied into the basis storage precision), c0 = S u_0, running residual e = c0.
-__global__ void k_cycle_reset(CycleState* cyc, const OuterState* ost, int j, int c3_on, double cond_thr,
-                              double* sigma) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    cyc->stopped = 0;
+// Start of inner cycle j, per problem: reset the cycle state (C3 scale = FFOM residual of the previous outer step,
+// beta at the first, Eq. 5); a problem that is done is marked stopped so every inner kernel skips it.
+__global__ void k_cycle_reset(const Plan P, int j, int c3_on, double cond_thr) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.P) return;
+    CycleState* cyc = P.cyc + p;
+    cyc->stopped = (P.pflag[p] & 1) ? 1 : 0;
     cyc->k = 0;
     cyc->reason = 0;
     cyc->brk_step = INT_MAX;
@@ -506,7 +554,8 @@ __global__ void k_cycle_reset(CycleState* cyc, const OuterState* ost, int j, int
     cyc->dmin = INFINITY;
     cyc->rho = INFINITY;
     cyc->cond_thr = cond_thr;
-    if (ost) {
+    if (j >= 0) {
+        const OuterState* ost = P.ost + p;
         const double sc = (j == 0) ? ost->beta : ost->ffom;
         cyc->c3_scale = sc;
         cyc->c3_tol = ost->tol_abs;
@@ -516,13 +565,13 @@ __global__ void k_cycle_reset(CycleState* cyc, const OuterState* ost, int j, int
         cyc->c3_tol = 0.0;
         cyc->c3_on = 0;
     }
-    sigma[0] = 1.0;
+    P.sigma[(int64_t)p * (P.m + 1)] = 1.0;
 }
 
-void launch_cycle_start(const Plan& p, int j, const double* v, const double* vscale_dev, int c3_on,
+void launch_cycle_start(const Plan& p, int j, const double* v, const double* vscale, int vstride, int c3_on,
                         double cond_thr) {
-    k_cycle_reset<<<1, 32, 0, p.st>>>(p.cyc, j >= 0 ? p.ost : nullptr, j, c3_on, cond_thr, p.sigma);
-    launch_sketch_partials(p, v, vscale_dev, p.U, p.cpart);
+    k_cycle_reset<<<(p.P + 127) / 128, 128, 0, p.st>>>(p, j, c3_on, cond_thr);
+    launch_sketch_partials(p, v, vscale, vstride, p.U, p.cpart);
     launch_sketch_reduce(p, p.cpart, p.c0, p.e);
     ++g_launches;
 }
@@ -531,9 +580,7 @@ template <int V, int U, int NW, typename MT, typename VT, typename AT>
 static void inner_spmv_v(const Plan& p, int i, const MT* val) {
     const size_t sm = (size_t)(p.Bn + 1) * sizeof(AT);
     set_smem((const void*)k_inner_spmv<V, U, NW, MT, VT, AT>, sm);
-    k_inner_spmv<V, U, NW, MT, VT, AT><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.s, i, p.sk_headroom, p.rp, p.col,
-                                                                 val, (const VT*)p.U, (AT*)p.W, (AT*)p.hpart,
-                                                                 (AT*)p.cpart, (AT*)p.normpart, p.seg, p.ent, p.cyc);
+    k_inner_spmv<V, U, NW, MT, VT, AT><<<p.nblk, 512, sm, p.st>>>(p, i, val);
 }
 
 template <int NW, typename MT, typename VT, typename AT>
@@ -568,9 +615,7 @@ void launch_inner_spmv(const Plan& p, int i) {
 
 template <int NW, typename VT, typename AT>
 static void inner_axpy_nw(const Plan& p, int i, bool last) {
-    k_inner_axpy<NW, VT, AT><<<p.nblk, 512, 0, p.st>>>(p.n, p.Bn, p.nblk, p.s, i, last ? 1 : 0, p.sk_scale,
-                                                       (VT*)p.U, (const AT*)p.W, p.sigma, (const AT*)p.normpart,
-                                                       (const AT*)p.hpart, (const AT*)p.cpart, p.C, p.hco, p.cyc);
+    k_inner_axpy<NW, VT, AT><<<p.nblk, 512, 0, p.st>>>(p, i, last ? 1 : 0);
 }
 
 template <typename VT, typename AT>
@@ -597,41 +642,38 @@ void launch_inner_axpy(const Plan& p, int i, bool last) {
 }
 
 cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st) {
-    const int nrmax = (p.s + kQrCluster - 1) / kQrCluster;
+    const int nq = p.qr_cluster;
+    const int nrmax = (p.s + nq - 1) / nq;
     const size_t sm = (size_t)(nrmax + 2 * p.m) * sizeof(double);
     set_smem((const void*)k_inner_qr, sm);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kQrCluster, 1, 1);
+    cfg.gridDim = dim3((unsigned)(nq * p.P), 1, 1);
     cfg.blockDim = dim3(128, 1, 1);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kQrCluster;
+    attr[0].val.clusterDim.x = nq;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     ++g_launches;
-    return cudaLaunchKernelEx(&cfg, k_inner_qr, p.s, p.m, i, (const double*)p.C, p.Q, p.R, p.d, p.e, p.rho, p.cyc);
+    return cudaLaunchKernelEx(&cfg, k_inner_qr, p, i);
 }
 
 void launch_inner_finish(const Plan& p, double* z) {
-    k_inner_ls<<<1, 32, (size_t)p.m * sizeof(double), p.st>>>(p.m, p.R, p.d, p.sigma, p.y, p.coef, p.cyc);
-    const int th = 256;
-    const int gr = (int)std::min<int64_t>(((int64_t)p.n + th - 1) / th, 152 * 8);
-    if (p.prec == kFP64) k_inner_gemv<double><<<gr, th, 0, p.st>>>(p.n, (const double*)p.U, p.coef, p.cyc, z);
-    else if (p.prec == kFP32) k_inner_gemv<float><<<gr, th, 0, p.st>>>(p.n, (const float*)p.U, p.coef, p.cyc, z);
-    else k_inner_gemv<__nv_bfloat16><<<gr, th, 0, p.st>>>(p.n, (const __nv_bfloat16*)p.U, p.coef, p.cyc, z);
+    k_inner_ls<<<p.P, 32, (size_t)p.m * sizeof(double), p.st>>>(p);
+    if (p.prec == kFP64) k_inner_gemv<double><<<p.nblk, 256, 0, p.st>>>(p, z);
+    else if (p.prec == kFP32) k_inner_gemv<float><<<p.nblk, 256, 0, p.st>>>(p, z);
+    else k_inner_gemv<__nv_bfloat16><<<p.nblk, 256, 0, p.st>>>(p, z);
     g_launches += 2;
 }
 
 void launch_export_basis(const Plan& p, double* out, int count) {
-    const int th = 256;
-    const int gr = (int)std::min<int64_t>(((int64_t)p.n + th - 1) / th, 152 * 8);
-    if (p.prec == kFP64) k_export_basis<double><<<gr, th, 0, p.st>>>(p.n, count, (const double*)p.U, p.sigma, out);
-    else if (p.prec == kFP32) k_export_basis<float><<<gr, th, 0, p.st>>>(p.n, count, (const float*)p.U, p.sigma, out);
-    else k_export_basis<__nv_bfloat16><<<gr, th, 0, p.st>>>(p.n, count, (const __nv_bfloat16*)p.U, p.sigma, out);
+    if (p.prec == kFP64) k_export_basis<double><<<p.nblk, 256, 0, p.st>>>(p, count, out);
+    else if (p.prec == kFP32) k_export_basis<float><<<p.nblk, 256, 0, p.st>>>(p, count, out);
+    else k_export_basis<__nv_bfloat16><<<p.nblk, 256, 0, p.st>>>(p, count, out);
     ++g_launches;
 }
 

@@ -1,4 +1,4 @@
-// Outer FGMRES (Algorithm 1) on the device, FP64 throughout.
+// Outer FGMRES (Algorithm 1) on the device for every problem of a batch, FP64 throughout.
 //
 // Outer step j:  w = A z_j (fused with the first batch of dot products v_l^T w), two classical Gram-Schmidt passes
 // against v_0..v_j (the reorthogonalised form of the orthogonalisation loop of Algorithm 1), h_{j+1,j} = ||w||,
@@ -6,6 +6,8 @@
 // column, which gives the FGMRES residual estimate |g_{j+1}| and the FFOM residual |g_{j+1}| / |c_j| (Eq. 4: the
 // FFOM residual is h_{j+1,j} |gamma_j|; in rotated form this is the FGMRES residual divided by the cosine of the
 // last rotation).  The FFOM residual feeds rule C3 of the next inner cycle through the bound of Eq. 5.
+// Row-block kernels skip the blocks of problems that are done; per-problem kernels reduce their problem's block
+// partials in block order, so every sum has a fixed order.
 #include "kernels.h"
 #include "spmv.cuh"
 
@@ -13,24 +15,29 @@
 
 namespace sfg {
 
+__device__ __forceinline__ bool outer_idle(const Plan& P, int p) { return (P.pflag[p] & 1) != 0; }
+
 // rb = b - A x (x may be null: rb = b); npart[b] = ||rb||^2 over the block, npart2[b] = ||b||^2 over the block.
 template <int V, int U>
 __global__ void __launch_bounds__(512, 2)
-    k_residual(int n, int Bn, const int* __restrict__ rp, const int* __restrict__ col,
-               const double* __restrict__ val, const double* __restrict__ bv, const double* __restrict__ x,
-               double* __restrict__ rb, double* __restrict__ npart, double* __restrict__ npart2) {
+    k_residual(const Plan P, const double* __restrict__ bv, const double* __restrict__ x, double* __restrict__ rb,
+               int only_final) {
     extern __shared__ double axb[];
     __shared__ double red[32];
     const int b = blockIdx.x;
-    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
+    const BlockInfo bi = block_info(P, b);
+    const int fl = P.pflag[bi.prob];
+    if (only_final ? !(fl & 2) : (fl & 1)) return;
     if (x) {
-        spmv_rows_to_smem<V, U, double, double, double>(rp, col, val, x, r0, r1, axb);
+        const int m0 = bi.v0 - bi.cs;
+        spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, x + bi.cs, m0, m0 + bi.len, axb);
         __syncthreads();
     }
     double a1 = 0.0, a2 = 0.0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    for (int k = threadIdx.x; k < bi.len; k += blockDim.x) {
+        const int r = bi.v0 + k;
         const double bb = bv[r];
-        const double rr = x ? bb - axb[r - r0] : bb;
+        const double rr = x ? bb - axb[k] : bb;
         if (rb) rb[r] = rr;
         a1 += rr * rr;
         a2 += bb * bb;
@@ -38,29 +45,30 @@ __global__ void __launch_bounds__(512, 2)
     a1 = block_sum(a1, red);
     a2 = block_sum(a2, red);
     if (threadIdx.x == 0) {
-        npart[b] = a1;
-        npart2[b] = a2;
+        P.npart[b] = a1;
+        P.npart2[b] = a2;
     }
 }
 
-void launch_residual(const Plan& p, const double* b, const double* x, double* rb) {
-    const size_t sm = (size_t)p.Bn * sizeof(double);
-    SFG_SPMV_DISPATCH(p.vec, (set_smem((const void*)k_residual<VV, UU>, sm), k_residual<VV, UU><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.rp, p.col, p.val, b, x,
-                                                                          rb, p.npart, p.npart2)));
+void launch_residual(const Plan& p, const double* b, const double* x, double* rb, bool only_final) {
+    const size_t sm = x ? (size_t)p.Bn * sizeof(double) : 0;
+    SFG_SPMV_DISPATCH(p.vec, (set_smem((const void*)k_residual<VV, UU>, sm),
+                              k_residual<VV, UU><<<p.nblk, 512, sm, p.st>>>(p, b, x, rb, only_final ? 1 : 0)));
     ++g_launches;
 }
 
-__global__ void k_init_state(int nblk, const double* __restrict__ npart, const double* __restrict__ npart2,
-                             double tol, OuterState* ost, double* nu) {
-    const int lane = threadIdx.x;
+// Per problem (one warp each): beta = ||r0||, ||b||, tol * ||b||, nu_0 = 1/beta, g_0 = beta.
+__global__ void k_init_state(const Plan P, double tol) {
+    const int p = blockIdx.x, lane = threadIdx.x;
     double a1 = 0.0, a2 = 0.0;
-    for (int q = lane; q < nblk; q += 32) {
-        a1 += npart[q];
-        a2 += npart2[q];
+    for (int q = P.prob_b0[p] + lane; q < P.prob_b0[p + 1]; q += 32) {
+        a1 += P.npart[q];
+        a2 += P.npart2[q];
     }
     a1 = warp_sum(a1);
     a2 = warp_sum(a2);
     if (lane == 0) {
+        OuterState* ost = P.ost + p;
         const double beta = sqrt(a1), bn = sqrt(a2);
         ost->j = 0;
         ost->conv_est = 0;
@@ -72,125 +80,142 @@ __global__ void k_init_state(int nblk, const double* __restrict__ npart, const d
         ost->ffom = beta;
         ost->true_res2 = a1;
         ost->tol_abs = tol * bn;
-        nu[0] = (beta > 0.0) ? 1.0 / beta : 0.0;
+        const int64_t o = (int64_t)p * (P.jmax + 1);
+        P.nu[o] = (beta > 0.0) ? 1.0 / beta : 0.0;
+        P.g[o] = beta;
     }
 }
 
-void launch_init_state(const Plan& p, double tol, int) {
-    k_init_state<<<1, 32, 0, p.st>>>(p.nblk, p.npart, p.npart2, tol, p.ost, p.nu);
+void launch_init_state(const Plan& p, double tol) {
+    k_init_state<<<p.P, 32, 0, p.st>>>(p, tol);
     ++g_launches;
 }
 
-__global__ void k_true_res(int nblk, const double* __restrict__ npart, OuterState* ost) {
+// Per problem flagged "finalise now": ost[p].true_res2 = sum of its blocks' npart.
+__global__ void k_true_res(const Plan P) {
+    const int p = blockIdx.x;
+    if (!(P.pflag[p] & 2)) return;
     double a = 0.0;
-    for (int q = threadIdx.x; q < nblk; q += 32) a += npart[q];
+    for (int q = P.prob_b0[p] + threadIdx.x; q < P.prob_b0[p + 1]; q += 32) a += P.npart[q];
     a = warp_sum(a);
-    if (threadIdx.x == 0) ost->true_res2 = a;
+    if (threadIdx.x == 0) P.ost[p].true_res2 = a;
 }
 
 void launch_true_residual_reduce(const Plan& p) {
-    k_true_res<<<1, 32, 0, p.st>>>(p.nblk, p.npart, p.ost);
+    k_true_res<<<p.P, 32, 0, p.st>>>(p);
     ++g_launches;
 }
 
-// w = A z into smem and Wo; opart[b*ldo + l] = Vb_l(block) . w(block) for l <= j.
-template <int V, int U>
-__global__ void __launch_bounds__(512, 2)
-    k_outer_spmv(int n, int Bn, int j, int ldo, const int* __restrict__ rp, const int* __restrict__ col,
-                 const double* __restrict__ val, const double* __restrict__ z, const double* __restrict__ Vb,
-                 double* __restrict__ Wo, double* __restrict__ opart) {
-    extern __shared__ double wb[];
-    const int b = blockIdx.x;
-    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
-    spmv_rows_to_smem<V, U, double, double, double>(rp, col, val, z, r0, r1, wb);
-    __syncthreads();
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) Wo[r] = wb[r - r0];
+// Dots of the block's part of v_0..v_j with the block vector wb (smem): opart[b*ldo + l], one warp per column.
+__device__ __forceinline__ void block_dots(const Plan& P, const BlockInfo& bi, int b, int j,
+                                           const double* __restrict__ wb) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ldo = P.jmax + 1;
     for (int l = warp; l <= j; l += nw) {
-        const double* vl = Vb + (int64_t)l * n;
+        const double* vl = P.Vb + (int64_t)l * P.N + bi.v0;
         double acc = 0.0;
-        for (int r = r0 + lane; r < r1; r += 32) acc += vl[r] * wb[r - r0];
+        for (int k = lane; k < bi.len; k += 32) acc += vl[k] * wb[k];
         acc = warp_sum(acc);
-        if (lane == 0) opart[(int64_t)b * ldo + l] = acc;
+        if (lane == 0) P.opart[(int64_t)b * ldo + l] = acc;
     }
 }
 
-// out[l] = nu[l] * sum_b opart[b*ldo + l] for l < ncols (one warp per column, fixed order)
-__global__ void k_reduce_cols(int nblk, int ncols, int ldo, const double* __restrict__ opart,
-                              const double* __restrict__ nu, double* __restrict__ out) {
+// w = A z_j into smem and Wo; opart[b*ldo + l] = Vb_l(block) . w(block) for l <= j.
+template <int V, int U>
+__global__ void __launch_bounds__(512, 2) k_outer_spmv(const Plan P, int j) {
+    extern __shared__ double wb[];
+    const int b = blockIdx.x;
+    const BlockInfo bi = block_info(P, b);
+    if (outer_idle(P, bi.prob)) return;
+    const double* z = P.Z + (int64_t)j * P.N;
+    const int m0 = bi.v0 - bi.cs;
+    spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, z + bi.cs, m0, m0 + bi.len, wb);
+    __syncthreads();
+    for (int k = threadIdx.x; k < bi.len; k += blockDim.x) P.Wo[bi.v0 + k] = wb[k];
+    block_dots(P, bi, b, j, wb);
+}
+
+// out[p*ldo + l] = nu[p][l] * sum over the blocks of problem p of opart[b*ldo + l]  (one warp per (p, l)).
+__global__ void k_reduce_cols(const Plan P, int ncols, double* __restrict__ out) {
     const int lane = threadIdx.x & 31;
-    const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (l >= ncols) return;
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= (int64_t)P.P * ncols) return;
+    const int p = (int)(w / ncols), l = (int)(w % ncols);
+    if (outer_idle(P, p)) return;
+    const int ldo = P.jmax + 1;
     double acc = 0.0;
-    for (int q = lane; q < nblk; q += 32) acc += opart[(int64_t)q * ldo + l];
+    for (int q = P.prob_b0[p] + lane; q < P.prob_b0[p + 1]; q += 32) acc += P.opart[(int64_t)q * ldo + l];
     acc = warp_sum(acc);
-    if (lane == 0) out[l] = nu[l] * acc;
+    if (lane == 0) out[(int64_t)p * ldo + l] = P.nu[(int64_t)p * ldo + l] * acc;
 }
 
 // One classical Gram-Schmidt subtraction w <- w - sum_{l<=j} h_l v_l with v_l = nu_l Vb_l.
 //  final == 0: result back into Wo and the next pass's dots into opart
-//  final == 1: result into dst (= Vb_{j+1}, unnormalised) and ||w||^2 partials into npart
+//  final == 1: result into Vb_{j+1} (unnormalised) and ||w||^2 partials into npart
 __global__ void __launch_bounds__(512, 2)
-    k_outer_cgs(int n, int Bn, int j, int ldo, int final_pass, const double* __restrict__ Vb,
-                const double* __restrict__ nu, const double* __restrict__ h, double* __restrict__ Wo,
-                double* __restrict__ opart, double* __restrict__ dst, double* __restrict__ npart) {
+    k_outer_cgs(const Plan P, int j, int final_pass, const double* __restrict__ h) {
     extern __shared__ double sm[];
-    double* cf = sm;              // [j+1]
-    double* wb = sm + (j + 1);    // [Bn]
+    double* cf = sm;            // [j+1]
+    double* wb = sm + (j + 1);  // [Bn]
     __shared__ double red[32];
-    for (int l = threadIdx.x; l <= j; l += blockDim.x) cf[l] = h[l] * nu[l];
-    __syncthreads();
     const int b = blockIdx.x;
-    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
+    const BlockInfo bi = block_info(P, b);
+    const int p = bi.prob;
+    if (outer_idle(P, p)) return;
+    const int N = P.N;
+    const int64_t o = (int64_t)p * (P.jmax + 1);
+    for (int l = threadIdx.x; l <= j; l += blockDim.x) cf[l] = h[o + l] * P.nu[o + l];
+    __syncthreads();
+    double* dst = P.Vb + (int64_t)(j + 1) * N;
     double nacc = 0.0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        double w = Wo[r];
-        for (int l = 0; l <= j; ++l) w -= cf[l] * Vb[(int64_t)l * n + r];
+    for (int k = threadIdx.x; k < bi.len; k += blockDim.x) {
+        const int r = bi.v0 + k;
+        double w = P.Wo[r];
+        for (int l = 0; l <= j; ++l) w -= cf[l] * P.Vb[(int64_t)l * N + r];
         if (final_pass) {
             dst[r] = w;
             nacc += w * w;
         } else {
-            Wo[r] = w;
-            wb[r - r0] = w;
+            P.Wo[r] = w;
+            wb[k] = w;
         }
     }
     if (final_pass) {
         nacc = block_sum(nacc, red);
-        if (threadIdx.x == 0) npart[b] = nacc;
+        if (threadIdx.x == 0) P.npart[b] = nacc;
         return;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int l = warp; l <= j; l += nw) {
-        const double* vl = Vb + (int64_t)l * n;
-        double acc = 0.0;
-        for (int r = r0 + lane; r < r1; r += 32) acc += vl[r] * wb[r - r0];
-        acc = warp_sum(acc);
-        if (lane == 0) opart[(int64_t)b * ldo + l] = acc;
-    }
+    block_dots(P, bi, b, j, wb);
 }
 
-// Hessenberg column j = h1 + h2 (and h_{j+1,j} = ||w||), Givens update, residual estimates, histories.
-__global__ void k_outer_givens(int j, int nblk, int ldH, const double* __restrict__ npart,
-                               const double* __restrict__ h1, const double* __restrict__ h2, double* __restrict__ H,
-                               double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
-                               double* __restrict__ nu, OuterState* ost, const CycleState* cyc,
-                               double* __restrict__ est_hist, double* __restrict__ ffom_hist,
-                               int* __restrict__ k_hist, int* __restrict__ reason_hist) {
-    const int lane = threadIdx.x;
+// Per problem (one warp): Hessenberg column j = h1 + h2 (and h_{j+1,j} = ||w||), Givens update, residual
+// estimates, histories.
+__global__ void k_outer_givens(const Plan P, int j) {
+    const int p = blockIdx.x, lane = threadIdx.x;
+    if (outer_idle(P, p)) return;
+    const int ldo = P.jmax + 1, J = P.jmax;
     double a = 0.0;
-    for (int q = lane; q < nblk; q += 32) a += npart[q];
+    for (int q = P.prob_b0[p] + lane; q < P.prob_b0[p + 1]; q += 32) a += P.npart[q];
     a = warp_sum(a);
     if (lane != 0) return;
-    k_hist[j] = cyc->k;
-    reason_hist[j] = cyc->reason;
+    OuterState* ost = P.ost + p;
+    const CycleState* cyc = P.cyc + p;
+    const int64_t oh = (int64_t)p * J, og = (int64_t)p * ldo;
+    P.k_hist[oh + j] = cyc->k;
+    P.reason_hist[oh + j] = cyc->reason;
     if (cyc->k == 0) {  // inner cycle produced no correction
         ost->breakdown = 2;
         return;
     }
     if (cyc->reason == 6) ost->nan = 1;
+    const double* h1 = P.h1 + og;
+    const double* h2 = P.h2 + og;
+    double* cs = P.cs + oh;
+    double* sn = P.sn + oh;
+    double* g = P.g + og;
     const double hn = sqrt(a);
-    double* colj = H + (int64_t)j * ldH;
+    double* colj = P.H + og * J + (int64_t)j * ldo;
     for (int l = 0; l <= j; ++l) colj[l] = h1[l] + h2[l];
     colj[j + 1] = hn;
     for (int l = 0; l < j; ++l) {
@@ -214,97 +239,93 @@ __global__ void k_outer_givens(int j, int nblk, int ldH, const double* __restric
     g[j + 1] = -s * gj;
     const double est = fabs(g[j + 1]);
     const double ffom = (c != 0.0) ? est / fabs(c) : INFINITY;
-    nu[j + 1] = (hn > 0.0) ? 1.0 / hn : 0.0;
+    P.nu[og + j + 1] = (hn > 0.0) ? 1.0 / hn : 0.0;
     ost->j = j + 1;
     ost->est = est;
     ost->ffom = ffom;
     ost->breakdown = (hn == 0.0) ? 1 : 0;
     ost->conv_est = (est <= ost->tol_abs) ? 1 : 0;
     if (!isfinite(est) || !isfinite(hn) || !isfinite(r)) ost->nan = 1;
-    est_hist[j] = est / ost->bnorm;
-    ffom_hist[j] = ffom / ost->bnorm;
-}
-
-__global__ void k_givens_init(double* g, const OuterState* ost) {
-    if (threadIdx.x == 0) g[0] = ost->beta;
+    P.est_hist[oh + j] = est / ost->bnorm;
+    P.ffom_hist[oh + j] = ffom / ost->bnorm;
 }
 
 void launch_outer_step(const Plan& p, int j) {
-    const int ldo = p.jmax + 1;
-    const double* z = p.Z + (int64_t)j * p.n;
-    if (j == 0) {
-        k_givens_init<<<1, 32, 0, p.st>>>(p.g, p.ost);
-        ++g_launches;
-    }
     const size_t sm = (size_t)p.Bn * sizeof(double);
-    SFG_SPMV_DISPATCH(p.vec, (set_smem((const void*)k_outer_spmv<VV, UU>, sm), k_outer_spmv<VV, UU><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, j, ldo, p.rp, p.col,
-                                                                             p.val, z, p.Vb, p.Wo, p.opart)));
+    SFG_SPMV_DISPATCH(p.vec, (set_smem((const void*)k_outer_spmv<VV, UU>, sm),
+                              k_outer_spmv<VV, UU><<<p.nblk, 512, sm, p.st>>>(p, j)));
     const int ncols = j + 1, wpb = 8;
-    const int rgrid = (ncols + wpb - 1) / wpb;
-    k_reduce_cols<<<rgrid, 32 * wpb, 0, p.st>>>(p.nblk, ncols, ldo, p.opart, p.nu, p.h1);
+    const int rgrid = (int)(((int64_t)p.P * ncols + wpb - 1) / wpb);
+    k_reduce_cols<<<rgrid, 32 * wpb, 0, p.st>>>(p, ncols, p.h1);
     const size_t sm2 = (size_t)(p.Bn + j + 1) * sizeof(double);
     set_smem((const void*)k_outer_cgs, sm2);
-    k_outer_cgs<<<p.nblk, 512, sm2, p.st>>>(p.n, p.Bn, j, ldo, 0, p.Vb, p.nu, p.h1, p.Wo, p.opart, nullptr,
-                                             nullptr);
-    k_reduce_cols<<<rgrid, 32 * wpb, 0, p.st>>>(p.nblk, ncols, ldo, p.opart, p.nu, p.h2);
-    k_outer_cgs<<<p.nblk, 512, (size_t)(j + 1) * sizeof(double), p.st>>>(
-        p.n, p.Bn, j, ldo, 1, p.Vb, p.nu, p.h2, p.Wo, nullptr, p.Vb + (int64_t)(j + 1) * p.n, p.npart);
-    k_outer_givens<<<1, 32, 0, p.st>>>(j, p.nblk, ldo, p.npart, p.h1, p.h2, p.H, p.cs, p.sn, p.g, p.nu, p.ost,
-                                       p.cyc, p.est_hist, p.ffom_hist, p.k_hist, p.reason_hist);
+    k_outer_cgs<<<p.nblk, 512, sm2, p.st>>>(p, j, 0, p.h1);
+    k_reduce_cols<<<rgrid, 32 * wpb, 0, p.st>>>(p, ncols, p.h2);
+    k_outer_cgs<<<p.nblk, 512, (size_t)(j + 1) * sizeof(double), p.st>>>(p, j, 1, p.h2);
+    k_outer_givens<<<p.P, 32, 0, p.st>>>(p, j);
     g_launches += 6;
 }
 
-// y = R^{-1} g over the rotated J x J triangle (one warp).
-__global__ void k_final_y(int J, int ldH, const double* __restrict__ H, const double* __restrict__ g,
-                          double* __restrict__ y) {
+// Per problem flagged "finalise now" (one warp): y = R^{-1} g over the rotated J x J triangle, J = the problem's
+// outer iteration count.
+__global__ void k_final_y(const Plan P) {
     extern __shared__ double rhs[];
+    const int p = blockIdx.x;
+    if (!(P.pflag[p] & 2)) return;
+    const int ldo = P.jmax + 1, J = P.ost[p].j;
+    const double* H = P.H + (int64_t)p * ldo * P.jmax;
+    const double* g = P.g + (int64_t)p * ldo;
+    double* y = P.yo + (int64_t)p * P.jmax;
     const int lane = threadIdx.x;
     for (int l = lane; l < J; l += 32) rhs[l] = g[l];
     __syncwarp();
     for (int l = J - 1; l >= 0; --l) {
-        const double yl = rhs[l] / H[(int64_t)l * ldH + l];
-        for (int q = lane; q < l; q += 32) rhs[q] -= H[(int64_t)l * ldH + q] * yl;
+        const double yl = rhs[l] / H[(int64_t)l * ldo + l];
+        for (int q = lane; q < l; q += 32) rhs[q] -= H[(int64_t)l * ldo + q] * yl;
         if (lane == 0) y[l] = yl;
         __syncwarp();
     }
 }
 
-__global__ void __launch_bounds__(256) k_final_x(int n, int J, const double* __restrict__ Z,
-                                                 const double* __restrict__ y, const double* __restrict__ x0,
+// x = x0 + Z y over the blocks of flagged problems.
+__global__ void __launch_bounds__(256) k_final_x(const Plan P, const double* __restrict__ x0,
                                                  double* __restrict__ x) {
-    __shared__ double yy[1024];
-    for (int l = threadIdx.x; l < J; l += blockDim.x) yy[l] = y[l];
+    __shared__ double yy[kMaxM];
+    const BlockInfo bi = block_info(P, blockIdx.x);
+    const int p = bi.prob;
+    if (!(P.pflag[p] & 2)) return;
+    const int J = P.ost[p].j, N = P.N;
+    for (int l = threadIdx.x; l < J; l += blockDim.x) yy[l] = P.yo[(int64_t)p * P.jmax + l];
     __syncthreads();
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = threadIdx.x; k < bi.len; k += blockDim.x) {
+        const int64_t r = bi.v0 + k;
         double acc = x0 ? x0[r] : 0.0;
-        for (int l = 0; l < J; ++l) acc += yy[l] * Z[(int64_t)l * n + r];
+        for (int l = 0; l < J; ++l) acc += yy[l] * P.Z[(int64_t)l * N + r];
         x[r] = acc;
     }
 }
 
 void launch_final_x(const Plan& p, int J, const double* x0, double* x) {
-    k_final_y<<<1, 32, (size_t)std::max(J, 1) * sizeof(double), p.st>>>(J, p.jmax + 1, p.H, p.g, p.yo);
-    const int th = 256;
-    const int gr = (int)std::min<int64_t>(((int64_t)p.n + th - 1) / th, 152 * 8);
-    k_final_x<<<gr, th, 0, p.st>>>(p.n, J, p.Z, p.yo, x0, x);
+    k_final_y<<<p.P, 32, (size_t)std::max(J, 1) * sizeof(double), p.st>>>(p);
+    k_final_x<<<p.nblk, 256, 0, p.st>>>(p, x0, x);
     g_launches += 2;
 }
 
 template <int V, int U>
 __global__ void __launch_bounds__(512, 2)
-    k_spmv_plain(int n, int Bn, const int* __restrict__ rp, const int* __restrict__ col,
-                 const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+    k_spmv_plain(const Plan P, const double* __restrict__ x, double* __restrict__ y) {
     extern __shared__ double yb[];
-    const int b = blockIdx.x;
-    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
-    spmv_rows_to_smem<V, U, double, double, double>(rp, col, val, x, r0, r1, yb);
+    const BlockInfo bi = block_info(P, blockIdx.x);
+    const int m0 = bi.v0 - bi.cs;
+    spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, x + bi.cs, m0, m0 + bi.len, yb);
     __syncthreads();
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) y[r] = yb[r - r0];
+    for (int k = threadIdx.x; k < bi.len; k += blockDim.x) y[bi.v0 + k] = yb[k];
 }
 
 void launch_spmv_f64(const Plan& p, const double* x, double* y) {
     const size_t sm = (size_t)p.Bn * sizeof(double);
-    SFG_SPMV_DISPATCH(p.vec, (set_smem((const void*)k_spmv_plain<VV, UU>, sm), k_spmv_plain<VV, UU><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.rp, p.col, p.val, x, y)));
+    SFG_SPMV_DISPATCH(p.vec, (set_smem((const void*)k_spmv_plain<VV, UU>, sm),
+                              k_spmv_plain<VV, UU><<<p.nblk, 512, sm, p.st>>>(p, x, y)));
     ++g_launches;
 }
 

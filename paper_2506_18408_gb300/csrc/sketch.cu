@@ -1,10 +1,10 @@
 // Sparse-sign subspace embedding S (Eq. 1; Clarkson-Woodruff when zeta = 1, Section 4.1) on the device.
 //
-// S is never stored densely.  Its pattern is drawn once per sketch size from SplitMix64 (counter form, see
-// sketch_column in common.cuh) and regrouped into *gather lists*: for each row block b of the vectors (the same
-// blocks the fused inner kernel uses) and each sketch row r, the list of (local offset, sign) of the columns j in
-// block b with S_rj != 0.  A kernel that holds block b of a vector in shared memory then forms its partial S x by
-// summing each sketch row's list in a fixed order -- deterministic, no atomics on floating-point data.
+// S is never stored densely.  Each system's pattern is drawn once per sketch size from SplitMix64 (counter form, see
+// sketch_column in common.cuh) and regrouped into *gather lists*: for each row block of the system (the blocks the
+// fused inner kernel uses) and each sketch row r, the list of (local offset, sign) of the columns j in the block
+// with S_rj != 0.  A kernel that holds the block of a vector in shared memory then forms its partial S x by summing
+// each sketch row's list in a fixed order -- deterministic, no atomics on floating-point data.
 #include "kernels.h"
 
 #include <algorithm>
@@ -43,23 +43,23 @@ __global__ void k_sketch_pattern(int n, int s, int zeta, int kind, uint64_t seed
     }
 }
 
-void launch_sketch_pattern(const Plan&, int n, int s, int zeta, int kind, uint64_t seed, int* rows, int8_t* neg,
+void launch_sketch_pattern(int n, int s, int zeta, int kind, uint64_t seed, int* rows, int8_t* neg,
                            cudaStream_t st) {
     k_sketch_pattern<<<(n + 255) / 256, 256, 0, st>>>(n, s, zeta, kind, seed, rows, neg);
     ++g_launches;
 }
 
-// counts[b*s + r] = number of nonzeros of sketch row r among the columns of block b
-__global__ void k_seg_count(int n, int s, int zeta, int Bn, const int* __restrict__ rows, int* __restrict__ counts) {
+// counts[k*s + r] = number of nonzeros of sketch row r among the columns of block k (Bq columns per block)
+__global__ void k_seg_count(int n, int s, int zeta, int Bq, const int* __restrict__ rows, int* __restrict__ counts) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    const int b = (int)(j / Bn);
-    for (int l = 0; l < zeta; ++l) atomicAdd(counts + (int64_t)b * s + rows[j * zeta + l], 1);
+    const int k = (int)(j / Bq);
+    for (int l = 0; l < zeta; ++l) atomicAdd(counts + (int64_t)k * s + rows[j * zeta + l], 1);
 }
 
-// Exclusive prefix sum of the list lengths rounded up to multiples of 8 (counts[0..len)) into seg[0..len], so every
-// list starts on a 16-byte boundary (single block; len up to a few million).
-__global__ void k_scan_single(const int* __restrict__ counts, int* __restrict__ seg, int len) {
+// seg[0..len] = base + exclusive prefix sum of the list lengths rounded up to multiples of 8 (counts[0..len)), so
+// every list starts on a 16-byte boundary (single block).
+__global__ void k_scan_single(const int* __restrict__ counts, int* __restrict__ seg, int len, int base) {
     __shared__ int sums[1024];
     const int tid = threadIdx.x, T = blockDim.x;
     const int chunk = (len + T - 1) / T;
@@ -74,12 +74,12 @@ __global__ void k_scan_single(const int* __restrict__ counts, int* __restrict__ 
         sums[tid] += v;
         __syncthreads();
     }
-    int run = sums[tid] - local;
+    int run = base + sums[tid] - local;
     for (int i = a; i < bnd; ++i) {
         seg[i] = run;
         run += (counts[i] + 7) & ~7;
     }
-    if (tid == T - 1) seg[len] = sums[T - 1];
+    if (tid == T - 1) seg[len] = base + sums[T - 1];
 }
 
 __global__ void k_fill_u16(int64_t cnt, uint16_t v, uint16_t* __restrict__ o) {
@@ -87,27 +87,27 @@ __global__ void k_fill_u16(int64_t cnt, uint16_t v, uint16_t* __restrict__ o) {
         o[i] = v;
 }
 
-// Fill the gather lists of block b (one warp per block).  Entries of a list appear in the order
+// Fill the gather lists of block k (one warp per block).  Entries of a list appear in the order
 // (column chunk of 32, slot l, lane), which is fixed, so the sums formed from them are reproducible.
-__global__ void k_seg_fill(int n, int s, int zeta, int Bn, const int* __restrict__ rows,
+__global__ void k_seg_fill(int n, int s, int zeta, int Bq, const int* __restrict__ rows,
                            const int8_t* __restrict__ neg, const int* __restrict__ seg,
                            uint16_t* __restrict__ ent) {
     extern __shared__ int cursor[];
-    const int b = blockIdx.x, lane = threadIdx.x;
+    const int k = blockIdx.x, lane = threadIdx.x;
     for (int r = lane; r < s; r += 32) cursor[r] = 0;
     __syncwarp();
-    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
+    const int c0 = k * Bq, c1 = min(n, c0 + Bq);
     const unsigned lt = (1u << lane) - 1u;
-    for (int base = r0; base < r1; base += 32) {
+    for (int base = c0; base < c1; base += 32) {
         const int j = base + lane;
-        const bool ok = j < r1;
+        const bool ok = j < c1;
         for (int l = 0; l < zeta; ++l) {
             const int r = ok ? rows[(int64_t)j * zeta + l] : -1;
             const unsigned peers = __match_any_sync(0xffffffffu, r);
             if (ok) {
                 const int rank = __popc(peers & lt);
-                const int pos = seg[(int64_t)b * s + r] + cursor[r] + rank;
-                ent[pos] = (uint16_t)((j - r0) | (neg[(int64_t)j * zeta + l] ? 0x8000 : 0));
+                const int pos = seg[(int64_t)k * s + r] + cursor[r] + rank;
+                ent[pos] = (uint16_t)((j - c0) | (neg[(int64_t)j * zeta + l] ? 0x8000 : 0));
             }
             __syncwarp();
             if (ok && lane == __ffs(peers) - 1) cursor[r] += __popc(peers);
@@ -116,49 +116,57 @@ __global__ void k_seg_fill(int n, int s, int zeta, int Bn, const int* __restrict
     }
 }
 
-void launch_sketch_count(int n, int s, int zeta, int Bn, int nblk, const int* rows, int* counts, int* seg,
-                         cudaStream_t st) {
-    k_seg_count<<<(n + 255) / 256, 256, 0, st>>>(n, s, zeta, Bn, rows, counts);
-    k_scan_single<<<1, 1024, 0, st>>>(counts, seg, nblk * s);
-    g_launches += 2;
+void launch_sketch_count(int n, int s, int zeta, int Bq, const int* rows, int* counts, cudaStream_t st) {
+    k_seg_count<<<(n + 255) / 256, 256, 0, st>>>(n, s, zeta, Bq, rows, counts);
+    ++g_launches;
 }
 
-void launch_sketch_fill(int n, int s, int zeta, int Bn, int nblk, const int* rows, const int8_t* neg,
-                        const int* seg, uint16_t* ent, int64_t total, cudaStream_t st) {
-    k_fill_u16<<<(int)std::min<int64_t>((total + 8 + 255) / 256, 4096), 256, 0, st>>>(total + 8, (uint16_t)Bn,
-                                                                                        ent);
-    k_seg_fill<<<nblk, 32, s * sizeof(int), st>>>(n, s, zeta, Bn, rows, neg, seg, ent);
-    g_launches += 2;
+void launch_list_scan(const int* counts, int* seg, int len, cudaStream_t st) {
+    k_scan_single<<<1, 1024, 0, st>>>(counts, seg, len, 0);
+    ++g_launches;
 }
 
-// Per-block partial sketch of xs = xscale * x; optionally stores (VT)xs into dst.  The value fed to the sketch is
+void launch_sketch_fill(int n, int s, int zeta, int Bq, const int* rows, const int8_t* neg, const int* seg,
+                        uint16_t* ent, cudaStream_t st) {
+    const int nl = (n + Bq - 1) / Bq;
+    k_seg_fill<<<nl, 32, s * sizeof(int), st>>>(n, s, zeta, Bq, rows, neg, seg, ent);
+    ++g_launches;
+}
+
+void launch_fill_u16(int64_t cnt, uint16_t v, uint16_t* out, cudaStream_t st) {
+    k_fill_u16<<<(int)std::min<int64_t>((cnt + 255) / 256, 4096), 256, 0, st>>>(cnt, v, out);
+    ++g_launches;
+}
+
+// Per-block partial sketch of xs = scale_p * x; optionally stores (VT)xs into dst.  The value fed to the sketch is
 // the stored (rounded) one, so S is applied to exactly the vector kept in the basis.  One thread per sketch row
 // walks its gather list; FP64 data are summed exactly in 64-bit fixed point, FP32 data in list order.
 template <typename VT, typename AT>
-__global__ void __launch_bounds__(512) k_sketch_partials(int n, int Bn, int s, int H, const double* __restrict__ x,
-                                                         const double* __restrict__ xscale, VT* __restrict__ dst,
-                                                         const int* __restrict__ seg,
-                                                         const uint16_t* __restrict__ ent, AT* __restrict__ part) {
+__global__ void __launch_bounds__(512) k_sketch_partials(const Plan P, const double* __restrict__ x,
+                                                         const double* __restrict__ xscale, int xstride,
+                                                         VT* __restrict__ dst, AT* __restrict__ part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AT* xb = reinterpret_cast<AT*>(smem_raw);
     __shared__ int emax_sh[32];
     const int b = blockIdx.x;
-    const int r0 = b * Bn, r1 = min(n, r0 + Bn);
-    const double sc = xscale ? *xscale : 1.0;
+    const BlockInfo bi = block_info(P, b);
+    if (P.pflag[bi.prob] & 1) return;
+    const int s = P.s, Bn = P.Bn;
+    const double sc = xscale ? xscale[(int64_t)bi.prob * xstride] : 1.0;
     int emax = 1;
     for (int r = threadIdx.x; r <= Bn; r += blockDim.x) {
         AT v = AT(0);
-        if (r < r1 - r0) {
-            v = (AT)(sc * x[r0 + r]);
+        if (r < bi.len) {
+            v = (AT)(sc * x[bi.v0 + r]);
             if (dst) {
-                store_as(dst + r0 + r, v);
+                store_as(dst + bi.v0 + r, v);
                 v = stored_value(v, dst);
             }
         }
         xb[r] = v;
         emax = max(emax, exp_of(v));
     }
-    const int* sg = seg + (int64_t)b * s;
+    const int* sg = P.seg + (int64_t)bi.list * s;
     if constexpr (sizeof(AT) == 8) {
         emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
         if ((threadIdx.x & 31) == 0) emax_sh[threadIdx.x >> 5] = emax;
@@ -166,56 +174,63 @@ __global__ void __launch_bounds__(512) k_sketch_partials(int n, int Bn, int s, i
         int Eb = 1;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) Eb = max(Eb, emax_sh[q]);
         long long* qb = reinterpret_cast<long long*>(xb);
-        for (int r = threadIdx.x; r <= Bn; r += blockDim.x) qb[r] = to_fixed((double)xb[r], Eb, H);
+        for (int r = threadIdx.x; r <= Bn; r += blockDim.x) qb[r] = to_fixed((double)xb[r], Eb, P.sk_headroom);
         __syncthreads();
-        const double unit = fixed_unit(0.0, Eb, H);
+        const double unit = fixed_unit(0.0, Eb, P.sk_headroom);
         const bool bad = exp_nonfinite(0.0, Eb);
         for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
-            const long long v = sum_list(ent, sg[rr], sg[rr + 1], qb);
+            const long long v = sum_list(P.ent, sg[rr], sg[rr + 1], qb);
             part[(int64_t)b * s + rr] = bad ? (AT)NAN : (AT)((double)v * unit);
         }
     } else {
         __syncthreads();
-        for (int rr = threadIdx.x; rr < s; rr += blockDim.x) part[(int64_t)b * s + rr] = sum_list(ent, sg[rr], sg[rr + 1], xb);
+        for (int rr = threadIdx.x; rr < s; rr += blockDim.x)
+            part[(int64_t)b * s + rr] = sum_list(P.ent, sg[rr], sg[rr + 1], xb);
     }
 }
 
-void launch_sketch_partials(const Plan& p, const double* x, const double* xscale_dev, void* dst, void* part) {
+void launch_sketch_partials(const Plan& p, const double* x, const double* xscale, int xstride, void* dst,
+                            void* part) {
     const size_t sm = (size_t)(p.Bn + 1) * (p.prec == kFP64 ? 8 : 4);
     if (p.prec == kFP64) {
         set_smem((const void*)k_sketch_partials<double, double>, sm);
-        k_sketch_partials<double, double><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.s, p.sk_headroom, x, xscale_dev,
-                                                                    (double*)dst, p.seg, p.ent, (double*)part);
+        k_sketch_partials<double, double><<<p.nblk, 512, sm, p.st>>>(p, x, xscale, xstride, (double*)dst,
+                                                                    (double*)part);
     } else if (p.prec == kFP32) {
         set_smem((const void*)k_sketch_partials<float, float>, sm);
-        k_sketch_partials<float, float><<<p.nblk, 512, sm, p.st>>>(p.n, p.Bn, p.s, p.sk_headroom, x, xscale_dev,
-                                                                  (float*)dst, p.seg, p.ent, (float*)part);
+        k_sketch_partials<float, float><<<p.nblk, 512, sm, p.st>>>(p, x, xscale, xstride, (float*)dst,
+                                                                  (float*)part);
     } else {
         set_smem((const void*)k_sketch_partials<__nv_bfloat16, float>, sm);
-        k_sketch_partials<__nv_bfloat16, float><<<p.nblk, 512, sm, p.st>>>(
-            p.n, p.Bn, p.s, p.sk_headroom, x, xscale_dev, (__nv_bfloat16*)dst, p.seg, p.ent, (float*)part);
+        k_sketch_partials<__nv_bfloat16, float><<<p.nblk, 512, sm, p.st>>>(p, x, xscale, xstride,
+                                                                          (__nv_bfloat16*)dst, (float*)part);
     }
     ++g_launches;
 }
 
+// out[p*s + r] = sk_scale * sum over the blocks of problem p of part[b*s + r] (block order).
 template <typename AT>
-__global__ void k_sketch_reduce(int nblk, int s, double scale, const AT* __restrict__ part, double* __restrict__ out,
+__global__ void k_sketch_reduce(const Plan P, const AT* __restrict__ part, double* __restrict__ out,
                                 double* __restrict__ out2) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= s) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = P.s;
+    if (t >= (int64_t)P.P * s) return;
+    const int p = (int)(t / s), r = (int)(t % s);
+    if (P.pflag[p] & 1) return;
     AT acc = AT(0);
-    for (int b = 0; b < nblk; ++b) acc += part[(int64_t)b * s + r];
-    const double v = scale * (double)acc;
-    out[r] = v;
-    if (out2) out2[r] = v;
+    for (int b = P.prob_b0[p]; b < P.prob_b0[p + 1]; ++b) acc += part[(int64_t)b * s + r];
+    const double v = P.sk_scale * (double)acc;
+    out[t] = v;
+    if (out2) out2[t] = v;
 }
 
 void launch_sketch_reduce(const Plan& p, const void* part, double* out, double* out2) {
-    const int th = 128, gr = (p.s + th - 1) / th;
+    const int64_t tot = (int64_t)p.P * p.s;
+    const int th = 128, gr = (int)((tot + th - 1) / th);
     if (p.prec == kFP64)
-        k_sketch_reduce<double><<<gr, th, 0, p.st>>>(p.nblk, p.s, p.sk_scale, (const double*)part, out, out2);
+        k_sketch_reduce<double><<<gr, th, 0, p.st>>>(p, (const double*)part, out, out2);
     else
-        k_sketch_reduce<float><<<gr, th, 0, p.st>>>(p.nblk, p.s, p.sk_scale, (const float*)part, out, out2);
+        k_sketch_reduce<float><<<gr, th, 0, p.st>>>(p, (const float*)part, out, out2);
     ++g_launches;
 }
 

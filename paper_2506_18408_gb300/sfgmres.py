@@ -23,12 +23,13 @@ OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NAN = -1, -2, -3, -4
 CSR_HOST = 1
 OPT_PRECISION, OPT_ZETA, OPT_COND_THRESHOLD, OPT_C3, OPT_MAX_OUTER, OPT_SKETCH_KIND, OPT_PROFILE, \
-    OPT_SPMV_VECTOR = range(1, 9)
+    OPT_SPMV_VECTOR, OPT_BLOCK_ROWS, OPT_GRAPH = range(1, 11)
+SOLVE_TRANSPOSE = 1
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SKETCH_KIND = {"sparse_sign": 0, "identity": 1}
 
-EXPORTED = ["sfgmres_create", "sfgmres_set_option", "sfgmres_get_option", "sfgmres_solve",
-            "sfgmres_solve_transpose", "sfgmres_update_values", "sfgmres_pattern_outer", "sfgmres_inner_cycle",
+EXPORTED = ["sfgmres_create", "sfgmres_create_batch", "sfgmres_set_option", "sfgmres_get_option", "sfgmres_solve",
+            "sfgmres_solve_transpose", "sfgmres_solve_batch", "sfgmres_update_values", "sfgmres_pattern_outer", "sfgmres_inner_cycle",
             "sfgmres_sketch_apply", "sfgmres_sketch_apply_noalloc", "sfgmres_sketch_pattern", "sfgmres_spmv",
             "sfgmres_destroy", "sfgmres_last_error", "sfgmres_version"]
 
@@ -41,6 +42,13 @@ class Stats(C.Structure):
                 ("t_inner_spmv_ms", C.c_double), ("n_inner_spmv", C.c_int64), ("t_inner_axpy_ms", C.c_double),
                 ("n_inner_axpy", C.c_int64), ("t_qr_ms", C.c_double), ("n_qr", C.c_int64),
                 ("t_total_ms", C.c_double)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("problems", C.c_int32), ("lockstep_outer", C.c_int32), ("total_inner", C.c_int64),
+                ("status", C.POINTER(C.c_int32)), ("outer_iters", C.POINTER(C.c_int32)),
+                ("rel_res_true", C.POINTER(C.c_double)), ("rel_res_est", C.POINTER(C.c_double)),
+                ("kernel_launches", C.c_int64), ("t_total_ms", C.c_double)]
 
 
 _lib = None
@@ -56,10 +64,12 @@ def load():
     lib = C.CDLL(LIB_PATH)
     vp, i32, i64, f64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint64
     lib.sfgmres_create.argtypes = [C.POINTER(vp), i64, i64, vp, vp, vp, u64, i32, vp]
+    lib.sfgmres_create_batch.argtypes = [C.POINTER(vp), i32, vp, i64, vp, vp, vp, u64, i32, vp]
     lib.sfgmres_set_option.argtypes = [vp, i32, f64]
     lib.sfgmres_get_option.argtypes = [vp, i32, C.POINTER(f64)]
     lib.sfgmres_solve.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, C.POINTER(Stats)]
     lib.sfgmres_solve_transpose.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, C.POINTER(Stats)]
+    lib.sfgmres_solve_batch.argtypes = [vp, i32, vp, vp, vp, i32, i32, i32, f64, i32, C.POINTER(BatchStats)]
     lib.sfgmres_update_values.argtypes = [vp, vp]
     lib.sfgmres_pattern_outer.argtypes = [vp, vp, vp, f64, vp]
     lib.sfgmres_inner_cycle.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, C.POINTER(i32), C.POINTER(i32)]
@@ -124,6 +134,18 @@ def sfgmres_create(n: int, nnz: int, row_ptr, col_idx, vals, sketch_seed: int, f
     return h.value
 
 
+def sfgmres_create_batch(sys_n, nnz: int, row_ptr, col_idx, vals, sketch_seed: int, flags: int = 0,
+                         stream: Optional[int] = None) -> int:
+    lib = load()
+    sn = np.ascontiguousarray(sys_n, dtype=np.int64)
+    h = C.c_void_p()
+    rc = lib.sfgmres_create_batch(C.byref(h), len(sn), _ptr(sn), nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
+                                  sketch_seed, flags, stream)
+    if rc != 0:
+        raise SFGMRESError(rc, lib.sfgmres_last_error(None).decode())
+    return h.value
+
+
 def sfgmres_set_option(h: int, key: int, value: float) -> None:
     _check(h, load().sfgmres_set_option(h, key, float(value)))
 
@@ -143,6 +165,12 @@ def sfgmres_solve_transpose(h: int, b, x0, x, m: int, s: int, k: int, tol: float
                             stats: Optional[Stats] = None) -> int:
     return _check(h, load().sfgmres_solve_transpose(h, _ptr(b), _ptr(x0), _ptr(x), m, s, k, tol,
                                                     C.byref(stats) if stats is not None else None))
+
+
+def sfgmres_solve_batch(h: int, nrhs: int, b, x0, x, m: int, s: int, k: int, tol: float, flags: int = 0,
+                        stats: Optional[BatchStats] = None) -> int:
+    return _check(h, load().sfgmres_solve_batch(h, nrhs, _ptr(b), _ptr(x0), _ptr(x), m, s, k, tol, flags,
+                                                C.byref(stats) if stats is not None else None))
 
 
 def sfgmres_update_values(h: int, vals) -> None:
@@ -190,7 +218,8 @@ def sfgmres_last_error(h: Optional[int]) -> str:
 
 # ---- convenience wrapper -------------------------------------------------------------------------------------------
 class Solver:
-    """A solver handle for one CSR matrix.
+    """A solver handle for one CSR matrix, or for a batch of systems given as one block-diagonal CSR matrix (``n`` a
+    list of the systems' orders; see ``sfgmres_create_batch``).
 
     ``row_ptr``/``col``/``val`` may be NumPy arrays (host; copied by the library) or CUDA tensors (int64, int32,
     float64).  ``options`` are set through :meth:`set` (``precision`` in {"fp64","fp32","bf16"}, ``zeta``,
@@ -200,12 +229,15 @@ class Solver:
 
     _KEYS = {"precision": OPT_PRECISION, "zeta": OPT_ZETA, "cond_threshold": OPT_COND_THRESHOLD, "c3": OPT_C3,
              "max_outer": OPT_MAX_OUTER, "sketch_kind": OPT_SKETCH_KIND, "profile": OPT_PROFILE,
-             "spmv_vector": OPT_SPMV_VECTOR}
+             "spmv_vector": OPT_SPMV_VECTOR, "block_rows": OPT_BLOCK_ROWS, "graph": OPT_GRAPH}
 
-    def __init__(self, n: int, row_ptr, col, val, sketch_seed: int = 1, stream=None, **options):
+    def __init__(self, n, row_ptr, col, val, sketch_seed: int = 1, stream=None, **options):
         import torch
 
-        self.n = int(n)
+        sys_n = [int(v) for v in np.atleast_1d(np.asarray(n))]
+        self.sys_n = sys_n
+        self.nsys = len(sys_n)
+        self.n = int(sum(sys_n))
         host = isinstance(row_ptr, np.ndarray)
         if host:
             row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
@@ -215,7 +247,11 @@ class Solver:
         if stream is None and torch.cuda.is_available():
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream
-        self.h = sfgmres_create(self.n, nnz, row_ptr, col, val, sketch_seed, CSR_HOST if host else 0, stream)
+        if self.nsys == 1:
+            self.h = sfgmres_create(self.n, nnz, row_ptr, col, val, sketch_seed, CSR_HOST if host else 0, stream)
+        else:
+            self.h = sfgmres_create_batch(sys_n, nnz, row_ptr, col, val, sketch_seed, CSR_HOST if host else 0,
+                                          stream)
         self.nnz = nnz
         for key, v in options.items():
             self.set(key, v)
@@ -258,6 +294,31 @@ class Solver:
                 "t_inner_spmv_ms": st.t_inner_spmv_ms, "n_inner_spmv": st.n_inner_spmv,
                 "t_inner_axpy_ms": st.t_inner_axpy_ms, "n_inner_axpy": st.n_inner_axpy, "t_qr_ms": st.t_qr_ms,
                 "n_qr": st.n_qr}
+        return out, info
+
+    def solve_batch(self, b, x0=None, *, nrhs: int, m: int, s: int, k: int, tol: float = 1e-8, out=None,
+                    transpose: bool = False):
+        """Solve for ``nrhs`` right-hand sides per system at once; ``b``/``x0``/``out`` hold ``nrhs * n`` values in
+        problem order (system-major, then right-hand side).  Returns ``(x, info)`` with per-problem lists."""
+        import torch
+
+        if out is None:
+            out = torch.empty_like(b) if hasattr(b, "data_ptr") else np.empty_like(b)
+        P = self.nsys * nrhs
+        st = BatchStats()
+        sa = (C.c_int32 * P)()
+        oa = (C.c_int32 * P)()
+        ra = (C.c_double * P)()
+        ea = (C.c_double * P)()
+        st.status = C.cast(sa, C.POINTER(C.c_int32))
+        st.outer_iters = C.cast(oa, C.POINTER(C.c_int32))
+        st.rel_res_true = C.cast(ra, C.POINTER(C.c_double))
+        st.rel_res_est = C.cast(ea, C.POINTER(C.c_double))
+        rc = sfgmres_solve_batch(self.h, nrhs, b, x0, out, m, s, k, tol, SOLVE_TRANSPOSE if transpose else 0, st)
+        info = {"status": rc, "problems": st.problems, "lockstep_outer": st.lockstep_outer,
+                "total_inner": st.total_inner, "status_p": list(sa), "outer_iters_p": list(oa),
+                "rel_res_true_p": list(ra), "rel_res_est_p": list(ea), "kernel_launches": st.kernel_launches,
+                "t_total_ms": st.t_total_ms}
         return out, info
 
     def update_values(self, vals) -> None:

@@ -109,3 +109,49 @@ def test_zipf_2m_solve_reaches_tol(zipf, prec):
     x, info = sv.solve(dev_vec(b), m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
     assert info["status"] == 0
     assert _rel_res(A.to_scipy(), b, x.cpu().numpy()) <= cfg.tol
+
+
+def test_batch_512_fp32_all_problems_reach_tol_and_sampled_match_oracle():
+    """The batched workload at full size (512 systems x 4 right-hand sides = 2048 problems, 176.6M unknowns; FP32
+    inner, FP64 outer) in the launch configuration bench.py times: every problem's residual recomputed on the CPU
+    is <= 1e-8, and three sampled problems (the smallest system, the largest, and a median one) match the oracle's
+    FP32-inner solve in outer iteration count (+-1)."""
+    import scipy.sparse as sp
+
+    from paper_2506_18408_gb300 import Solver
+
+    cfg = workloads.CONFIGS["batch_512"]
+    A = cfg.build_matrix()
+    b = cfg.build_rhs(A.n)
+    sv = Solver(list(A.sys_n), A.row_ptr, A.col, A.val, sketch_seed=cfg.sketch_seed, zeta=cfg.zeta,
+                max_outer=cfg.max_outer, precision=cfg.precision)
+    x, info = sv.solve_batch(dev_vec(b), nrhs=cfg.nrhs, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
+    sv.close()
+    x = x.cpu().numpy()
+    torch.cuda.empty_cache()
+    assert info["status"] == 0 and info["problems"] == 2048
+    # every residual, recomputed with scipy: the problems of right-hand side r form one column of an n x 4 block
+    sl = workloads.problem_slices(A.sys_n, cfg.nrhs)
+    n = A.n
+    off = np.concatenate([[0], np.cumsum(A.sys_n)])
+    X = np.empty((n, cfg.nrhs))
+    Bm = np.empty((n, cfg.nrhs))
+    for p, (q, a, nq) in enumerate(sl):
+        r = p % cfg.nrhs
+        X[off[q]:off[q] + nq, r] = x[a:a + nq]
+        Bm[off[q]:off[q] + nq, r] = b[a:a + nq]
+    R = Bm - sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(n, n)) @ X
+    rr = np.sqrt(np.add.reduceat(R * R, off[:-1], axis=0))
+    bb = np.sqrt(np.add.reduceat(Bm * Bm, off[:-1], axis=0))
+    rel = rr / bb
+    assert rel.max() <= cfg.tol, rel.max()
+    # sampled problems against the oracle with the same inner precision
+    blocks = workloads.split_blocks(A)
+    order = np.argsort(A.sys_n, kind="stable")
+    for q in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        p = q * cfg.nrhs
+        _, a, nq = sl[p]
+        ref = ofg.fgmres(blocks[q].to_scipy(), b[a:a + nq], m=cfg.m, s=cfg.s, t=cfg.t, tol=cfg.tol,
+                         max_outer=cfg.max_outer, inner="fp32")
+        assert ref.status == ofg.CONVERGED
+        assert abs(info["outer_iters_p"][p] - ref.outer_iters) <= 1, (q, info["outer_iters_p"][p], ref.outer_iters)

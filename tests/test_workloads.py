@@ -66,3 +66,40 @@ def test_rhs_streams_independent():
     assert not np.allclose(a, b)
     u = workloads.rhs(1000, seed=0, dist="uniform")
     assert u.min() >= -1 and u.max() <= 1
+
+
+def test_block_diag_round_trip_and_problem_slices():
+    mats = [workloads.convdiff(5, (1.0, 2.0)), workloads.random_zipf(40, seed=1), workloads.convdiff(3, (0.0,))]
+    A = workloads.block_diag(mats)
+    assert A.n == sum(M.n for M in mats) and A.nnz == sum(M.nnz for M in mats)
+    assert list(A.sys_n) == [M.n for M in mats]
+    D = A.to_scipy().toarray()
+    off = 0
+    for M in mats:
+        blk = D[off:off + M.n, off:off + M.n]
+        np.testing.assert_array_equal(blk, M.to_scipy().toarray())
+        D[off:off + M.n, off:off + M.n] = 0.0
+        off += M.n
+    assert not D.any()  # nothing outside the diagonal blocks
+    for M, B in zip(mats, workloads.split_blocks(A)):
+        np.testing.assert_array_equal(B.row_ptr, M.row_ptr)
+        np.testing.assert_array_equal(B.col, M.col)
+        np.testing.assert_array_equal(B.val, M.val)
+    sl = workloads.problem_slices(A.sys_n, 3)
+    assert [q for q, _, _ in sl] == [0, 0, 0, 1, 1, 1, 2, 2, 2]
+    starts = [a for _, a, _ in sl]
+    lens = [n for _, _, n in sl]
+    assert starts[0] == 0 and all(a + n == a2 for a, n, a2 in zip(starts, lens, starts[1:]))
+    assert starts[-1] + lens[-1] == 3 * A.n
+
+
+def test_convdiff_batch_recipe():
+    A = workloads.convdiff_batch(40, 32, 512, 50.0, seed=0)
+    N = np.sqrt(A.sys_n).round().astype(np.int64)
+    assert np.all(N * N == A.sys_n) and N.min() >= 32 and N.max() <= 512
+    # 5-point stencil: nnz = 5 N^2 - 4 N per system
+    assert A.nnz == int(np.sum(5 * N * N - 4 * N))
+    b = workloads.batch_rhs(A.sys_n, 4, seed=0)
+    assert b.shape == (4 * A.n,)
+    cfg = workloads.CONFIGS["batch_512"]
+    assert (cfg.nrhs, cfg.m, cfg.t, cfg.s, cfg.precision) == (4, 40, 2, 160, "fp32")

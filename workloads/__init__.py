@@ -15,6 +15,10 @@ Generators
   diagonal, ``L-1`` distinct uniformly random off-diagonal columns, values ``N(0,1)``, diagonal set to ``1.2`` times
   the absolute off-diagonal row sum (strictly diagonally dominant, hence nonsingular).
 * :func:`rhs` -- right-hand sides ``N(0,1)`` or ``U(-1,1)``.
+* :func:`convdiff_batch` -- a batch of independent 2D convection-diffusion systems with grid sides uniform in
+  ``[nmin, nmax]`` and ``beta ~ U(0, beta_max)^2`` per system, returned as one block-diagonal CSR matrix
+  (:func:`block_diag`) with the systems' orders in ``CSR.sys_n``; :func:`batch_rhs` draws ``nrhs`` right-hand sides
+  per system in problem order (system-major, then right-hand side).
 
 Every generator draws from ``numpy.random.default_rng([seed, stream])`` with a fixed stream tag per purpose, so the
 same ``seed`` gives independent streams for ``A``, ``b``, ``x*`` and batch parameters.
@@ -24,7 +28,7 @@ CSR arrays are returned as ``(row_ptr int64[n+1], col int32[nnz], val float64[nn
 from __future__ import annotations
 
 import dataclasses
-from typing import Dict, Tuple
+from typing import Dict, List, Optional, Tuple
 
 import numpy as np
 
@@ -42,6 +46,7 @@ class CSR:
     row_ptr: np.ndarray  # int64[n+1]
     col: np.ndarray  # int32[nnz]
     val: np.ndarray  # float64[nnz]
+    sys_n: Optional[np.ndarray] = None  # orders of the diagonal blocks of a batch (None: one system)
 
     @property
     def nnz(self) -> int:
@@ -142,6 +147,57 @@ def rhs(n: int, seed: int = 0, dist: str = "normal", stream: int = STREAM_RHS, n
     raise ValueError(dist)
 
 
+def block_diag(mats: List[CSR]) -> CSR:
+    """The block-diagonal matrix diag(A_0, A_1, ...) in CSR (global column indices), with ``sys_n`` set."""
+    sys_n = np.asarray([A.n for A in mats], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(sys_n)])
+    noff = np.concatenate([[0], np.cumsum([A.nnz for A in mats])])
+    row_ptr = np.concatenate([[0]] + [A.row_ptr[1:] + noff[q] for q, A in enumerate(mats)]).astype(np.int64)
+    col = np.concatenate([A.col.astype(np.int64) + off[q] for q, A in enumerate(mats)]).astype(np.int32)
+    val = np.concatenate([A.val for A in mats])
+    return CSR(int(off[-1]), row_ptr, col, val, sys_n)
+
+
+def split_blocks(A: CSR) -> List[CSR]:
+    """The diagonal blocks of a block-diagonal CSR built by :func:`block_diag` (local column indices)."""
+    out = []
+    off = 0
+    for nq in A.sys_n:
+        nq = int(nq)
+        a, e = int(A.row_ptr[off]), int(A.row_ptr[off + nq])
+        out.append(CSR(nq, A.row_ptr[off:off + nq + 1] - a, (A.col[a:e].astype(np.int64) - off).astype(np.int32),
+                       A.val[a:e].copy()))
+        off += nq
+    return out
+
+
+def convdiff_batch(nsys: int, nmin: int = 32, nmax: int = 512, beta_max: float = 50.0, seed: int = 0) -> CSR:
+    """Batch of 2D upwind convection-diffusion systems (see module docstring), block-diagonal CSR."""
+    rng = np.random.default_rng([seed, STREAM_BATCH])
+    sides = rng.integers(nmin, nmax + 1, size=nsys)
+    betas = rng.uniform(0.0, beta_max, size=(nsys, 2))
+    return block_diag([convdiff(int(N), betas[q]) for q, N in enumerate(sides)])
+
+
+def batch_rhs(sys_n, nrhs: int, seed: int = 0, dist: str = "normal") -> np.ndarray:
+    """``nrhs`` right-hand sides per system in problem order: problem ``p = q * nrhs + r`` occupies the ``sys_n[q]``
+    entries starting at ``nrhs * off_q + r * sys_n[q]``; one N(0,1) (or U(-1,1)) draw of the whole vector."""
+    total = int(np.sum(sys_n)) * nrhs
+    return rhs(total, seed=seed, dist=dist, stream=STREAM_RHS)
+
+
+def problem_slices(sys_n, nrhs: int):
+    """(system, start, length) of every problem of a batch, in problem order."""
+    out = []
+    off = 0
+    for q, nq in enumerate(sys_n):
+        nq = int(nq)
+        for r in range(nrhs):
+            out.append((q, nrhs * off + r * nq, nq))
+        off += nq
+    return out
+
+
 @dataclasses.dataclass
 class Config:
     """One solver workload: matrix recipe, right-hand side recipe and sGMRES/FGMRES parameters.
@@ -160,6 +216,8 @@ class Config:
     tol: float = 1e-8
     max_outer: int = 50
     seed: int = 0
+    nrhs: int = 1
+    precision: str = "fp64"
 
     def build_matrix(self) -> CSR:
         kind = self.matrix[0]
@@ -169,9 +227,17 @@ class Config:
         if kind == "zipf":
             _, n = self.matrix
             return random_zipf(n, seed=self.seed)
+        if kind == "convdiff_batch":
+            _, nsys, nmin, nmax, beta_max = self.matrix
+            return convdiff_batch(nsys, nmin, nmax, beta_max, seed=self.seed)
         raise ValueError(kind)
 
     def build_rhs(self, n: int) -> np.ndarray:
+        """Right-hand side(s): ``(n,)`` for one system and one right-hand side, else ``nrhs * n`` values in problem
+        order."""
+        if self.matrix[0] == "convdiff_batch" or self.nrhs > 1:
+            return batch_rhs([n] if self.matrix[0] != "convdiff_batch" else self.build_matrix().sys_n, self.nrhs,
+                             seed=self.seed, dist=self.rhs_dist)
         return rhs(n, seed=self.seed, dist=self.rhs_dist)
 
 
@@ -184,4 +250,11 @@ CONFIGS: Dict[str, Config] = {
     "zipf_2m": Config("zipf_2m", ("zipf", 2_000_000), "uniform", m=60, t=4, s=240),
     # 3D convection-diffusion 64^3 (adjoint workload); m=50, t=2, s=200
     "cd3d_64": Config("cd3d_64", ("convdiff", 64, (50.0, 30.0, 10.0)), "normal", m=50, t=2, s=200),
+    # batch: 512 2D convection-diffusion systems, sides U{32..512}, beta ~ U(0,50)^2, 4 right-hand sides each;
+    # m=40, t=2, s=160, FP32 inner cycles with the FP64 outer FGMRES
+    # (the 512^2 systems with weak convection need ~45 outer iterations, hence max_outer = 60)
+    "batch_512": Config("batch_512", ("convdiff_batch", 512, 32, 512, 50.0), "normal", m=40, t=2, s=160, nrhs=4,
+                        precision="fp32", max_outer=60),
+    # small batch of the same recipe (sides 16..48, 12 systems, 3 right-hand sides) for oracle parity
+    "batch_small": Config("batch_small", ("convdiff_batch", 12, 16, 48, 50.0), "normal", m=40, t=2, s=160, nrhs=3),
 }
