@@ -261,6 +261,9 @@ def run_batch(args, dev, stream):
     xd = torch.empty_like(bd)
     del b
     P = len(A.sys_n) * cfg.nrhs
+    t0 = time.perf_counter()
+    tile = sv.autotune(nrhs=cfg.nrhs, m=cfg.m, s=cfg.s, k=cfg.t)  # row-block size and SpMV width, outside the timing
+    tune_s = time.perf_counter() - t0
     kw = dict(nrhs=cfg.nrhs, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol, out=xd)
     for _ in range(args.batch_warmup):
         sv.solve_batch(bd, **kw)
@@ -283,7 +286,8 @@ def run_batch(args, dev, stream):
             "warmup": args.batch_warmup, "problems": P, "unknowns": int(A.n) * cfg.nrhs, "nnz": int(A.nnz),
             "converged": int(sum(1 for v in st if v == 0)), "lockstep_outer": info["lockstep_outer"],
             "max_outer": max(info["outer_iters_p"]), "total_inner": info["total_inner"],
-            "max_rel_res_true": max(info["rel_res_true_p"]), "kernel_launches": info["kernel_launches"]}
+            "max_rel_res_true": max(info["rel_res_true_p"]), "kernel_launches": info["kernel_launches"],
+            "autotune": {"block_rows": tile[0], "spmv_vector": tile[1], "step_ms": tile[2], "tune_s": tune_s}}
 
 
 def cpu_baseline(outer_iters):

@@ -190,6 +190,20 @@ SFGMRES_API int sfgmres_solve_batch(sfgmres_t h, int32_t nrhs, const double* b, 
                                     int32_t m, int32_t s, int32_t k, double tol, int32_t flags,
                                     sfgmres_batch_stats* st);
 
+/* Autotune the launch shape of the fused inner kernels for this handle: for each candidate row-block size (the
+ * default rule's size and a ladder of multiples of 32 between 256 and 8192) and, for matrices with rows longer than
+ * 16 entries, each sub-warp width of the inner SpMV (8 or 32 lanes per row), time short inner sGMRES cycles
+ * (min(m, 8) steps, C1/C2 only, a constant unit start vector for every problem, best of two timed runs after a
+ * warm-up) with nrhs right-hand sides per system, and keep the fastest per inner step.  The choice is stored in the options
+ * SFGMRES_OPT_BLOCK_ROWS and SFGMRES_OPT_SPMV_VECTOR (the method's arithmetic is unchanged; only the order of block
+ * partial sums follows the block size).  The paper has no counterpart: this picks GB300 tile shapes.
+ *   nrhs, m, s, k       the solve parameters to tune for
+ *   block_rows_out, spmv_vector_out (host int32, may be NULL): the chosen sizes
+ *   step_ms_out         (host double, may be NULL): the measured time of one inner step (all problems), ms
+ * Returns SFGMRES_OK or an error (the options are then left unchanged). */
+SFGMRES_API int sfgmres_autotune(sfgmres_t h, int32_t nrhs, int32_t m, int32_t s, int32_t k, int32_t* block_rows_out,
+                                 int32_t* spmv_vector_out, double* step_ms_out);
+
 /* Replace the stored values of A (same sparsity pattern, same order as at sfgmres_create): vals is float64[nnz],
  * host or device.  The FP32 copy and the transpose's values follow. */
 SFGMRES_API int sfgmres_update_values(sfgmres_t h, const double* vals);

@@ -1270,6 +1270,89 @@ int sfgmres_solve_batch(sfgmres_t h, int32_t nrhs, const double* b, const double
     return status;
 }
 
+int sfgmres_autotune(sfgmres_t h, int32_t nrhs, int32_t m, int32_t s, int32_t k, int32_t* block_rows_out,
+                     int32_t* spmv_vector_out, double* step_ms_out) {
+    if (!h) return SFGMRES_ERR_INVALID_ARG;
+    if (nrhs < 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "nrhs must be >= 1");
+    int rc = check_params(h, m, s, k);
+    if (rc) return rc;
+    CK(cudaSetDevice(h->dev));
+    // candidate row-block sizes: the default rule's size and a ladder of smaller and larger ones (multiples of 32)
+    std::vector<int> cand;
+    int maxn = 0;
+    for (int q = 0; q < h->nsys; ++q) maxn = std::max(maxn, h->sys_n[q]);
+    const int base = (h->nsys == 1) ? single_block_rows(h->n, h->sms) : kBatchBlockRows;
+    for (int v : {base, base / 2, base / 4, base / 8, 512, 1024, 2048, 4096, 8192}) {
+        v = std::min(kBlockRowsMax, std::max(256, (v / 32) * 32));
+        if (v > ((maxn + 31) / 32) * 32 && v != base) continue;  // larger than every system: same as smaller ones
+        if (std::find(cand.begin(), cand.end(), v) == cand.end()) cand.push_back(v);
+    }
+    // candidate lanes per row: the default rule's choice, and the sub-warp widths for matrices with long rows
+    std::vector<int> vecs = {0};
+    if (h->maxlen > 16)
+        for (int v : {8, 32}) vecs.push_back(v);  // the inner kernel has 8- and 32-lane variants
+    const int save_block = h->block_rows, save_vec = h->vec_opt, save_graph = h->use_graph;
+    const int steps = std::min(m, 8);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = INFINITY;
+    int best_b = save_block, best_v = save_vec;
+    for (int bq : cand) {
+        h->block_rows = bq;
+        set_list_geometry(h);
+        for (int vv : vecs) {
+            h->vec_opt = vv;
+            h->vec = vv ? vv : choose_vec(h->nnz, h->n, h->maxlen);
+            Plan P;
+            Geo* g = nullptr;
+            if ((rc = prepare(h, nrhs, steps, s, k, 0, &P, &g))) break;
+            // a unit-norm start vector for every problem (the timing does not depend on its values)
+            if ((rc = ensure(h, h->bst, (size_t)P.N * 8))) break;
+            if ((rc = ensure(h, h->xst, (size_t)P.N * 8))) break;
+            double* v0 = (double*)h->bst.p;
+            k_fill<<<grid_for(P.N), 256, 0, h->st>>>(P.N, 1.0 / std::sqrt((double)std::max(1, maxn)), v0);
+            float tbest = INFINITY;
+            for (int rep = 0; rep < 3 && rc == 0; ++rep) {
+                cudaEventRecord(e0, h->st);
+                rc = run_cycle(h, P, -1, v0, nullptr, 0, 0, (double*)h->xst.p);
+                cudaEventRecord(e1, h->st);
+                if (cudaStreamSynchronize(h->st) != cudaSuccess) rc = fail(h, SFGMRES_ERR_CUDA, "autotune run failed");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tbest = std::min(tbest, ms);  // the first run is a warm-up
+            }
+            if (rc) break;
+            const double per_step = tbest / steps;
+            if (per_step < best) {
+                best = per_step;
+                best_b = bq;
+                best_v = vv;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->use_graph = save_graph;
+    if (rc) {  // leave the handle as it was
+        h->block_rows = save_block;
+        h->vec_opt = save_vec;
+        h->vec = save_vec ? save_vec : choose_vec(h->nnz, h->n, h->maxlen);
+        set_list_geometry(h);
+        return rc;
+    }
+    h->block_rows = best_b;
+    h->vec_opt = best_v;
+    h->vec = best_v ? best_v : choose_vec(h->nnz, h->n, h->maxlen);
+    set_list_geometry(h);
+    if (block_rows_out) *block_rows_out = h->sys_Bq.empty() ? 0 : h->sys_Bq[0];
+    if (spmv_vector_out) *spmv_vector_out = h->vec;
+    if (step_ms_out) *step_ms_out = best;
+    CK(cudaGetLastError());
+    return SFGMRES_OK;
+}
+
 int sfgmres_update_values(sfgmres_t h, const double* vals) {
     if (!h) return SFGMRES_ERR_INVALID_ARG;
     if (!vals && h->nnz > 0) return fail(h, SFGMRES_ERR_INVALID_ARG, "vals must not be NULL");

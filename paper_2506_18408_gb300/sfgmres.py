@@ -29,7 +29,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SKETCH_KIND = {"sparse_sign": 0, "identity": 1}
 
 EXPORTED = ["sfgmres_create", "sfgmres_create_batch", "sfgmres_set_option", "sfgmres_get_option", "sfgmres_solve",
-            "sfgmres_solve_transpose", "sfgmres_solve_batch", "sfgmres_update_values", "sfgmres_pattern_outer", "sfgmres_inner_cycle",
+            "sfgmres_solve_transpose", "sfgmres_solve_batch", "sfgmres_autotune", "sfgmres_update_values", "sfgmres_pattern_outer", "sfgmres_inner_cycle",
             "sfgmres_sketch_apply", "sfgmres_sketch_apply_noalloc", "sfgmres_sketch_pattern", "sfgmres_spmv",
             "sfgmres_destroy", "sfgmres_last_error", "sfgmres_version"]
 
@@ -70,6 +70,7 @@ def load():
     lib.sfgmres_solve.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, C.POINTER(Stats)]
     lib.sfgmres_solve_transpose.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, C.POINTER(Stats)]
     lib.sfgmres_solve_batch.argtypes = [vp, i32, vp, vp, vp, i32, i32, i32, f64, i32, C.POINTER(BatchStats)]
+    lib.sfgmres_autotune.argtypes = [vp, i32, i32, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(f64)]
     lib.sfgmres_update_values.argtypes = [vp, vp]
     lib.sfgmres_pattern_outer.argtypes = [vp, vp, vp, f64, vp]
     lib.sfgmres_inner_cycle.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, C.POINTER(i32), C.POINTER(i32)]
@@ -171,6 +172,13 @@ def sfgmres_solve_batch(h: int, nrhs: int, b, x0, x, m: int, s: int, k: int, tol
                         stats: Optional[BatchStats] = None) -> int:
     return _check(h, load().sfgmres_solve_batch(h, nrhs, _ptr(b), _ptr(x0), _ptr(x), m, s, k, tol, flags,
                                                 C.byref(stats) if stats is not None else None))
+
+
+def sfgmres_autotune(h: int, nrhs: int, m: int, s: int, k: int):
+    """Time candidate row-block sizes / SpMV widths and keep the fastest; returns (block_rows, spmv_vector, step_ms)."""
+    b, v, t = C.c_int32(), C.c_int32(), C.c_double()
+    _check(h, load().sfgmres_autotune(h, nrhs, m, s, k, C.byref(b), C.byref(v), C.byref(t)), allow_positive=False)
+    return b.value, v.value, t.value
 
 
 def sfgmres_update_values(h: int, vals) -> None:
@@ -320,6 +328,11 @@ class Solver:
                 "rel_res_true_p": list(ra), "rel_res_est_p": list(ea), "kernel_launches": st.kernel_launches,
                 "t_total_ms": st.t_total_ms}
         return out, info
+
+    def autotune(self, *, m: int, s: int, k: int, nrhs: int = 1):
+        """Pick the row-block size and SpMV width by timing short inner cycles; returns ``(block_rows, spmv_vector,
+        step_ms)``."""
+        return sfgmres_autotune(self.h, nrhs, m, s, k)
 
     def update_values(self, vals) -> None:
         """Replace the stored values of A (same pattern and order)."""

@@ -200,3 +200,25 @@ def test_graph_replay_and_eager_launches_give_identical_results(small):
         for x, it, ks in outs[1:]:
             assert np.array_equal(x, outs[0][0])
             assert it == outs[0][1] and ks == outs[0][2]
+
+
+def test_autotune_picks_a_valid_shape_and_solves_stay_correct(small):
+    cfg, A, b = small
+    sv = _solver(A, max_outer=cfg.max_outer)
+    br, vec, step_ms = sv.autotune(nrhs=cfg.nrhs, m=cfg.m, s=cfg.s, k=cfg.t)
+    assert 256 <= br <= 8192 and br % 32 == 0 and step_ms > 0
+    assert sv.get("block_rows") == br
+    x, info = sv.solve_batch(dev_vec(b), nrhs=cfg.nrhs, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
+    x = x.cpu().numpy()
+    assert info["status"] == 0
+    for Aq, bp, xp in _per_problem(A, cfg.nrhs, b, x):
+        assert _rel_res(Aq, bp, xp) <= cfg.tol
+    Z = workloads.random_zipf(30_000, seed=3)  # long rows: the SpMV width is tuned too
+    from paper_2506_18408_gb300 import Solver
+
+    sz = Solver(Z.n, Z.row_ptr, Z.col, Z.val, sketch_seed=1)
+    br, vec, _ = sz.autotune(m=20, s=80, k=4)
+    assert vec in (1, 2, 4, 8, 16, 32)
+    bz = workloads.rhs(Z.n, seed=1)
+    xz, iz = sz.solve(dev_vec(bz), m=20, s=80, k=4, tol=1e-8)
+    assert iz["status"] == 0 and _rel_res(Z, bz, xz.cpu().numpy()) <= 1e-8
