@@ -62,7 +62,11 @@ extern "C" {
 #define SFGMRES_OPT_MAX_OUTER 5      /* outer FGMRES iteration budget (default 50) */
 #define SFGMRES_OPT_SKETCH_KIND 6    /* 0 = sparse-sign (default), 1 = identity (requires s == n; tests) */
 #define SFGMRES_OPT_PROFILE 7        /* 1 = time the kernels with CUDA events (see sfgmres_stats), default 0 */
-#define SFGMRES_OPT_SPMV_VECTOR 8    /* lanes per CSR row in the SpMV (2,4,8,16,32); 0 = chosen from nnz/n */
+#define SFGMRES_OPT_SPMV_VECTOR 8    /* lanes per CSR row in the SpMV (2,4,8,16,32), or 0 (default) = chosen by the
+                                        library: one thread per row when no row has more than 16 entries, else the
+                                        length-binned SpMV (each row block's rows ordered by length: short rows one
+                                        thread each, 17..64 entries 8 lanes, longer rows a warp).  Reading it
+                                        returns the shape in use: 1, 2..32, or 0 for the length-binned SpMV. */
 #define SFGMRES_OPT_BLOCK_ROWS 9     /* rows per row block of the fused inner kernels: a multiple of 32 in
                                         [32, 8192], or 0 (default) = chosen by the library (one system: about a
                                         multiple of the SM count of blocks; several systems: 4096).  Reading it
@@ -72,7 +76,12 @@ extern "C" {
                                         are kept while the solve's parameters and workspaces stay the same.  0: the
                                         kernels are launched one by one.  Results are identical either way.
                                         SFGMRES_OPT_PROFILE = 1 launches one by one. */
-
+#define SFGMRES_OPT_RHS_GROUP 11     /* sfgmres_solve_batch with nrhs > 1 on a matrix whose rows have at most 16
+                                        entries: right-hand sides of one system served by one CTA of the fused inner
+                                        SpMV, which then reads A and the sketch lists once for all of them; 1
+                                        (default, not grouped) .. 4 (3 runs as 4).  Only the order of the block
+                                        partial sums differs from 1.  On GB300 the latency-bound inner kernel runs
+                                        slower grouped (measured), hence the default. */
 /* ---- sfgmres_solve_batch flags ---------------------------------------------------------------------------- */
 #define SFGMRES_SOLVE_TRANSPOSE 1    /* solve A_q^T x = b for every problem (see sfgmres_solve_transpose) */
 

@@ -42,6 +42,8 @@ struct Geo {
     int P = 0, N = 0, nblk = 0;
     DevBuf tab;  // int: blk_v0, blk_len, blk_cs, blk_list, blk_prob [nblk each], prob_b0 [P+1], pflag [P]
     uint64_t used = 0;
+    int grpG = 0, ngrp = 0;  // groups of G right-hand sides' blocks (grouped inner SpMV)
+    DevBuf grp;              // int: grp_b, grp_n, grp_st [ngrp each]
 };
 
 constexpr int kGeoCache = 4;
@@ -82,6 +84,7 @@ struct sfgmres_ctx {
     // options
     int prec = kFP64, zeta = 8, c3 = 1, max_outer = 50, kind = 0, profile = 0, vec_opt = 0, block_rows = 0;
     int use_graph = 1;
+    int rhs_group = 1;  // right-hand sides per grouped inner-SpMV CTA (1: not grouped)
     double cond_thr = 1e15;
 
     // list-block geometry (depends on the systems and the block-rows option; version bumps on change)
@@ -91,6 +94,14 @@ struct sfgmres_ctx {
     // vector-block geometries, cached per number of right-hand sides
     Geo geos[kGeoCache];
     uint64_t geo_clock = 0;
+
+    // length-binned SpMV row orders for A [0] and A^T [1] (built for one geometry version), and the matrix row
+    // blocks' first rows and lengths on the device
+    uint16_t* perm[2] = {nullptr, nullptr};
+    int* cls[2] = {nullptr, nullptr};
+    int bins_ver[2] = {-1, -1};
+    int* lb = nullptr;  // lb_m0 [nl], lb_len [nl]
+    int lb_ver = -1;
 
     // sketch gather lists (cached for one (s, zeta, kind, geometry version))
     int sk_s = -1, sk_zeta = -1, sk_kind = -1, sk_ver = -1, sk_headroom = 0;
@@ -188,16 +199,8 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Lanes per CSR row: one thread per row when every row is short (stencils), else a sub-warp sized by the mean.
-int choose_vec(int64_t nnz, int n, int maxlen) {
-    if (maxlen <= 16) return 1;
-    const double avg = n ? (double)nnz / n : 1.0;
-    if (avg <= 3.0) return 2;
-    if (avg <= 6.0) return 4;
-    if (avg <= 12.0) return 8;
-    if (avg <= 24.0) return 16;
-    return 32;
-}
+// SpMV shape: one thread per row when every row is short (stencils), else the length-binned SpMV (0).
+int choose_vec(int64_t, int, int maxlen) { return maxlen <= 16 ? 1 : 0; }
 
 // Row blocks of one system: nblk a multiple of the SM count where possible, Bn a multiple of 32, <= kBlockRowsMax.
 int single_block_rows(int n, int sms) {
@@ -414,6 +417,7 @@ int get_geometry(sfgmres_ctx* h, int nrhs, Geo** out) {
         tab.insert(tab.end(), pb0.begin(), pb0.end());
         tab.resize(tab.size() + P, 0);  // pflag
         g->nrhs = -1;
+        g->grpG = 0;
         int rc = ensure(h, g->tab, tab.size() * sizeof(int));
         if (rc) return rc;
         CK(cudaMemcpyAsync(g->tab.p, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
@@ -465,6 +469,35 @@ int ensure_transpose(sfgmres_ctx* h) {
     return 0;
 }
 
+// Row orders of the length-binned SpMV for A (or A^T), built for the current row-block geometry.
+int ensure_bins(sfgmres_ctx* h, bool transpose) {
+    const int t = transpose ? 1 : 0;
+    if (h->bins_ver[t] == h->geo_ver && h->perm[t]) return 0;
+    if (h->lb_ver != h->geo_ver) {
+        if (h->lb) cudaFree(h->lb);
+        h->lb = nullptr;
+        std::vector<int> hb(2 * (size_t)h->nl);
+        for (int q = 0; q < h->nsys; ++q) {
+            const int nq = h->sys_n[q], Bq = h->sys_Bq[q];
+            for (int k = 0, L = h->sys_l0[q]; k * Bq < nq; ++k, ++L) {
+                hb[L] = h->sys_moff[q] + k * Bq;
+                hb[h->nl + L] = std::min(Bq, nq - k * Bq);
+            }
+        }
+        CK(cudaMalloc(&h->lb, hb.size() * sizeof(int)));
+        CK(cudaMemcpy(h->lb, hb.data(), hb.size() * sizeof(int), cudaMemcpyHostToDevice));
+        h->lb_ver = h->geo_ver;
+    }
+    if (!h->perm[t]) CK(cudaMalloc(&h->perm[t], std::max<size_t>(h->n, 1) * sizeof(uint16_t)));
+    if (h->cls[t]) cudaFree(h->cls[t]);
+    h->cls[t] = nullptr;
+    CK(cudaMalloc(&h->cls[t], 2 * (size_t)h->nl * sizeof(int)));
+    launch_bin_rows(h->nl, transpose ? h->rpT : h->rp, h->lb, h->lb + h->nl, h->perm[t], h->cls[t], h->st);
+    CK(cudaGetLastError());
+    h->bins_ver[t] = h->geo_ver;
+    return 0;
+}
+
 // Matrix and geometry fields of a Plan (enough for the SpMV and the per-block helpers).
 void plan_geometry(sfgmres_ctx* h, const Geo* g, bool transpose, Plan& P) {
     P.nnz = h->nnz;
@@ -473,6 +506,8 @@ void plan_geometry(sfgmres_ctx* h, const Geo* g, bool transpose, Plan& P) {
     P.val = transpose ? h->valT : h->val;
     P.val32 = transpose ? h->val32T : h->val32;
     P.vec = transpose ? (h->vec_opt ? h->vec_opt : h->vecT) : h->vec;
+    P.perm = (P.vec == 0) ? h->perm[transpose ? 1 : 0] : nullptr;
+    P.cls = (P.vec == 0) ? h->cls[transpose ? 1 : 0] : nullptr;
     P.N = g->N;
     P.P = g->P;
     P.nblk = g->nblk;
@@ -491,6 +526,38 @@ void plan_geometry(sfgmres_ctx* h, const Geo* g, bool transpose, Plan& P) {
 
 int* pflag_of(const Geo* g) { return (int*)g->tab.p + 5 * (int64_t)g->nblk + g->P + 1; }
 
+// Groups of row blocks for the grouped inner SpMV: for every system and every matrix row block, the blocks of
+// right-hand sides r0 .. r0+G-1 (block index stride = the system's blocks per right-hand side).
+int ensure_groups(sfgmres_ctx* h, Geo* g, int G) {
+    if (g->grpG == G) return 0;
+    const int R = g->nrhs;
+    std::vector<int> gbv, gnv, gsv;
+    for (int q = 0; q < h->nsys; ++q) {
+        const int nlq = (h->sys_n[q] + h->sys_Bq[q] - 1) / h->sys_Bq[q];
+        // blocks of problem (q, r) start at prob_b0[q*R + r] = base_q + r * nlq
+        int base = 0;
+        for (int q2 = 0; q2 < q; ++q2) base += R * ((h->sys_n[q2] + h->sys_Bq[q2] - 1) / h->sys_Bq[q2]);
+        for (int r0 = 0; r0 < R; r0 += G)
+            for (int k = 0; k < nlq; ++k) {
+                gbv.push_back(base + r0 * nlq + k);
+                gnv.push_back(std::min(G, R - r0));
+                gsv.push_back(nlq);
+            }
+    }
+    std::vector<int> tab;
+    tab.insert(tab.end(), gbv.begin(), gbv.end());
+    tab.insert(tab.end(), gnv.begin(), gnv.end());
+    tab.insert(tab.end(), gsv.begin(), gsv.end());
+    g->grpG = 0;
+    int rc = ensure(h, g->grp, tab.size() * sizeof(int));
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(g->grp.p, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    g->grpG = G;
+    g->ngrp = (int)gbv.size();
+    return 0;
+}
+
 // Allocates the workspaces of a solve with nrhs right-hand sides per system and fills a Plan (for A, or for A^T
 // when transpose is set).  Every problem's flag is reset to "active".
 int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Geo** geo_out, bool transpose = false) {
@@ -500,6 +567,10 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     if ((rc = build_sketch(h, s))) return rc;
     if (transpose && (rc = ensure_transpose(h))) return rc;
     if (h->prec != kFP64 && (rc = ensure_f32(h, transpose))) return rc;
+    {
+        const int v = transpose ? (h->vec_opt ? h->vec_opt : h->vecT) : h->vec;
+        if (v == 0 && (rc = ensure_bins(h, transpose))) return rc;
+    }
     const size_t vt = (h->prec == kFP64) ? 8 : (h->prec == kFP32 ? 4 : 2);
     const size_t at = (h->prec == kFP64) ? 8 : 4;
     const size_t N = (size_t)g->N;
@@ -553,6 +624,22 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
 
     Plan& P = *p;
     plan_geometry(h, g, transpose, P);
+    // grouped inner SpMV for several right-hand sides of one-thread-per-row matrices
+    int G = 1;
+    if (nrhs > 1 && P.vec == 1 && h->rhs_group > 1) {
+        G = h->rhs_group;
+        G = std::min(G, nrhs);
+        if (G > 2) G = 4;  // kernels exist for groups of 2 and 4 (a group may hold fewer members)
+    }
+    if (G > 1) {
+        if ((rc = ensure_groups(h, g, G))) return rc;
+        const int* gt = (const int*)g->grp.p;
+        P.G = G;
+        P.ngrp = g->ngrp;
+        P.grp_b = gt;
+        P.grp_n = gt + g->ngrp;
+        P.grp_st = gt + 2 * (int64_t)g->ngrp;
+    }
     P.s = s;
     P.zeta = h->sk_zeta;
     P.kind = h->kind;
@@ -672,7 +759,8 @@ int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const doubl
 std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
     std::vector<uint64_t> k;
     auto u = [&](const void* p) { k.push_back((uint64_t)(uintptr_t)p); };
-    for (const void* p : std::initializer_list<const void*>{(const void*)P.rp, (const void*)P.col, (const void*)P.val, (const void*)P.val32,
+    for (const void* p : std::initializer_list<const void*>{(const void*)P.grp_b, (const void*)P.perm, (const void*)P.cls,
+                                                            (const void*)P.rp, (const void*)P.col, (const void*)P.val, (const void*)P.val32,
                           (const void*)P.blk_v0, (const void*)P.seg, (const void*)P.ent, P.U, P.W,
                           (const void*)P.sigma, P.normpart, P.hpart, P.cpart, (const void*)P.C, (const void*)P.Q,
                           (const void*)P.R, (const void*)P.d, (const void*)P.e, (const void*)P.c0,
@@ -684,7 +772,7 @@ std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
                           (const void*)P.ffom_hist, (const void*)P.k_hist, (const void*)P.reason_hist,
                           (const void*)P.ost, (const void*)P.st, (const void*)h->qst})
         u(p);
-    for (int64_t v : std::initializer_list<int64_t>{(int64_t)P.nnz, (int64_t)P.vec, (int64_t)P.N, (int64_t)P.P, (int64_t)P.nblk, (int64_t)P.Bn,
+    for (int64_t v : std::initializer_list<int64_t>{(int64_t)P.G, (int64_t)P.ngrp, (int64_t)P.nnz, (int64_t)P.vec, (int64_t)P.N, (int64_t)P.P, (int64_t)P.nblk, (int64_t)P.Bn,
                       (int64_t)P.s, (int64_t)P.zeta, (int64_t)P.kind, (int64_t)P.sk_headroom, (int64_t)P.prec,
                       (int64_t)P.m, (int64_t)P.t, (int64_t)P.qr_cluster, (int64_t)P.jmax, (int64_t)h->c3})
         k.push_back((uint64_t)v);
@@ -1111,13 +1199,21 @@ int sfgmres_destroy(sfgmres_t h) {
         if (q) cudaFree(q);
     if (h->seg) cudaFree(h->seg);
     if (h->ent) cudaFree(h->ent);
+    for (int t = 0; t < 2; ++t) {
+        if (h->perm[t]) cudaFree(h->perm[t]);
+        if (h->cls[t]) cudaFree(h->cls[t]);
+    }
+    if (h->lb) cudaFree(h->lb);
     DevBuf* bufs[] = {&h->U, &h->W, &h->sigma, &h->normpart, &h->hpart, &h->cpart, &h->C, &h->Q, &h->R, &h->d,
                       &h->e, &h->c0, &h->rho, &h->y, &h->coef, &h->hco, &h->cyc, &h->Vb, &h->Z, &h->nu, &h->Wo,
                       &h->opart, &h->npart, &h->npart2, &h->h1, &h->h2, &h->H, &h->cs, &h->sn, &h->g, &h->yo,
                       &h->est_hist, &h->ffom_hist, &h->k_hist, &h->reason_hist, &h->ost, &h->bst, &h->xst,
                       &h->x0st};
     for (DevBuf* b : bufs) release(*b);
-    for (Geo& g : h->geos) release(g.tab);
+    for (Geo& g : h->geos) {
+        release(g.tab);
+        release(g.grp);
+    }
     drop_graphs(h);
     release_host(h->h_ost);
     release_host(h->h_cyc);
@@ -1178,6 +1274,10 @@ int sfgmres_set_option(sfgmres_t h, int32_t key, double v) {
             h->vec_opt = iv;
             h->vec = iv ? iv : choose_vec(h->nnz, h->n, h->maxlen);
             return 0;
+        case SFGMRES_OPT_RHS_GROUP:
+            if (iv != v || iv < 1 || iv > 4) return fail(h, SFGMRES_ERR_INVALID_ARG, "rhs group must be 1..4");
+            h->rhs_group = iv;
+            return 0;
         case SFGMRES_OPT_GRAPH:
             if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "graph must be 0 or 1");
             h->use_graph = iv;
@@ -1208,6 +1308,7 @@ int sfgmres_get_option(sfgmres_t h, int32_t key, double* v) {
         case SFGMRES_OPT_SPMV_VECTOR: *v = h->vec; return 0;
         case SFGMRES_OPT_BLOCK_ROWS: *v = h->sys_Bq.empty() ? 0 : h->sys_Bq[0]; return 0;
         case SFGMRES_OPT_GRAPH: *v = h->use_graph; return 0;
+        case SFGMRES_OPT_RHS_GROUP: *v = h->rhs_group; return 0;
         default: return fail(h, SFGMRES_ERR_INVALID_ARG, "unknown option key");
     }
 }
@@ -1459,6 +1560,7 @@ int sfgmres_spmv(sfgmres_t h, const double* xv, double* yv) {
     Geo* g = nullptr;
     int rc = get_geometry(h, 1, &g);
     if (rc) return rc;
+    if (h->vec == 0 && (rc = ensure_bins(h, false))) return rc;
     Plan P;
     plan_geometry(h, g, false, P);
     launch_spmv_f64(P, xv, yv);

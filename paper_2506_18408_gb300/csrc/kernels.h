@@ -28,7 +28,9 @@ struct Plan {
     const int* col = nullptr;
     const double* val = nullptr;
     const float* val32 = nullptr;  // FP32 copy (inner FP32/BF16 modes)
-    int vec = 8;                   // SpMV lanes per row (1 = one thread per row)
+    int vec = 8;                   // SpMV lanes per row (1 = one thread per row, 0 = length-binned)
+    const uint16_t* perm = nullptr;  // length-binned SpMV: per matrix row block, its rows in length order
+    const int* cls = nullptr;        // [2 * list blocks]: rows with <= 16 entries, rows with <= 64 entries
 
     // problems and row blocks
     int N = 0;                     // total vector length (sum over problems)
@@ -42,6 +44,12 @@ struct Plan {
     const int* blk_prob = nullptr; // [nblk] problem
     const int* prob_b0 = nullptr;  // [P+1] blocks of problem p: prob_b0[p] .. prob_b0[p+1]
     const int* pflag = nullptr;    // [P] bit 0: done (skip), bit 1: finalise now
+    // groups of row blocks that are the same matrix rows of G right-hand sides of one system (the grouped inner
+    // SpMV reads A and the gather lists once per group): members grp_b[g] + j * grp_st[g], j < grp_n[g]
+    int G = 1, ngrp = 0;
+    const int* grp_b = nullptr;
+    const int* grp_n = nullptr;
+    const int* grp_st = nullptr;
 
     // sketch: for list block L and sketch row r the list ent[seg[L*s + r] .. seg[L*s + r + 1])
     int s = 0, zeta = 0, kind = 0;
@@ -110,6 +118,12 @@ __device__ __forceinline__ BlockInfo block_info(const Plan& p, int b) {
     return bi;
 }
 
+// Length-class boundaries of block b's rows for the length-binned SpMV (zero when the plan has none).
+__device__ __forceinline__ void block_bins(const Plan& p, const BlockInfo& bi, int& n0, int& n01) {
+    n0 = p.cls ? p.cls[2 * bi.list] : 0;
+    n01 = p.cls ? p.cls[2 * bi.list + 1] : 0;
+}
+
 // ---- sketch (sketch.cu) ----
 // Pattern of one system's sketch: rows[j*zeta + l], neg[j*zeta + l] for its n columns.
 void launch_sketch_pattern(int n, int s, int zeta, int kind, uint64_t seed, int* rows, int8_t* neg,
@@ -159,6 +173,11 @@ void launch_transpose(int n, int64_t nnz, const int* rp, const int* col, int* co
 void launch_gather_vals(int64_t nnz, const int* src, const double* val, double* out, cudaStream_t st);
 void launch_pattern_outer(int n, const int* rp, const int* col, const double* u, const double* v, double alpha,
                           double* out, cudaStream_t st);
+// Row order of every matrix row block (nl blocks, block L = rows lb_m0[L] .. + lb_len[L]) for the length-binned
+// SpMV: perm[m0 + i] = local offset of the i-th row in (class, length, position) order; cls[2L], cls[2L+1] = number
+// of rows with at most 16 and at most 64 entries.
+void launch_bin_rows(int nl, const int* rp, const int* lb_m0, const int* lb_len, uint16_t* perm, int* cls,
+                     cudaStream_t st);
 
 // Raise the dynamic shared-memory limit of kernel `func` to at least `bytes` (cached per kernel).
 void set_smem(const void* func, size_t bytes);

@@ -30,7 +30,10 @@ __global__ void __launch_bounds__(512, 2)
     if (only_final ? !(fl & 2) : (fl & 1)) return;
     if (x) {
         const int m0 = bi.v0 - bi.cs;
-        spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, x + bi.cs, m0, m0 + bi.len, axb);
+        int n0, n01;
+        block_bins(P, bi, n0, n01);
+        spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, x + bi.cs, m0, m0 + bi.len, axb, P.perm,
+                                                        n0, n01);
         __syncthreads();
     }
     double a1 = 0.0, a2 = 0.0;
@@ -129,7 +132,10 @@ __global__ void __launch_bounds__(512, 2) k_outer_spmv(const Plan P, int j) {
     if (outer_idle(P, bi.prob)) return;
     const double* z = P.Z + (int64_t)j * P.N;
     const int m0 = bi.v0 - bi.cs;
-    spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, z + bi.cs, m0, m0 + bi.len, wb);
+    int n0, n01;
+    block_bins(P, bi, n0, n01);
+    spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, z + bi.cs, m0, m0 + bi.len, wb, P.perm, n0,
+                                                    n01);
     __syncthreads();
     for (int k = threadIdx.x; k < bi.len; k += blockDim.x) P.Wo[bi.v0 + k] = wb[k];
     block_dots(P, bi, b, j, wb);
@@ -317,7 +323,10 @@ __global__ void __launch_bounds__(512, 2)
     extern __shared__ double yb[];
     const BlockInfo bi = block_info(P, blockIdx.x);
     const int m0 = bi.v0 - bi.cs;
-    spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, x + bi.cs, m0, m0 + bi.len, yb);
+    int n0, n01;
+    block_bins(P, bi, n0, n01);
+    spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, x + bi.cs, m0, m0 + bi.len, yb, P.perm, n0,
+                                                    n01);
     __syncthreads();
     for (int k = threadIdx.x; k < bi.len; k += blockDim.x) y[bi.v0 + k] = yb[k];
 }

@@ -111,4 +111,60 @@ void launch_pattern_outer(int n, const int* rp, const int* col, const double* u,
     ++g_launches;
 }
 
+// Length class of a row: its length for rows of at most 16 entries, 17 for 17..64 entries, 18 for longer rows.
+__device__ __forceinline__ int length_key(int len) { return len <= 16 ? len : (len <= 64 ? 17 : 18); }
+
+// One CTA (256 threads) per row block: counting sort of the block's rows by length key, stable (rows of equal key
+// keep their order), so the order -- and every sum formed in it -- is deterministic.
+__global__ void __launch_bounds__(256) k_bin_rows(const int* __restrict__ rp, const int* __restrict__ lb_m0,
+                                                  const int* __restrict__ lb_len, uint16_t* __restrict__ perm,
+                                                  int* __restrict__ cls) {
+    constexpr int NK = 19, NW = 8;
+    __shared__ int cnt[NK], cur[NK], wc[NW][NK];
+    const int L = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m0 = lb_m0[L], len = lb_len[L];
+    if (tid < NK) cnt[tid] = 0;
+    __syncthreads();
+    for (int k = tid; k < len; k += blockDim.x) atomicAdd(&cnt[length_key(rp[m0 + k + 1] - rp[m0 + k])], 1);
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int b = 0; b < NK; ++b) {
+            cur[b] = run;
+            run += cnt[b];
+        }
+        cls[2 * L] = cur[17];
+        cls[2 * L + 1] = cur[18];
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    for (int base = 0; base < len; base += blockDim.x) {
+        for (int q = tid; q < NW * NK; q += blockDim.x) wc[q / NK][q % NK] = 0;
+        __syncthreads();
+        const int k = base + tid;
+        const bool ok = k < len;
+        const int key = ok ? length_key(rp[m0 + k + 1] - rp[m0 + k]) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (ok && lane == __ffs(peers) - 1) wc[warp][key] = __popc(peers);
+        __syncthreads();
+        if (ok) {
+            int pos = cur[key] + __popc(peers & lt);
+            for (int w = 0; w < warp; ++w) pos += wc[w][key];
+            perm[m0 + pos] = (uint16_t)k;
+        }
+        __syncthreads();
+        if (tid < NK) {
+            int tot = 0;
+            for (int w = 0; w < NW; ++w) tot += wc[w][tid];
+            cur[tid] += tot;
+        }
+        __syncthreads();
+    }
+}
+
+void launch_bin_rows(int nl, const int* rp, const int* lb_m0, const int* lb_len, uint16_t* perm, int* cls,
+                     cudaStream_t st) {
+    k_bin_rows<<<nl, 256, 0, st>>>(rp, lb_m0, lb_len, perm, cls);
+    ++g_launches;
+}
+
 }  // namespace sfg

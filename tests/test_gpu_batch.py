@@ -218,7 +218,24 @@ def test_autotune_picks_a_valid_shape_and_solves_stay_correct(small):
 
     sz = Solver(Z.n, Z.row_ptr, Z.col, Z.val, sketch_seed=1)
     br, vec, _ = sz.autotune(m=20, s=80, k=4)
-    assert vec in (1, 2, 4, 8, 16, 32)
+    assert vec in (0, 1, 2, 4, 8, 16, 32)  # 0 = the length-binned SpMV
     bz = workloads.rhs(Z.n, seed=1)
     xz, iz = sz.solve(dev_vec(bz), m=20, s=80, k=4, tol=1e-8)
     assert iz["status"] == 0 and _rel_res(Z, bz, xz.cpu().numpy()) <= 1e-8
+
+
+@pytest.mark.parametrize("group,prec", [(2, "fp64"), (4, "fp32")])
+def test_rhs_grouped_inner_spmv_matches_ungrouped(small, group, prec):
+    """The grouped inner SpMV (several right-hand sides of a system per CTA) changes only the order of block partial
+    sums: the same outer counts and solutions agreeing far below the solve tolerance."""
+    cfg, A, b = small
+    sv = _solver(A, max_outer=cfg.max_outer, precision=prec)
+    x1, i1 = sv.solve_batch(dev_vec(b), nrhs=cfg.nrhs, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
+    sv.set("rhs_group", group)
+    x2, i2 = sv.solve_batch(dev_vec(b), nrhs=cfg.nrhs, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
+    assert i2["status"] == 0
+    assert all(abs(a - c) <= 1 for a, c in zip(i1["outer_iters_p"], i2["outer_iters_p"]))
+    x1, x2 = x1.cpu().numpy(), x2.cpu().numpy()
+    assert np.linalg.norm(x1 - x2) <= 1e-6 * np.linalg.norm(x1)
+    for Aq, bp, xp in _per_problem(A, cfg.nrhs, b, x2):
+        assert _rel_res(Aq, bp, xp) <= cfg.tol
