@@ -132,6 +132,10 @@ __global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __re
     if (stop_sh) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int s = P.s, Bn = P.Bn, N = P.N;
+    if (threadIdx.x == 32) {  // the block's sketch gather lists (contiguous), needed after the SpMV: into L2 now
+        const int la = P.seg[(int64_t)bi.list * s], lb = P.seg[(int64_t)bi.list * s + s];
+        prefetch_l2(P.ent + la, (size_t)(lb - la) * sizeof(uint16_t));
+    }
     const VT* Ub = (const VT*)P.U;
     AT* W = (AT*)P.W;
     const int lo = i - NW + 1;  // window u_lo..u_i (NW = min(t, i+1))
@@ -152,22 +156,31 @@ __global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __re
         emax = dots_pass<NW>(N, bi.v0, bi.len, Ub, lo, i, wblk, W, acc, nrm);
     }
     if (threadIdx.x == 0) wblk[Bn] = AT(0);
+    // block sums of ||u_i||^2 and the window dots in one round: each warp's sums (shuffle trees), then the warps'
+    // partials in warp order; the block's largest exponent of w' with them
     {
-        const AT v = block_sum_lean(nrm, red);
-        if (threadIdx.x == 0) ((AT*)P.normpart)[b] = v;
-    }
+        AT (*red2)[16] = reinterpret_cast<AT (*)[16]>(red);  // [NW + 1][16]
+        const AT v = warp_sum(nrm);
+        if (lane == 0) red2[0][warp] = v;
 #pragma unroll
-    for (int q = 0; q < NW; ++q) {
-        const AT v = block_sum_lean(acc[q], red);
-        if (threadIdx.x == 0) ((AT*)P.hpart)[(int64_t)b * kMaxTrunc + q] = v;
+        for (int q = 0; q < NW; ++q) {
+            const AT d = warp_sum(acc[q]);
+            if (lane == 0) red2[1 + q][warp] = d;
+        }
+        emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
+        if (lane == 0) emax_sh[warp] = emax;
+        __syncthreads();
+        if (threadIdx.x <= NW) {
+            AT t = AT(0);
+            for (int w = 0; w < nw; ++w) t += red2[threadIdx.x][w];
+            if (threadIdx.x == 0) ((AT*)P.normpart)[b] = t;
+            else ((AT*)P.hpart)[(int64_t)b * kMaxTrunc + threadIdx.x - 1] = t;
+        }
     }
     const int* sg = P.seg + (int64_t)bi.list * s;
     AT* cpart = (AT*)P.cpart;
     if constexpr (sizeof(AT) == 8) {
         // exact fixed-point sketch sums (integer adds; the FP64 pipe stays with the SpMV)
-        emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
-        if (lane == 0) emax_sh[warp] = emax;
-        __syncthreads();
         int Eb = 1;
         for (int q = 0; q < nw; ++q) Eb = max(Eb, emax_sh[q]);
         const int H = P.sk_headroom;
