@@ -212,6 +212,7 @@ def run_ours(args):
 
     solver.close()
     batch = None if args.no_batch else run_batch(args, dev, stream)
+    others = None if args.no_others else run_others(args, dev, stream)
     cpu = cpu_baseline(last["outer_iters"]) if (rank == 0 and not args.no_cpu) else None
     if rank == 0:
         res = {
@@ -236,6 +237,7 @@ def run_ours(args):
             "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n},
             "batch": batch,
+            "workloads": others,
             "gpu_launches": int(round(launches)) * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
@@ -243,6 +245,82 @@ def run_ours(args):
         print(json.dumps(res))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _event_time(fn, stream, K, W):
+    import torch
+
+    for _ in range(W):
+        fn()
+    ts, out = [], None
+    for _ in range(K):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.median(ts), out
+
+
+def run_others(args, dev, stream):
+    """The other workloads, each timed with CUDA events on the solver's stream (median of K after W warm-ups):
+    2D 64^2 (latency bound: microseconds per solve and solves per second), the random Zipf matrix (FP64, FP32
+    inner, BF16 basis), and the differentiation workload (3D 64^3, 16 right-hand sides: forward solves plus the
+    adjoint backward through torch.autograd)."""
+    import torch
+
+    from paper_2506_18408_gb300 import Solver, sfgmres_solve_autograd
+
+    out = {}
+    cfg = workloads.CONFIGS["cd2d_64"]
+    A = cfg.build_matrix()
+    bd = torch.from_numpy(cfg.build_rhs(A.n)).to(dev)
+    sv = Solver(A.n, A.row_ptr, A.col, A.val, sketch_seed=cfg.sketch_seed, max_outer=cfg.max_outer,
+                stream=stream.cuda_stream)
+    for prec in ("fp64", "fp32"):
+        sv.set("precision", prec)
+        sec, (_, info) = _event_time(lambda: sv.solve(bd, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol), stream, 20, 5)
+        out[f"cd2d_64_{prec}"] = {"us_per_solve": sec * 1e6, "solves_per_s": 1.0 / sec,
+                                  "outer_iters": info["outer_iters"], "total_inner": info["total_inner"],
+                                  "rel_res_true": info["rel_res_true"], "kernel_launches": info["kernel_launches"]}
+    sv.close()
+    cfg = workloads.CONFIGS["zipf_2m"]
+    A = cfg.build_matrix()
+    bd = torch.from_numpy(cfg.build_rhs(A.n)).to(dev)
+    sv = Solver(A.n, A.row_ptr, A.col, A.val, sketch_seed=cfg.sketch_seed, max_outer=cfg.max_outer,
+                stream=stream.cuda_stream)
+    for prec in ("fp64", "fp32", "bf16"):
+        sv.set("precision", prec)
+        sec, (_, info) = _event_time(lambda: sv.solve(bd, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol), stream, 3, 1)
+        out[f"zipf_2m_{prec}"] = {"s_per_solve": sec, "outer_iters": info["outer_iters"],
+                                  "total_inner": info["total_inner"], "rel_res_true": info["rel_res_true"],
+                                  "nnz": int(A.nnz)}
+    sv.close()
+    cfg = workloads.CONFIGS["cd3d_64"]
+    A = cfg.build_matrix()
+    B = torch.from_numpy(workloads.rhs(A.n, seed=0, nrhs=16)).to(dev)
+    xs = torch.from_numpy(workloads.rhs(A.n, seed=0, stream=workloads.STREAM_XSTAR, nrhs=16)).to(dev)
+    vals = torch.from_numpy(A.val).to(dev)
+    sv = Solver(A.n, A.row_ptr, A.col, A.val, sketch_seed=cfg.sketch_seed, max_outer=cfg.max_outer,
+                stream=stream.cuda_stream)
+
+    def fwd_bwd():
+        v = vals.clone().requires_grad_(True)
+        b = B.clone().requires_grad_(True)
+        x = sfgmres_solve_autograd(sv, v, b, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
+        loss = ((x - xs) ** 2).sum()
+        loss.backward()
+        return loss
+
+    for prec in ("fp64", "fp32"):
+        sv.set("precision", prec)
+        sec, _ = _event_time(fwd_bwd, stream, 3, 1)
+        out[f"cd3d_64_x16_grad_{prec}"] = {"s_forward_backward": sec, "rhs": 16}
+    sv.close()
+    return out
 
 
 def run_batch(args, dev, stream):
@@ -352,6 +430,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve line")
+    ap.add_argument("--no-others", action="store_true", help="skip the other workloads' lines")
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--batch-warmup", type=int, default=1)
     args = ap.parse_args()

@@ -82,6 +82,15 @@ extern "C" {
                                         (default, not grouped) .. 4 (3 runs as 4).  Only the order of the block
                                         partial sums differs from 1.  On GB300 the latency-bound inner kernel runs
                                         slower grouped (measured), hence the default. */
+#define SFGMRES_OPT_PERSISTENT 12    /* 1: for problems of at most 8 row blocks (one-thread-per-row matrices,
+                                        truncation k <= 4) each inner cycle runs as one persistent launch, a
+                                        cluster of up to 8 CTAs per problem doing every step, the least squares and
+                                        z = B y, with the reductions in distributed shared memory; a single system
+                                        of order n <= 65536 is then cut into 8 row blocks.  0 (default): one launch
+                                        per kernel and step (replayed from CUDA graphs), which measured faster on
+                                        GB300 for these sizes.  Both compute the method's sums; the order of the
+                                        cross-block sums differs.  SFGMRES_OPT_PROFILE = 1 uses the per-step
+                                        kernels. */
 /* ---- sfgmres_solve_batch flags ---------------------------------------------------------------------------- */
 #define SFGMRES_SOLVE_TRANSPOSE 1    /* solve A_q^T x = b for every problem (see sfgmres_solve_transpose) */
 

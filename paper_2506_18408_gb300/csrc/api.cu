@@ -42,6 +42,7 @@ struct Geo {
     int P = 0, N = 0, nblk = 0;
     DevBuf tab;  // int: blk_v0, blk_len, blk_cs, blk_list, blk_prob [nblk each], prob_b0 [P+1], pflag [P]
     uint64_t used = 0;
+    int maxbp = 0;           // largest number of blocks of one problem
     int grpG = 0, ngrp = 0;  // groups of G right-hand sides' blocks (grouped inner SpMV)
     DevBuf grp;              // int: grp_b, grp_n, grp_st [ngrp each]
 };
@@ -84,6 +85,7 @@ struct sfgmres_ctx {
     // options
     int prec = kFP64, zeta = 8, c3 = 1, max_outer = 50, kind = 0, profile = 0, vec_opt = 0, block_rows = 0;
     int use_graph = 1;
+    int persistent = 0;  // 1: whole-cycle persistent kernel where the plan allows it
     int rhs_group = 1;  // right-hand sides per grouped inner-SpMV CTA (1: not grouped)
     double cond_thr = 1e15;
 
@@ -224,6 +226,8 @@ void set_list_geometry(sfgmres_ctx* h) {
     h->sys_l0.assign(h->nsys + 1, 0);
     int Bq;
     if (h->block_rows) Bq = h->block_rows;
+    else if (h->nsys == 1 && h->persistent && h->n <= kPersistCluster * kBlockRowsMax)
+        Bq = std::max(32, ((h->n + kPersistCluster - 1) / kPersistCluster + 31) / 32 * 32);  // one cluster's blocks
     else if (h->nsys == 1) Bq = single_block_rows(h->n, h->sms);
     else Bq = kBatchBlockRows;
     int Bn = 32, nl = 0;
@@ -424,6 +428,8 @@ int get_geometry(sfgmres_ctx* h, int nrhs, Geo** out) {
         CK(cudaStreamSynchronize(h->st));
         g->nrhs = nrhs;
         g->ver = h->geo_ver;
+        g->maxbp = 0;
+        for (int p = 0; p < P; ++p) g->maxbp = std::max(g->maxbp, pb0[p + 1] - pb0[p]);
         g->P = P;
         g->N = (int)N64;
         g->nblk = nblk;
@@ -520,6 +526,7 @@ void plan_geometry(sfgmres_ctx* h, const Geo* g, bool transpose, Plan& P) {
     P.blk_list = t + 3 * (int64_t)nb;
     P.blk_prob = t + 4 * (int64_t)nb;
     P.prob_b0 = t + 5 * (int64_t)nb;
+    P.maxbp = g->maxbp;
     P.pflag = t + 5 * (int64_t)nb + g->P + 1;
     P.st = h->st;
 }
@@ -732,9 +739,21 @@ double ev_sum(const std::vector<EventPair>& pool, size_t count) {
 // configured), j < 0 standalone.  The sketched-QR update of step i runs on the side stream after step i's sketch
 // column is ready, overlapping the next step's SpMV; the main stream waits for the last QR update before the
 // least-squares solve.
+// Cluster size of the whole-cycle persistent kernel for this plan, or 0 where the per-step kernels run: small problems
+// (at most kPersistCluster row blocks each) with one thread per row and t <= 4, not profiled.
+int persistent_cluster(const sfgmres_ctx* h, const Plan& P) {
+    if (!h->persistent || h->profile || P.vec != 1 || P.t > 4 || P.maxbp < 1 || P.maxbp > kPersistCluster) return 0;
+    if (persistent_smem(P, P.maxbp) > 200 * 1024) return 0;
+    return P.maxbp;
+}
+
 int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const double* vscale, int vstride, int c3,
               double* z) {
     launch_cycle_start(P, j, v, vscale, vstride, c3, h->cond_thr);
+    if (const int nq = persistent_cluster(h, P)) {
+        CK(launch_cycle_persistent(P, nq, z));
+        return 0;
+    }
     for (int i = 0; i < P.m; ++i) {
         const bool last = (i == P.m - 1);
         if (h->profile) ev_begin(h, h->ev_spmv, h->n_spmv, h->st);
@@ -1278,6 +1297,13 @@ int sfgmres_set_option(sfgmres_t h, int32_t key, double v) {
             if (iv != v || iv < 1 || iv > 4) return fail(h, SFGMRES_ERR_INVALID_ARG, "rhs group must be 1..4");
             h->rhs_group = iv;
             return 0;
+        case SFGMRES_OPT_PERSISTENT:
+            if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "persistent must be 0 or 1");
+            if (iv != h->persistent) {
+                h->persistent = iv;
+                set_list_geometry(h);
+            }
+            return 0;
         case SFGMRES_OPT_GRAPH:
             if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "graph must be 0 or 1");
             h->use_graph = iv;
@@ -1309,6 +1335,7 @@ int sfgmres_get_option(sfgmres_t h, int32_t key, double* v) {
         case SFGMRES_OPT_BLOCK_ROWS: *v = h->sys_Bq.empty() ? 0 : h->sys_Bq[0]; return 0;
         case SFGMRES_OPT_GRAPH: *v = h->use_graph; return 0;
         case SFGMRES_OPT_RHS_GROUP: *v = h->rhs_group; return 0;
+        case SFGMRES_OPT_PERSISTENT: *v = h->persistent; return 0;
         default: return fail(h, SFGMRES_ERR_INVALID_ARG, "unknown option key");
     }
 }

@@ -43,6 +43,7 @@ struct Plan {
     const int* blk_list = nullptr; // [nblk] gather-list block
     const int* blk_prob = nullptr; // [nblk] problem
     const int* prob_b0 = nullptr;  // [P+1] blocks of problem p: prob_b0[p] .. prob_b0[p+1]
+    int maxbp = 0;                 // largest number of blocks of one problem
     const int* pflag = nullptr;    // [P] bit 0: done (skip), bit 1: finalise now
     // groups of row blocks that are the same matrix rows of G right-hand sides of one system (the grouped inner
     // SpMV reads A and the gather lists once per group): members grp_b[g] + j * grp_st[g], j < grp_n[g]
@@ -155,6 +156,14 @@ void launch_inner_axpy(const Plan& p, int i, bool last);
 cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st);  // cluster launch on stream st
 void launch_inner_finish(const Plan& p, double* z);  // y = R^{-1} d, z = sum_l y_l b_l (FP64)
 void launch_export_basis(const Plan& p, double* out, int count);  // out[l*N + r] = sigma_l * u_l[r] (FP64)
+
+// ---- persistent cycle (persistent.cu) ----
+// The whole inner cycle (all steps, least squares and z = B y) in one launch, one cluster of nq CTAs per problem
+// (nq = the largest number of row blocks of a problem, at most kPersistCluster); for plans with one thread per row
+// and t <= 4.
+constexpr int kPersistCluster = 8;
+size_t persistent_smem(const Plan& p, int nq);
+cudaError_t launch_cycle_persistent(const Plan& p, int nq, double* z);
 
 // ---- outer FGMRES and helpers (outer.cu) ----
 // rb = b - A x (x may be NULL = 0), npart/npart2 partials of ||rb||^2 and ||b||^2; rb may be NULL.
