@@ -169,19 +169,6 @@ __device__ __forceinline__ int exp_of(double w) {
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Bulk prefetch of [p, p + bytes) into L2 (cp.async.bulk.prefetch: a hint with no completion to wait for).  The range
-// is shrunk to whole 16-byte units inside it, so nothing outside the range is touched; issued by the calling thread.
-__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
-    uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
-    const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
-    while (a < e) {
-        const uint32_t n = (uint32_t)min((uintptr_t)(1u << 16), e - a);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
-        a += n;
-    }
-}
-
-// ------------------------------------------------------------------------------------------------------------
 // Sketch gather lists.  For row block b and sketch row r the list ent[seg[b*s + r] .. seg[b*s + r + 1]) holds one
 // 16-bit entry per nonzero S_rj with j in the block: bits 0..14 the offset of j in the block, bit 15 the sign.  Every
 // list starts at a multiple of 8 entries and is padded to a multiple of 8 with entries that point at the block's

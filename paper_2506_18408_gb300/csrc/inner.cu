@@ -132,10 +132,6 @@ __global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __re
     if (stop_sh) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int s = P.s, Bn = P.Bn, N = P.N;
-    if (threadIdx.x == 32) {  // the block's sketch gather lists (contiguous), needed after the SpMV: into L2 now
-        const int la = P.seg[(int64_t)bi.list * s], lb = P.seg[(int64_t)bi.list * s + s];
-        prefetch_l2(P.ent + la, (size_t)(lb - la) * sizeof(uint16_t));
-    }
     const VT* Ub = (const VT*)P.U;
     AT* W = (AT*)P.W;
     const int lo = i - NW + 1;  // window u_lo..u_i (NW = min(t, i+1))
