@@ -6,7 +6,7 @@ nnz = 14,581,760; beta = (50, 30, 10); b ~ N(0,1) seed 0; inner m = 100, truncat
 nonzeros per column, seed 1; tol 1e-8), with b and A resident in HBM.  The headline is the plain FP64 solver; the
 FP32-inner and BF16-basis forms are reported beside it on the same inputs.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--profile-case]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--profile-case [cd3d_128|zipf_2m]]
 
 ``--impl reference`` times the CPU oracle (plain FP64 NumPy/SciPy restatement of the method) on a bounded sample
 of the same workload.  ``--profile-case`` runs two short solves for ncu captures and prints nothing else.
@@ -138,6 +138,19 @@ def run_ours(args):
     xd = torch.empty_like(bd)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2 (129 MB)
 
+    if args.profile_case == "zipf_2m":
+        # the random Zipf matrix (length-binned SpMV), FP64 then FP32 inner, m = 20, two outer steps
+        solver.close()
+        zc = workloads.CONFIGS["zipf_2m"]
+        Z = zc.build_matrix()
+        zb = torch.from_numpy(zc.build_rhs(Z.n)).to(dev)
+        zs = Solver(Z.n, Z.row_ptr, Z.col, Z.val, sketch_seed=zc.sketch_seed, max_outer=2, stream=stream.cuda_stream)
+        for prec in ("fp64", "fp32"):
+            zs.set("precision", prec)
+            zs.solve(zb, m=20, s=zc.s, k=zc.t, tol=zc.tol)
+        torch.cuda.synchronize()
+        zs.close()
+        return
     if args.profile_case:
         # same matrix, sketch and kernels; a short basis (m = 20) and two outer steps keep the device footprint
         # (~0.6 GB) and the launch count small for ncu
@@ -427,7 +440,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--profile-case", nargs="?", const="cd3d_128", default=None,
+                    help="short solves for ncu captures: cd3d_128 (default) or zipf_2m")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve line")
     ap.add_argument("--no-others", action="store_true", help="skip the other workloads' lines")
