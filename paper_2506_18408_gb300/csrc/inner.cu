@@ -520,11 +520,34 @@ __global__ void __launch_bounds__(512) k_inner_axpy(const Plan P, int i, int las
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// Sketched QR update of column i, one cluster of nq CTAs per problem (cluster index = problem); CTA q of a cluster
-// owns rows [s q / nq, s (q+1) / nq) of Q and of the working vectors, and partial dot products are exchanged
-// through distributed shared memory and summed in rank order (deterministic).  Every early exit is decided from
-// values all CTAs of the cluster share.  CTAs are small (128 threads) so they fit beside the inner SpMV's CTAs, and
-// every long FP64 dependency chain is split into four independent accumulators (combined in a fixed order).
+// Sketched QR update of column i, one cluster of nq CTAs per problem (cluster index = problem); CTA q owns rows
+// [s q / nq, s (q+1) / nq) of Q and of the working vectors.  Partial dot products go through distributed shared
+// memory and are summed in rank order (deterministic, the same values in every CTA, so every decision is taken
+// identically everywhere).  Five cluster barriers per update: one per Gram-Schmidt pass (the two passes' partials
+// live in separate buffers), one for ||p||^2 and p^T e together (d_i = p^T e / r_ii), one for the updated residual
+// norm, and a last one before any CTA leaves.  Each CTA reads the stop state itself (written by earlier launches;
+// the one field another stream may change meanwhile, the breakdown step, only ever moves to values above i).
+// CTAs are small (128 threads) so they fit beside the inner SpMV's CTAs, and every long FP64 dependency chain is
+// split into four independent accumulators (combined in a fixed order).
+__device__ __forceinline__ double qr_rank_sum(cg::cluster_group& cl, double* base, int off, int nq) {
+    double v[kQrCluster];
+#pragma unroll
+    for (int r2 = 0; r2 < kQrCluster; ++r2) v[r2] = (r2 < nq) ? cl.map_shared_rank(base, r2)[off] : 0.0;
+    double acc = 0.0;
+#pragma unroll
+    for (int r2 = 0; r2 < kQrCluster; ++r2) acc += v[r2];
+    return acc;
+}
+
+// Sum over the CTA's 128 threads of v (warp trees, then the 4 warps in order); valid in every thread.
+__device__ __forceinline__ double qr_block_sum(double v, double* red4) {
+    v = warp_sum(v);
+    __syncthreads();  // red4 is free (its previous values have been read)
+    if ((threadIdx.x & 31) == 0) red4[threadIdx.x >> 5] = v;
+    __syncthreads();
+    return (red4[0] + red4[1]) + (red4[2] + red4[3]);
+}
+
 __global__ void __launch_bounds__(128) k_inner_qr(const Plan P, int i) {
     cg::cluster_group cl = cg::this_cluster();
     const int q = (int)cl.block_rank(), nq = (int)cl.num_blocks();
@@ -541,28 +564,24 @@ __global__ void __launch_bounds__(128) k_inner_qr(const Plan P, int i) {
     const int nrmax = (s + nq - 1) / nq;
     extern __shared__ double qsm[];
     double* p = qsm;               // [nrmax] this CTA's rows of the working vector
-    double* apart = qsm + nrmax;   // [m] partial projections over this CTA's rows
-    double* a = apart + m;         // [m] full projections
-    __shared__ double red[128];
+    double* apart = qsm + nrmax;   // [2][m] partial projections over this CTA's rows, one buffer per pass
+    double* a = apart + 2 * m;     // [m] full projections
+    __shared__ double red4[4];
     __shared__ double scal[4];
-    __shared__ int code_sh;
-    // state read by every CTA before the first cluster barrier (rank 0 writes it only after the last one)
+    // the cycle state as earlier launches left it (the same for every CTA of the cluster)
     const double dmax0 = cyc->dmax, dmin0 = cyc->dmin, thr = cyc->cond_thr;
-    if (q == 0 && threadIdx.x == 0)
-        code_sh = (cyc->stopped || (P.pflag[prob] & 1)) ? 1 : (cyc->brk_step <= i ? 2 : 0);
-    cl.sync();
-    const int code = *cl.map_shared_rank(&code_sh, 0);
-    cl.sync();
+    const int code = (cyc->stopped || (P.pflag[prob] & 1)) ? 1 : (cyc->brk_step <= i ? 2 : 0);
     if (code) {
         if (code == 2 && q == 0 && threadIdx.x == 0) {
             cyc->stopped = 1;  // u_i has zero (or non-finite) norm: the cycle keeps k = i columns
             cyc->reason = cyc->brk_reason;
         }
-        return;
+        return;  // the whole cluster returns
     }
     for (int r = threadIdx.x; r < nr; r += blockDim.x) p[r] = C[(int64_t)i * s + rlo + r];
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
+        double* ap = apart + pass * m;
         for (int l = threadIdx.x; l < i; l += blockDim.x) {
             const double* ql = Q + (int64_t)l * s + rlo;
             double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
@@ -574,15 +593,11 @@ __global__ void __launch_bounds__(128) k_inner_qr(const Plan P, int i) {
                 c3 += ql[r + 3] * p[r + 3];
             }
             for (; r < nr; ++r) c0 += ql[r] * p[r];
-            apart[l] = (c0 + c1) + (c2 + c3);
+            ap[l] = (c0 + c1) + (c2 + c3);
         }
-        cl.sync();
-        for (int l = threadIdx.x; l < i; l += blockDim.x) {
-            double acc = 0.0;
-            for (int qq = 0; qq < nq; ++qq) acc += cl.map_shared_rank(apart, qq)[l];
-            a[l] = acc;
-        }
-        cl.sync();  // every CTA has read the partials before the next pass overwrites them
+        cl.sync();  // this pass's partials of every CTA are in place
+        for (int l = threadIdx.x; l < i; l += blockDim.x) a[l] = qr_rank_sum(cl, ap, l, nq);
+        __syncthreads();
         for (int r = threadIdx.x; r < nr; r += blockDim.x) {
             const double* qr = Q + rlo + r;
             double v0 = p[r], v1 = 0.0, v2 = 0.0, v3 = 0.0;
@@ -601,14 +616,21 @@ __global__ void __launch_bounds__(128) k_inner_qr(const Plan P, int i) {
                 R[(int64_t)i * m + l] = (pass ? R[(int64_t)i * m + l] : 0.0) + a[l];
         __syncthreads();
     }
-    double v2 = 0.0;
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) v2 += p[r] * p[r];
-    v2 = block_sum_lean(v2, red);
-    if (threadIdx.x == 0) scal[0] = v2;
+    // r_ii = ||p|| and p^T e from one exchange
+    double v2 = 0.0, pe = 0.0;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        v2 += p[r] * p[r];
+        pe += p[r] * e[rlo + r];
+    }
+    v2 = qr_block_sum(v2, red4);
+    pe = qr_block_sum(pe, red4);
+    if (threadIdx.x == 0) {
+        scal[0] = v2;
+        scal[1] = pe;
+    }
     cl.sync();
-    double nn = 0.0;
-    for (int qq = 0; qq < nq; ++qq) nn += cl.map_shared_rank(scal, qq)[0];
-    const double rii = sqrt(nn);
+    const double rii = sqrt(qr_rank_sum(cl, scal, 0, nq));
+    const double pet = qr_rank_sum(cl, scal, 1, nq);
     const double dmax = fmax(dmax0, rii);
     const double dmin = (i == 0) ? rii : fmin(dmin0, rii);
     const double kappa = (dmin > 0.0) ? dmax / dmin : INFINITY;
@@ -618,34 +640,23 @@ __global__ void __launch_bounds__(128) k_inner_qr(const Plan P, int i) {
             cyc->k = i;
             cyc->reason = (i == 0) ? 5 : 2;
         }
-        cl.sync();
+        cl.sync();  // no CTA leaves while another may still read its shared memory
         return;
     }
     const double inv = 1.0 / rii;
-    double dd = 0.0;
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-        const double qv = p[r] * inv;
-        p[r] = qv;
-        Q[(int64_t)i * s + rlo + r] = qv;
-        dd += qv * e[rlo + r];
-    }
-    dd = block_sum_lean(dd, red);
-    if (threadIdx.x == 0) scal[1] = dd;
-    cl.sync();
-    double di = 0.0;
-    for (int qq = 0; qq < nq; ++qq) di += cl.map_shared_rank(scal, qq)[1];
+    const double di = pet * inv;
     double ee = 0.0;
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-        const double ev = e[rlo + r] - di * p[r];
+        const double qv = p[r] * inv;
+        Q[(int64_t)i * s + rlo + r] = qv;
+        const double ev = e[rlo + r] - di * qv;
         e[rlo + r] = ev;
         ee += ev * ev;
     }
-    ee = block_sum_lean(ee, red);
+    ee = qr_block_sum(ee, red4);
     if (threadIdx.x == 0) scal[2] = ee;
     cl.sync();
-    double rr2 = 0.0;
-    for (int qq = 0; qq < nq; ++qq) rr2 += cl.map_shared_rank(scal, qq)[2];
-    const double rh = sqrt(rr2);
+    const double rh = sqrt(qr_rank_sum(cl, scal, 2, nq));
     if (q == 0 && threadIdx.x == 0) {
         R[(int64_t)i * m + i] = rii;
         d[i] = di;
@@ -877,7 +888,7 @@ void launch_inner_axpy(const Plan& p, int i, bool last) {
 cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st) {
     const int nq = p.qr_cluster;
     const int nrmax = (p.s + nq - 1) / nq;
-    const size_t sm = (size_t)(nrmax + 2 * p.m) * sizeof(double);
+    const size_t sm = (size_t)(nrmax + 3 * p.m) * sizeof(double);
     set_smem((const void*)k_inner_qr, sm);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nq * p.P), 1, 1);
