@@ -332,6 +332,20 @@ def run_others(args, dev, stream):
         sv.set("precision", prec)
         sec, _ = _event_time(fwd_bwd, stream, 3, 1)
         out[f"cd3d_64_x16_grad_{prec}"] = {"s_forward_backward": sec, "rhs": 16}
+    # the 16 right-hand sides as one batched FP32-inner solve against 16 plain FP64 solves one after another
+    Bf = B.reshape(-1).contiguous()
+    kw = dict(m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
+    sv.set("precision", "fp32")
+    t_batch, _ = _event_time(lambda: sv.solve_batch(Bf, nrhs=16, **kw), stream, 3, 1)
+    sv.set("precision", "fp64")
+
+    def sequential():
+        for r in range(16):
+            sv.solve(B[r], **kw)
+
+    t_seq, _ = _event_time(sequential, stream, 2, 1)
+    out["cd3d_64_x16_batched_vs_plain"] = {"batched_fp32_inner_s": t_batch, "plain_fp64_sequential_s": t_seq,
+                                           "speedup": t_seq / t_batch}
     sv.close()
     return out
 
@@ -371,6 +385,22 @@ def run_batch(args, dev, stream):
     sv.close()
     sec = statistics.mean(times)
     st = info["status_p"]
+    # the plain FP64 solver on the same inputs, problem by problem, on a seeded sample of problems
+    rng = np.random.default_rng([0, workloads.STREAM_SAMPLE])
+    sample = sorted(rng.choice(P, size=16, replace=False).tolist())
+    blocks = workloads.split_blocks(A)
+    sl = workloads.problem_slices(A.sys_n, cfg.nrhs)
+    t_plain = 0.0
+    for p in sample:
+        q, a0, nq = sl[p]
+        Aq = blocks[q]
+        one = Solver(Aq.n, Aq.row_ptr, Aq.col, Aq.val, sketch_seed=cfg.sketch_seed, zeta=cfg.zeta,
+                     max_outer=cfg.max_outer, stream=stream.cuda_stream)
+        bq = bd[a0:a0 + nq].contiguous()
+        tq, _ = _event_time(lambda: one.solve(bq, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol), stream, 1, 1)
+        t_plain += tq
+        one.close()
+    plain_est = t_plain * P / len(sample)
     return {"workload": "batch_512: 512 2D convection-diffusion systems, sides U{32..512}, beta~U(0,50)^2, "
                         "4 RHS ~N(0,1) each; m=40, k=2, s=160, FP32 inner + FP64 outer, tol 1e-8",
             "value": P / sec, "unit": "solves/s", "time_s": sec, "steps": args.batch_steps,
@@ -378,7 +408,9 @@ def run_batch(args, dev, stream):
             "converged": int(sum(1 for v in st if v == 0)), "lockstep_outer": info["lockstep_outer"],
             "max_outer": max(info["outer_iters_p"]), "total_inner": info["total_inner"],
             "max_rel_res_true": max(info["rel_res_true_p"]), "kernel_launches": info["kernel_launches"],
-            "autotune": {"block_rows": tile[0], "spmv_vector": tile[1], "step_ms": tile[2], "tune_s": tune_s}}
+            "autotune": {"block_rows": tile[0], "spmv_vector": tile[1], "step_ms": tile[2], "tune_s": tune_s},
+            "plain_fp64_per_problem": {"sample_problems": sample, "sample_s": t_plain,
+                                       "extrapolated_s": plain_est, "batched_speedup": plain_est / sec}}
 
 
 def cpu_baseline(outer_iters):
