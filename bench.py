@@ -185,7 +185,11 @@ def run_ours(args):
         return times, infos
 
     with ClockSampler(local) as clk:
-        t64, i64 = timed("fp64", args.steps, args.warmup, profile=True)
+        t64, i64 = timed("fp64", args.steps, args.warmup)
+        # the same solves with the kernels bracketed by CUDA events (event nodes in the captured graphs): the
+        # per-launch duration of the fused inner kernel for the roofline.  The events lengthen the solve, so the
+        # headline time comes from the unprofiled solves above.
+        tp, ip = timed("fp64", max(3, args.steps // 2), 1, profile=True)
     t32, i32 = timed("fp32", args.steps, max(3, args.warmup // 2))
     t16, i16 = timed("bf16", args.steps, max(3, args.warmup // 2))
     sec = statistics.mean(t64)
@@ -210,7 +214,7 @@ def run_ours(args):
 
     last = i64[-1]
     launches = sum(i["kernel_launches"] for i in i64) / len(i64)
-    k1_ms = sum(i["t_inner_spmv_ms"] for i in i64) / sum(i["n_inner_spmv"] for i in i64)
+    k1_ms = sum(i["t_inner_spmv_ms"] for i in ip) / sum(i["n_inner_spmv"] for i in ip)
     hbm, peak_src = _peaks()
     Bn = int(solver.get("block_rows"))  # rows per block in use (the library's choice)
     nblk = -(-n // Bn)
@@ -246,7 +250,9 @@ def run_ours(args):
             "roofline": {"kernel": "k_inner_spmv (fused SpMV + truncated-Arnoldi dots + sketch partials, FP64)",
                          "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": peak_src, "traffic": traffic,
-                         "alg_bytes_per_launch": abytes, "avg_launch_ms": k1_ms},
+                         "alg_bytes_per_launch": abytes, "avg_launch_ms": k1_ms,
+                         "launches_timed": int(sum(i["n_inner_spmv"] for i in ip)),
+                         "profiled_solve_s": statistics.mean(tp)},
             "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n},
             "batch": batch,

@@ -69,13 +69,14 @@ extern "C" {
                                         returns the shape in use: 1, 2..32, or 0 for the length-binned SpMV. */
 #define SFGMRES_OPT_BLOCK_ROWS 9     /* rows per row block of the fused inner kernels: a multiple of 32 in
                                         [32, 8192], or 0 (default) = chosen by the library (one system: about a
-                                        multiple of the SM count of blocks; several systems: 4096).  Reading it
-                                        returns the size in use. */
+                                        multiple of the SM count of blocks, less 8 SMs with FP64 inner cycles, which
+                                        are left to the sketched-QR update running beside the fused kernel; several
+                                        systems: 4096).  Reading it returns the size in use. */
 #define SFGMRES_OPT_GRAPH 10         /* 1 (default): each outer step (one inner cycle for every problem and the outer
                                         FGMRES update) is captured once into a CUDA graph and replayed; the graphs
                                         are kept while the solve's parameters and workspaces stay the same.  0: the
                                         kernels are launched one by one.  Results are identical either way.
-                                        SFGMRES_OPT_PROFILE = 1 launches one by one. */
+                                        With SFGMRES_OPT_PROFILE = 1 the timing events are part of the graphs. */
 #define SFGMRES_OPT_RHS_GROUP 11     /* sfgmres_solve_batch with nrhs > 1 on a matrix whose rows have at most 16
                                         entries: right-hand sides of one system served by one CTA of the fused inner
                                         SpMV, which then reads A and the sketch lists once for all of them; 1
@@ -110,9 +111,10 @@ typedef struct {
     double rel_res_true;     /* recomputed ||b - A x|| / ||b|| of the returned x */
     double rel_res_est;      /* last Givens estimate */
     int64_t kernel_launches; /* kernels this call launched */
-    /* with SFGMRES_OPT_PROFILE = 1 (otherwise 0): */
+    /* with SFGMRES_OPT_PROFILE = 1 (otherwise 0), over the launches of the inner steps that built a basis vector
+       (steps i < k_j of each outer step j; the launches after a cycle stopped only read the stop flag): */
     double t_inner_spmv_ms;  /* total device time of the fused inner SpMV + dot + sketch kernel */
-    int64_t n_inner_spmv;    /* its launches */
+    int64_t n_inner_spmv;    /* its launches counted */
     double t_inner_axpy_ms;  /* total device time of the truncated-Arnoldi update kernel */
     int64_t n_inner_axpy;
     double t_qr_ms;          /* total device time of the sketched-QR update kernel */

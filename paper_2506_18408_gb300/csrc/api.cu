@@ -73,6 +73,19 @@ struct sfgmres_ctx {
     double* valT = nullptr;
     float* val32T = nullptr;
     int maxlenT = 0, vecT = 8;
+    // SELL-32 copies of A ([0]) and A^T ([1]) for the one-thread-per-row inner SpMV, built on first use
+    struct Sell {
+        int* off = nullptr;
+        uint8_t* len = nullptr;
+        int* col = nullptr;
+        double* val = nullptr;
+        float* val32 = nullptr;
+        int64_t total = 0;  // entries, padding included
+    } sell[2];
+    int sl_ns = 0;                 // slices (the same for A and A^T: block-diagonal with the same blocks)
+    int* sl_sys = nullptr;         // [nsys + 1] first slice of each system, then [nsys + 1] first row of each system
+    int* sl_base = nullptr;        // [list blocks] first slice of each list block
+    int sl_base_ver = -1;
     uint64_t seed = 0;
     cudaStream_t st = nullptr;
     bool own_stream = false;
@@ -125,9 +138,13 @@ struct sfgmres_ctx {
     std::vector<cudaGraphExec_t> graph_exec;
     std::vector<int64_t> graph_launches;
 
-    // profiling
+    // profiling: event pairs per inner kernel; outer step j records its m launches of each kernel into pairs
+    // [base, base + m) of each pool (captured into the step's graph, or recorded as the kernels are launched)
     std::vector<EventPair> ev_spmv, ev_axpy, ev_qr;
-    size_t n_spmv = 0, n_axpy = 0, n_qr = 0;
+    size_t ev_next = 0;   // next free pair (the same index in all three pools)
+    size_t ev_graph = 0;  // pairs [0, ev_graph) belong to the cached graphs
+    std::vector<size_t> graph_ev;           // base pair of each cached graph (SIZE_MAX: captured without events)
+    std::vector<std::pair<int, size_t>> ev_steps;  // this solve's outer steps: (j, base pair)
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
 
     std::string err;
@@ -205,7 +222,12 @@ bool is_device_ptr(const void* p) {
 int choose_vec(int64_t, int, int maxlen) { return maxlen <= 16 ? 1 : 0; }
 
 // Row blocks of one system: nblk a multiple of the SM count where possible, Bn a multiple of 32, <= kBlockRowsMax.
-int single_block_rows(int n, int sms) {
+// FP64 inner cycles size the blocks for all SMs but one QR cluster's: the sketched QR of step i runs beside the
+// fused inner kernel of step i+1, and a one-wave FP64 inner kernel whose CTAs share SMs with the QR cluster waits
+// on those stragglers (measured on 128^3: 137 us per step with 304 blocks, 112 us with 288).  The FP32 and BF16
+// inner kernels are short enough that the QR does not slow them, and all SMs serve them best.
+int single_block_rows(int n, int sms, int prec) {
+    if (prec == 0 && sms > 2 * kQrCluster) sms -= kQrCluster;
     int q = 1, b = 32;
     for (;;) {
         const int64_t per = ((int64_t)n + (int64_t)sms * q - 1) / ((int64_t)sms * q);
@@ -228,7 +250,7 @@ void set_list_geometry(sfgmres_ctx* h) {
     if (h->block_rows) Bq = h->block_rows;
     else if (h->nsys == 1 && h->persistent && h->n <= kPersistCluster * kBlockRowsMax)
         Bq = std::max(32, ((h->n + kPersistCluster - 1) / kPersistCluster + 31) / 32 * 32);  // one cluster's blocks
-    else if (h->nsys == 1) Bq = single_block_rows(h->n, h->sms);
+    else if (h->nsys == 1) Bq = single_block_rows(h->n, h->sms, h->prec);
     else Bq = kBatchBlockRows;
     int Bn = 32, nl = 0;
     for (int q = 0; q < h->nsys; ++q) {
@@ -504,6 +526,70 @@ int ensure_bins(sfgmres_ctx* h, bool transpose) {
     return 0;
 }
 
+// SELL-32 copy of A (or A^T) for the one-thread-per-row inner SpMV, with its FP32 values when need32; the list
+// blocks' first slices follow the row-block geometry.
+int ensure_sell(sfgmres_ctx* h, bool transpose, bool need32) {
+    sfgmres_ctx::Sell& S = h->sell[transpose ? 1 : 0];
+    const int* rp = transpose ? h->rpT : h->rp;
+    const int* col = transpose ? h->colT : h->col;
+    const double* val = transpose ? h->valT : h->val;
+    if (!h->sl_sys) {
+        std::vector<int> t(2 * (size_t)(h->nsys + 1), 0);
+        int64_t ns = 0;
+        for (int q = 0; q < h->nsys; ++q) {
+            t[q] = (int)ns;
+            ns += (h->sys_n[q] + 31) / 32;
+        }
+        if (ns > INT32_MAX - 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "too many rows for the SELL-32 layout");
+        t[h->nsys] = (int)ns;
+        for (int q = 0; q <= h->nsys; ++q) t[h->nsys + 1 + q] = h->sys_moff[q];
+        CK(cudaMalloc(&h->sl_sys, t.size() * sizeof(int)));
+        CK(cudaMemcpy(h->sl_sys, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice));
+        h->sl_ns = (int)ns;
+    }
+    const int ns = h->sl_ns;
+    const int* sl0 = h->sl_sys;
+    const int* moff = h->sl_sys + h->nsys + 1;
+    if (!S.off) {
+        int* wid = nullptr;
+        CK(cudaMalloc(&S.off, ((size_t)ns + 1) * sizeof(int)));
+        CK(cudaMalloc(&S.len, std::max<size_t>((size_t)ns * 32, 1)));
+        CK(cudaMalloc(&wid, std::max<size_t>((size_t)ns, 1) * sizeof(int)));
+        launch_sell_build(ns, sl0, h->nsys, moff, rp, S.len, wid, S.off, h->st);
+        int tot = 0;
+        CK(cudaMemcpyAsync(&tot, S.off + ns, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        cudaFree(wid);
+        CK(cudaGetLastError());
+        S.total = (int64_t)tot * 32;
+        CK(cudaMalloc(&S.col, std::max<int64_t>(S.total, 1) * sizeof(int)));
+        CK(cudaMalloc(&S.val, std::max<int64_t>(S.total, 1) * sizeof(double)));
+        launch_sell_fill(ns, sl0, h->nsys, moff, rp, col, val, S.off, S.len, S.col, S.val, h->st);
+        CK(cudaGetLastError());
+    }
+    if (need32 && !S.val32) {
+        CK(cudaMalloc(&S.val32, std::max<int64_t>(S.total, 1) * sizeof(float)));
+        k_to_f32<<<grid_for(S.total), 256, 0, h->st>>>(S.total, S.val, S.val32);
+        ++g_launches;
+        CK(cudaGetLastError());
+    }
+    if (h->sl_base_ver != h->geo_ver) {
+        std::vector<int> hb((size_t)std::max(h->nl, 1), 0);
+        int ns0 = 0;
+        for (int q = 0; q < h->nsys; ++q) {
+            const int nq = h->sys_n[q], Bq = h->sys_Bq[q];
+            for (int k = 0, L = h->sys_l0[q]; k * Bq < nq; ++k, ++L) hb[L] = ns0 + k * (Bq / 32);
+            ns0 += (nq + 31) / 32;
+        }
+        if (h->sl_base) cudaFree(h->sl_base);
+        h->sl_base = nullptr;
+        CK(cudaMalloc(&h->sl_base, hb.size() * sizeof(int)));
+        CK(cudaMemcpy(h->sl_base, hb.data(), hb.size() * sizeof(int), cudaMemcpyHostToDevice));
+        h->sl_base_ver = h->geo_ver;
+    }
+    return 0;
+}
+
 // Matrix and geometry fields of a Plan (enough for the SpMV and the per-block helpers).
 void plan_geometry(sfgmres_ctx* h, const Geo* g, bool transpose, Plan& P) {
     P.nnz = h->nnz;
@@ -514,6 +600,14 @@ void plan_geometry(sfgmres_ctx* h, const Geo* g, bool transpose, Plan& P) {
     P.vec = transpose ? (h->vec_opt ? h->vec_opt : h->vecT) : h->vec;
     P.perm = (P.vec == 0) ? h->perm[transpose ? 1 : 0] : nullptr;
     P.cls = (P.vec == 0) ? h->cls[transpose ? 1 : 0] : nullptr;
+    const sfgmres_ctx::Sell& S = h->sell[transpose ? 1 : 0];
+    const bool sl = (P.vec == 1) && S.off && h->sl_base_ver == h->geo_ver;
+    P.sl_off = sl ? S.off : nullptr;
+    P.sl_len = sl ? S.len : nullptr;
+    P.sl_col = sl ? S.col : nullptr;
+    P.sl_val = sl ? S.val : nullptr;
+    P.sl_val32 = sl ? S.val32 : nullptr;
+    P.sl_base = sl ? h->sl_base : nullptr;
     P.N = g->N;
     P.P = g->P;
     P.nblk = g->nblk;
@@ -577,6 +671,7 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     {
         const int v = transpose ? (h->vec_opt ? h->vec_opt : h->vecT) : h->vec;
         if (v == 0 && (rc = ensure_bins(h, transpose))) return rc;
+        if (v == 1 && (rc = ensure_sell(h, transpose, h->prec != kFP64))) return rc;
     }
     const size_t vt = (h->prec == kFP64) ? 8 : (h->prec == kFP32 ? 4 : 2);
     const size_t at = (h->prec == kFP64) ? 8 : 4;
@@ -714,21 +809,29 @@ int check_params(sfgmres_ctx* h, int m, int s, int t) {
 }
 
 // ---- profiling helpers ----
-void ev_begin(sfgmres_ctx*, std::vector<EventPair>& pool, size_t idx, cudaStream_t st) {
-    if (idx >= pool.size()) {
-        EventPair e;
-        cudaEventCreate(&e.a);
-        cudaEventCreate(&e.b);
-        pool.push_back(e);
-    }
-    cudaEventRecord(pool[idx].a, st);
+// Pairs [base, base + count) of all three pools exist afterwards.
+int ev_reserve(sfgmres_ctx* h, size_t base, size_t count) {
+    for (auto* pool : {&h->ev_spmv, &h->ev_axpy, &h->ev_qr})
+        while (pool->size() < base + count) {
+            EventPair e;
+            CK(cudaEventCreate(&e.a));
+            if (cudaEventCreate(&e.b) != cudaSuccess) {
+                cudaEventDestroy(e.a);
+                CK(cudaGetLastError());
+            }
+            pool->push_back(e);
+        }
+    return 0;
 }
-void ev_end(sfgmres_ctx*, std::vector<EventPair>& pool, size_t idx, cudaStream_t st) {
-    cudaEventRecord(pool[idx].b, st);
+// Records one event; inside a stream capture it becomes an event-record node of the graph, so the graph's replays
+// time the kernels too.
+void ev_rec(cudaEvent_t e, cudaStream_t st, bool capturing) {
+    if (capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
 }
-double ev_sum(const std::vector<EventPair>& pool, size_t count) {
+double ev_sum(const std::vector<EventPair>& pool, size_t base, size_t count) {
     double tot = 0.0;
-    for (size_t i = 0; i < count; ++i) {
+    for (size_t i = base; i < base + count; ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, pool[i].a, pool[i].b) == cudaSuccess) tot += ms;
     }
@@ -747,26 +850,28 @@ int persistent_cluster(const sfgmres_ctx* h, const Plan& P) {
     return P.maxbp;
 }
 
+// ev: base event pair of this cycle's launches (profiling), or SIZE_MAX; capturing: inside a stream capture.
 int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const double* vscale, int vstride, int c3,
-              double* z) {
+              double* z, size_t ev = SIZE_MAX, bool capturing = false) {
     launch_cycle_start(P, j, v, vscale, vstride, c3, h->cond_thr);
     if (const int nq = persistent_cluster(h, P)) {
         CK(launch_cycle_persistent(P, nq, z));
         return 0;
     }
+    const bool prof = (ev != SIZE_MAX);
     for (int i = 0; i < P.m; ++i) {
         const bool last = (i == P.m - 1);
-        if (h->profile) ev_begin(h, h->ev_spmv, h->n_spmv, h->st);
+        if (prof) ev_rec(h->ev_spmv[ev + i].a, h->st, capturing);
         launch_inner_spmv(P, i);
-        if (h->profile) ev_end(h, h->ev_spmv, h->n_spmv++, h->st);
-        if (h->profile) ev_begin(h, h->ev_axpy, h->n_axpy, h->st);
+        if (prof) ev_rec(h->ev_spmv[ev + i].b, h->st, capturing);
+        if (prof) ev_rec(h->ev_axpy[ev + i].a, h->st, capturing);
         launch_inner_axpy(P, i, last);
-        if (h->profile) ev_end(h, h->ev_axpy, h->n_axpy++, h->st);
+        if (prof) ev_rec(h->ev_axpy[ev + i].b, h->st, capturing);
         CK(cudaEventRecord(h->ev_c, h->st));
         CK(cudaStreamWaitEvent(h->qst, h->ev_c, 0));
-        if (h->profile) ev_begin(h, h->ev_qr, h->n_qr, h->qst);
+        if (prof) ev_rec(h->ev_qr[ev + i].a, h->qst, capturing);
         CK(launch_inner_qr(P, i, h->qst));
-        if (h->profile) ev_end(h, h->ev_qr, h->n_qr++, h->qst);
+        if (prof) ev_rec(h->ev_qr[ev + i].b, h->qst, capturing);
     }
     CK(cudaEventRecord(h->ev_q, h->qst));
     CK(cudaStreamWaitEvent(h->st, h->ev_q, 0));
@@ -780,7 +885,8 @@ std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
     auto u = [&](const void* p) { k.push_back((uint64_t)(uintptr_t)p); };
     for (const void* p : std::initializer_list<const void*>{(const void*)P.grp_b, (const void*)P.perm, (const void*)P.cls,
                                                             (const void*)P.rp, (const void*)P.col, (const void*)P.val, (const void*)P.val32,
-                          (const void*)P.blk_v0, (const void*)P.seg, (const void*)P.ent, P.U, P.W,
+                          (const void*)P.blk_v0, (const void*)P.seg, (const void*)P.sl_off, (const void*)P.sl_col,
+                          (const void*)P.sl_val, (const void*)P.sl_val32, (const void*)P.sl_base, (const void*)P.sl_len, (const void*)P.ent, P.U, P.W,
                           (const void*)P.sigma, P.normpart, P.hpart, P.cpart, (const void*)P.C, (const void*)P.Q,
                           (const void*)P.R, (const void*)P.d, (const void*)P.e, (const void*)P.c0,
                           (const void*)P.rho, (const void*)P.y, (const void*)P.coef, (const void*)P.hco,
@@ -793,7 +899,8 @@ std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
         u(p);
     for (int64_t v : std::initializer_list<int64_t>{(int64_t)P.G, (int64_t)P.ngrp, (int64_t)P.nnz, (int64_t)P.vec, (int64_t)P.N, (int64_t)P.P, (int64_t)P.nblk, (int64_t)P.Bn,
                       (int64_t)P.s, (int64_t)P.zeta, (int64_t)P.kind, (int64_t)P.sk_headroom, (int64_t)P.prec,
-                      (int64_t)P.m, (int64_t)P.t, (int64_t)P.qr_cluster, (int64_t)P.jmax, (int64_t)h->c3})
+                      (int64_t)P.m, (int64_t)P.t, (int64_t)P.qr_cluster, (int64_t)P.jmax, (int64_t)h->c3,
+                      (int64_t)h->profile})
         k.push_back((uint64_t)v);
     uint64_t bits;
     std::memcpy(&bits, &P.sk_scale, 8);
@@ -809,31 +916,58 @@ void drop_graphs(sfgmres_ctx* h) {
     h->graph_exec.clear();
     h->graph_launches.clear();
     h->graph_key.clear();
+    h->graph_ev.clear();
+    h->ev_graph = 0;
 }
 
 // One outer step j (inner cycle j and the outer FGMRES update) for every active problem.  With graphs on, the step
-// is captured from the handle's streams once per plan and j, then replayed as a single graph launch.
+// is captured from the handle's streams once per plan and j, then replayed as a single graph launch.  With profiling
+// on, the step's inner-kernel launches are bracketed by events (event-record nodes of the graph).
 int outer_step(sfgmres_ctx* h, const Plan& P, int j) {
-    auto enqueue = [&]() -> int {
-        int rc = run_cycle(h, P, j, P.Vb + (int64_t)j * P.N, P.nu + j, P.jmax + 1, h->c3, P.Z + (int64_t)j * P.N);
+    auto enqueue = [&](size_t ev, bool capturing) -> int {
+        int rc = run_cycle(h, P, j, P.Vb + (int64_t)j * P.N, P.nu + j, P.jmax + 1, h->c3, P.Z + (int64_t)j * P.N,
+                           ev, capturing);
         if (rc) return rc;
         launch_outer_step(P, j);
         return 0;
     };
-    if (!h->use_graph || h->profile) return enqueue();
+    const bool prof = h->profile && !persistent_cluster(h, P);
+    auto take_events = [&](size_t& ev) -> int {
+        ev = SIZE_MAX;
+        if (!prof) return 0;
+        int rc = ev_reserve(h, h->ev_next, (size_t)P.m);
+        if (rc) return rc;
+        ev = h->ev_next;
+        h->ev_next += (size_t)P.m;
+        h->ev_steps.push_back({j, ev});
+        return 0;
+    };
+    int rc;
+    if (!h->use_graph) {
+        size_t ev;
+        if ((rc = take_events(ev))) return rc;
+        return enqueue(ev, false);
+    }
     std::vector<uint64_t> key = plan_key(h, P);
     if (key != h->graph_key) {
         drop_graphs(h);
         h->graph_key = key;
+        h->ev_next = 0;
     }
     if ((int)h->graph_exec.size() <= j) {
         h->graph_exec.resize(j + 1, nullptr);
         h->graph_launches.resize(j + 1, 0);
+        h->graph_ev.resize(j + 1, SIZE_MAX);
     }
     if (!h->graph_exec[j]) {
         const int64_t l0 = g_launches;
+        // a graph's events stay its own: pairs after every cached graph's, below those of one-by-one launches
+        h->ev_next = h->ev_graph;
+        size_t ev;
+        if ((rc = take_events(ev))) return rc;
+        if (prof) h->ev_steps.pop_back();  // recorded below, once the graph exists
         CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
-        int rc = enqueue();
+        rc = enqueue(ev, true);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->st, &graph);
         if (rc) {
@@ -847,8 +981,11 @@ int outer_step(sfgmres_ctx* h, const Plan& P, int j) {
         CK(e);
         h->graph_exec[j] = ex;
         h->graph_launches[j] = g_launches - l0;
+        h->graph_ev[j] = ev;
+        if (prof) h->ev_graph = h->ev_next;
         g_launches = l0;
     }
+    if (h->graph_ev[j] != SIZE_MAX) h->ev_steps.push_back({j, h->graph_ev[j]});
     CK(cudaGraphLaunch(h->graph_exec[j], h->st));
     g_launches += h->graph_launches[j];
     return 0;
@@ -901,7 +1038,8 @@ int solve_core(sfgmres_t h, bool transpose, int nrhs, const double* b, const dou
     int* dflag = pflag_of(g);
     OuterState* host_ost = (OuterState*)h->h_ost.p;
     const bool x_dev = is_device_ptr(x);
-    h->n_spmv = h->n_axpy = h->n_qr = 0;
+    h->ev_steps.clear();
+    h->ev_next = h->ev_graph;  // one-by-one launches reuse the pairs after the cached graphs'
     CK(cudaEventRecord(h->ev_t0, h->st));
     // private copies of b and x0 (x may alias x0, and host inputs are staged)
     CK(cudaMemcpyAsync(db, b, nbytes, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
@@ -1071,12 +1209,20 @@ int solve_single(sfgmres_t h, bool transpose, const double* b, const double* x0,
         cudaEventElapsedTime(&tms, h->ev_t0, h->ev_t1);
         st->t_total_ms = tms;
         if (h->profile) {
-            st->t_inner_spmv_ms = ev_sum(h->ev_spmv, h->n_spmv);
-            st->n_inner_spmv = (int64_t)h->n_spmv;
-            st->t_inner_axpy_ms = ev_sum(h->ev_axpy, h->n_axpy);
-            st->n_inner_axpy = (int64_t)h->n_axpy;
-            st->t_qr_ms = ev_sum(h->ev_qr, h->n_qr);
-            st->n_qr = (int64_t)h->n_qr;
+            // the launches of inner steps i < k_j of each outer step j (those that built a basis vector); the
+            // launches after the cycle stopped only read the stop flag and return
+            st->t_inner_spmv_ms = st->t_inner_axpy_ms = st->t_qr_ms = 0.0;
+            st->n_inner_spmv = st->n_inner_axpy = st->n_qr = 0;
+            for (const auto& js : h->ev_steps) {
+                if (js.first >= cnt) continue;
+                const size_t kw = (size_t)std::max(0, std::min(kh[js.first], P.m));
+                st->t_inner_spmv_ms += ev_sum(h->ev_spmv, js.second, kw);
+                st->t_inner_axpy_ms += ev_sum(h->ev_axpy, js.second, kw);
+                st->t_qr_ms += ev_sum(h->ev_qr, js.second, kw);
+                st->n_inner_spmv += (int64_t)kw;
+                st->n_inner_axpy += (int64_t)kw;
+                st->n_qr += (int64_t)kw;
+            }
         } else {
             st->t_inner_spmv_ms = st->t_inner_axpy_ms = st->t_qr_ms = 0.0;
             st->n_inner_spmv = st->n_inner_axpy = st->n_qr = 0;
@@ -1223,6 +1369,11 @@ int sfgmres_destroy(sfgmres_t h) {
         if (h->cls[t]) cudaFree(h->cls[t]);
     }
     if (h->lb) cudaFree(h->lb);
+    for (auto& S : h->sell)
+        for (void* q : {(void*)S.off, (void*)S.len, (void*)S.col, (void*)S.val, (void*)S.val32})
+            if (q) cudaFree(q);
+    if (h->sl_sys) cudaFree(h->sl_sys);
+    if (h->sl_base) cudaFree(h->sl_base);
     DevBuf* bufs[] = {&h->U, &h->W, &h->sigma, &h->normpart, &h->hpart, &h->cpart, &h->C, &h->Q, &h->R, &h->d,
                       &h->e, &h->c0, &h->rho, &h->y, &h->coef, &h->hco, &h->cyc, &h->Vb, &h->Z, &h->nu, &h->Wo,
                       &h->opart, &h->npart, &h->npart2, &h->h1, &h->h2, &h->H, &h->cs, &h->sn, &h->g, &h->yo,
@@ -1261,7 +1412,10 @@ int sfgmres_set_option(sfgmres_t h, int32_t key, double v) {
     switch (key) {
         case SFGMRES_OPT_PRECISION:
             if (iv < 0 || iv > 2 || iv != v) return fail(h, SFGMRES_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
-            h->prec = iv;
+            if (iv != h->prec) {
+                h->prec = iv;
+                if (h->nsys == 1 && !h->block_rows) set_list_geometry(h);  // the default row blocks depend on it
+            }
             return 0;
         case SFGMRES_OPT_ZETA:
             if (iv < 1 || iv > kMaxZeta || iv != v) return fail(h, SFGMRES_ERR_INVALID_ARG, "zeta must be 1..16");
@@ -1409,7 +1563,7 @@ int sfgmres_autotune(sfgmres_t h, int32_t nrhs, int32_t m, int32_t s, int32_t k,
     std::vector<int> cand;
     int maxn = 0;
     for (int q = 0; q < h->nsys; ++q) maxn = std::max(maxn, h->sys_n[q]);
-    const int base = (h->nsys == 1) ? single_block_rows(h->n, h->sms) : kBatchBlockRows;
+    const int base = (h->nsys == 1) ? single_block_rows(h->n, h->sms, h->prec) : kBatchBlockRows;
     for (int v : {base, base / 2, base / 4, base / 8, 512, 1024, 2048, 4096, 8192}) {
         v = std::min(kBlockRowsMax, std::max(256, (v / 32) * 32));
         if (v > ((maxn + 31) / 32) * 32 && v != base) continue;  // larger than every system: same as smaller ones
@@ -1492,6 +1646,13 @@ int sfgmres_update_values(sfgmres_t h, const double* vals) {
     if (h->rpT) {
         launch_gather_vals(h->nnz, h->srcT, h->val, h->valT, h->st);
         if (h->val32T) k_to_f32<<<grid_for(h->nnz), 256, 0, h->st>>>(h->nnz, h->valT, h->val32T);
+    }
+    for (int t = 0; t < 2; ++t) {  // the SELL-32 copies' values
+        sfgmres_ctx::Sell& S = h->sell[t];
+        if (!S.off) continue;
+        launch_sell_fill(h->sl_ns, h->sl_sys, h->nsys, h->sl_sys + h->nsys + 1, t ? h->rpT : h->rp, nullptr,
+                         t ? h->valT : h->val, S.off, S.len, nullptr, S.val, h->st);
+        if (S.val32) k_to_f32<<<grid_for(S.total), 256, 0, h->st>>>(S.total, S.val, S.val32);
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->st));

@@ -32,28 +32,51 @@ __device__ __forceinline__ bool cycle_idle(const Plan& P, int p, int i) {
     return c->stopped || c->brk_step <= i || (P.pflag[p] & 1);
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 // ---------------------------------------------------------------------------------------------------------------
-// Phase 1, one thread per row: w' = A u_i over the block (vector rows v0 .. v0+len = matrix rows v0-cs ..) fused
-// with storing w' (global W and the shared block copy), the window dot products acc_q += u_{lo+q}[r] * w'[r] and
-// ||u_i||^2.  The window values and the next row group's extents are loaded before the row's SpMV, so they are in
-// flight together.  Returns the thread's largest exponent of w'.
+// Entries pk .. pk+CNT-1 of the thread's row in the SELL-32 copy (cp, vp: the lane's first entry; consecutive
+// entries 32 apart, so each load is coalesced across the warp); entries past the row's end (rl) are not gathered.
+template <int CNT, typename MT, typename XT, typename AT>
+__device__ __forceinline__ void sell_chunk(const int* __restrict__ cp, const MT* __restrict__ vp,
+                                           const XT* __restrict__ x, int rl, int pk, AT& sum) {
+    int c[CNT];
+    AT v[CNT];
+#pragma unroll
+    for (int q = 0; q < CNT; ++q) {
+        c[q] = __ldg(cp + (pk + q) * 32);
+        v[q] = (AT)__ldg(vp + (pk + q) * 32);
+    }
+#pragma unroll
+    for (int q = 0; q < CNT; ++q)
+        if (pk + q < rl) sum += v[q] * load_as(x + c[q], AT());
+}
+
+// Phase 1, one thread per row, from the SELL-32 copy of A: w' = A u_i over the block (vector rows v0 .. v0+len,
+// whose matrix rows start the list block's first slice sb; warp rows kw .. kw+31 are slice sb + kw/32), fused with
+// storing w' (global W and the shared block copy), the window dot products acc_q += u_{lo+q}[r] * w'[r] and
+// ||u_i||^2.  Each row is summed in entry order, the warp issuing as many FMAs as its slice is wide.  The window
+// values and the next slice's extent are loaded before the row's SpMV, so they are in flight together.  Returns
+// the thread's largest exponent of w'.
 template <int NW, typename MT, typename VT, typename AT>
-__device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ rp, const int* __restrict__ col,
-                                                const MT* __restrict__ val, const VT* __restrict__ Ub, int i, int lo,
-                                                int v0, int len, int cs, AT* __restrict__ wblk, AT* __restrict__ W,
-                                                AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
+__device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ soff, const uint8_t* __restrict__ slen,
+                                              const int* __restrict__ scol, const MT* __restrict__ sval, int sb,
+                                              const VT* __restrict__ Ub, int i, int lo, int v0, int len, int cs,
+                                              AT* __restrict__ wblk, AT* __restrict__ W, AT (&acc)[NW > 0 ? NW : 1],
+                                              AT& nrm) {
     const int lane = threadIdx.x & 31;
     const VT* x = Ub + (int64_t)i * N;
-    const VT* xs = x + cs;                // gather base: vector index of matrix column c is c + cs
-    const int* rpm = rp + (v0 - cs);      // row pointers of the block's matrix rows
+    const VT* xs = x + cs;  // gather base: vector index of matrix column c is c + cs
     int emax = 1;
     int kw = threadIdx.x & ~31;
-    int a = 0, rl = 0;
-    if (kw + lane < len) {
-        a = __ldg(rpm + kw + lane);
-        rl = __ldg(rpm + kw + lane + 1) - a;
+    int o0 = 0, o1 = 0, rl = 0;
+    if (kw < len) {
+        const int sid = sb + (kw >> 5);
+        o0 = __ldg(soff + sid);
+        o1 = __ldg(soff + sid + 1);
+        rl = __ldg(slen + (int64_t)sid * 32 + lane);
     }
-    for (; kw < len; kw += blockDim.x) {  // warp-uniform loop over the block's rows
+    for (; kw < len; kw += blockDim.x) {  // warp-uniform loop over the block's slices
         const int k = kw + lane;
         const bool ok = k < len;
         const int r = v0 + k;
@@ -63,20 +86,29 @@ __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ r
         AT ui;  // u_i[r] (the last window vector when there is a window) for ||u_i||^2
         if constexpr (NW > 0) ui = uw[NW - 1];
         else ui = ok ? ld_plain(x + r) : AT(0);
-        const int kn = k + (int)blockDim.x;
-        int an = 0, rln = 0;
+        const int kn = kw + (int)blockDim.x;
+        int o0n = 0, o1n = 0, rln = 0;
         if (kn < len) {
-            an = __ldg(rpm + kn);
-            rln = __ldg(rpm + kn + 1) - an;
+            const int sid = sb + (kn >> 5);
+            o0n = __ldg(soff + sid);
+            o1n = __ldg(soff + sid + 1);
+            rln = __ldg(slen + (int64_t)sid * 32 + lane);
         }
-        const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)rl);
+        const int w = o1 - o0;
+        // every 128-byte line of the slice's columns and values requested at once (one line per lane; w <= 16
+        // entries, so at most 32 lines of FP64 values): the later chunks' loads then find their lines in flight
+        // instead of starting another round trip to memory each
+        if (lane < w) prefetch_l1(scol + (int64_t)(o0 + lane) * 32);
+        if (lane < w * (int)(sizeof(MT) / 4)) prefetch_l1(reinterpret_cast<const char*>(sval + (int64_t)o0 * 32) + lane * 128);
+        const int* cp = scol + (int64_t)o0 * 32 + lane;
+        const MT* vp = sval + (int64_t)o0 * 32 + lane;
         AT sum = AT(0);
-        for (int pk = 0; pk < maxlen; pk += 4) {
-            switch (min(maxlen - pk, 4)) {
-                case 1: row_chunk<1>(col, val, xs, a, rl, pk, sum); break;
-                case 2: row_chunk<2>(col, val, xs, a, rl, pk, sum); break;
-                case 3: row_chunk<3>(col, val, xs, a, rl, pk, sum); break;
-                default: row_chunk<4>(col, val, xs, a, rl, pk, sum); break;
+        for (int pk = 0; pk < w; pk += 4) {
+            switch (min(w - pk, 4)) {
+                case 1: sell_chunk<1>(cp, vp, xs, rl, pk, sum); break;
+                case 2: sell_chunk<2>(cp, vp, xs, rl, pk, sum); break;
+                case 3: sell_chunk<3>(cp, vp, xs, rl, pk, sum); break;
+                default: sell_chunk<4>(cp, vp, xs, rl, pk, sum); break;
             }
         }
         if (ok) {
@@ -87,7 +119,8 @@ __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ r
         for (int q = 0; q < NW; ++q) acc[q] += uw[q] * sum;
         nrm += ui * ui;
         emax = max(emax, exp_of(sum));
-        a = an;
+        o0 = o0n;
+        o1 = o1n;
         rl = rln;
     }
     return emax;
@@ -141,7 +174,8 @@ __global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __re
     int emax;
     AT nrm = AT(0);  // ||u_i||^2 over the block (the vector this step multiplies)
     if constexpr (V == 1) {
-        emax = spmv_dots_scalar<NW>(N, P.rp, P.col, val, Ub, i, lo, bi.v0, bi.len, bi.cs, wblk, W, acc, nrm);
+        emax = spmv_dots_sell<NW>(N, P.sl_off, P.sl_len, P.sl_col, val, P.sl_base[bi.list], Ub, i, lo, bi.v0,
+                                  bi.len, bi.cs, wblk, W, acc, nrm);
     } else {
         const int m0 = bi.v0 - bi.cs;
         int n0, n01;
@@ -803,10 +837,15 @@ static void inner_spmv_v(const Plan& p, int i, const MT* val) {
     k_inner_spmv<V, U, NW, MT, VT, AT><<<p.nblk, 512, sm, p.st>>>(p, i, val);
 }
 
+static const double* sell_values(const Plan& p, const double*) { return p.sl_val; }
+static const float* sell_values(const Plan& p, const float*) { return p.sl_val32; }
+
 template <int NW, typename MT, typename VT, typename AT>
 static void inner_spmv_nw(const Plan& p, int i, const MT* val) {
+    const MT* sv = sell_values(p, val);
     if (p.vec == 0) inner_spmv_v<0, 1, NW, MT, VT, AT>(p, i, val);
-    else if (p.vec == 1) inner_spmv_v<1, 1, NW, MT, VT, AT>(p, i, val);
+    else if (p.vec == 1 && p.sl_off && sv) inner_spmv_v<1, 1, NW, MT, VT, AT>(p, i, sv);  // SELL-32 copy
+    else if (p.vec == 1) inner_spmv_v<8, 4, NW, MT, VT, AT>(p, i, val);  // (no SELL-32 copy in this plan)
     else if (p.vec <= 8) inner_spmv_v<8, 4, NW, MT, VT, AT>(p, i, val);
     else inner_spmv_v<32, 2, NW, MT, VT, AT>(p, i, val);
 }

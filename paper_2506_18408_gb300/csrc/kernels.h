@@ -29,6 +29,14 @@ struct Plan {
     const double* val = nullptr;
     const float* val32 = nullptr;  // FP32 copy (inner FP32/BF16 modes)
     int vec = 8;                   // SpMV lanes per row (1 = one thread per row, 0 = length-binned)
+    // SELL-32 copy for the one-thread-per-row SpMV (vec == 1): slice widths as prefix sums in units of 32 entries,
+    // per-lane row lengths, columns and values in slice order, and the first slice of every list block
+    const int* sl_off = nullptr;
+    const uint8_t* sl_len = nullptr;
+    const int* sl_col = nullptr;
+    const double* sl_val = nullptr;
+    const float* sl_val32 = nullptr;
+    const int* sl_base = nullptr;
     const uint16_t* perm = nullptr;  // length-binned SpMV: per matrix row block, its rows in length order
     const int* cls = nullptr;        // [2 * list blocks]: rows with <= 16 entries, rows with <= 64 entries
 
@@ -187,6 +195,15 @@ void launch_pattern_outer(int n, const int* rp, const int* col, const double* u,
 // of rows with at most 16 and at most 64 entries.
 void launch_bin_rows(int nl, const int* rp, const int* lb_m0, const int* lb_len, uint16_t* perm, int* cls,
                      cudaStream_t st);
+// SELL-32 copy of a matrix whose rows have at most 255 entries: ns slices of 32 rows, slice s covering rows
+// moff[q] + 32 (s - sl0[q]) .. of system q (sl0: first slice of each system, nsys + 1 entries).  launch_sell_build
+// writes the row lengths len[ns * 32], the slice widths wid[ns] and their prefix sums off[ns + 1] (in units of 32
+// entries); launch_sell_fill writes columns (when scol is not null) and values in slice order.
+void launch_sell_build(int ns, const int* sl0, int nsys, const int* moff, const int* rp, uint8_t* len, int* wid,
+                       int* off, cudaStream_t st);
+void launch_sell_fill(int ns, const int* sl0, int nsys, const int* moff, const int* rp, const int* col,
+                      const double* val, const int* off, const uint8_t* len, int* scol, double* sval,
+                      cudaStream_t st);
 
 // Raise the dynamic shared-memory limit of kernel `func` to at least `bytes` (cached per kernel).
 void set_smem(const void* func, size_t bytes);

@@ -167,4 +167,74 @@ void launch_bin_rows(int nl, const int* rp, const int* lb_m0, const int* lb_len,
     ++g_launches;
 }
 
+// ---- SELL-32 copy of a matrix with short rows ----
+// Slice s holds rows moff[q] + 32 c .. of system q (c = s - sl0[q]); entry e of the slice's lane l sits at
+// (off[s] + e) * 32 + l, so the 32 lanes of a warp read entry e of their rows with one coalesced load.  A slice is
+// as wide as its longest row; a lane past its row's end (or past the system's last row) holds column 0, value 0,
+// and its length says so.
+
+__device__ __forceinline__ int sell_system(const int* __restrict__ sl0, int nsys, int64_t s) {
+    int lo = 0, hi = nsys - 1;  // the last q with sl0[q] <= s
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sl0[mid] <= s) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One warp per slice: row lengths and the slice width.
+__global__ void k_sell_len(int ns, const int* __restrict__ sl0, int nsys, const int* __restrict__ moff,
+                           const int* __restrict__ rp, uint8_t* __restrict__ len, int* __restrict__ wid) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = w0; s < ns; s += nwarps) {
+        const int q = sell_system(sl0, nsys, s);
+        const int r = moff[q] + 32 * (int)(s - sl0[q]) + lane;
+        const int l = (r < moff[q + 1]) ? rp[r + 1] - rp[r] : 0;
+        len[s * 32 + lane] = (uint8_t)l;
+        const int w = (int)__reduce_max_sync(0xffffffffu, (unsigned)l);
+        if (lane == 0) wid[s] = w;
+    }
+}
+
+// One warp per slice: columns and values in slice order (entry order within each row).
+__global__ void k_sell_fill(int ns, const int* __restrict__ sl0, int nsys, const int* __restrict__ moff,
+                            const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+                            const int* __restrict__ off, const uint8_t* __restrict__ len, int* __restrict__ scol,
+                            double* __restrict__ sval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = w0; s < ns; s += nwarps) {
+        const int q = sell_system(sl0, nsys, s);
+        const int r = moff[q] + 32 * (int)(s - sl0[q]) + lane;
+        const int l = len[s * 32 + lane];
+        const int a = (l > 0) ? rp[r] : 0;
+        const int64_t base = (int64_t)off[s] * 32 + lane;
+        const int w = off[s + 1] - off[s];
+        for (int e = 0; e < w; ++e) {
+            if (scol) scol[base + (int64_t)e * 32] = (e < l) ? col[a + e] : 0;
+            sval[base + (int64_t)e * 32] = (e < l) ? val[a + e] : 0.0;
+        }
+    }
+}
+
+static int sell_grid(int ns) { return (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)ns + 7) / 8, 152 * 64)); }
+
+void launch_sell_build(int ns, const int* sl0, int nsys, const int* moff, const int* rp, uint8_t* len, int* wid,
+                       int* off, cudaStream_t st) {
+    k_sell_len<<<sell_grid(ns), 256, 0, st>>>(ns, sl0, nsys, moff, rp, len, wid);
+    k_scan_plain<<<1, 1024, 0, st>>>(wid, off, ns);
+    g_launches += 2;
+}
+
+void launch_sell_fill(int ns, const int* sl0, int nsys, const int* moff, const int* rp, const int* col,
+                      const double* val, const int* off, const uint8_t* len, int* scol, double* sval,
+                      cudaStream_t st) {
+    k_sell_fill<<<sell_grid(ns), 256, 0, st>>>(ns, sl0, nsys, moff, rp, col, val, off, len, scol, sval);
+    ++g_launches;
+}
+
 }  // namespace sfg

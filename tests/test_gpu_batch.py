@@ -268,3 +268,29 @@ def test_persistent_cycle_matches_per_step_kernels(small, prec):
         for Aq, bp, xp in _per_problem(A, cfg.nrhs, b, res[pers][0]):
             assert _rel_res(Aq, bp, xp) <= cfg.tol
     assert all(abs(a - c) <= 1 for a, c in zip(res[1][1]["outer_iters_p"], res[0][1]["outer_iters_p"]))
+
+
+def test_profiled_solves_time_the_working_launches_with_and_without_graphs():
+    """Profiling puts the kernel timing events into the captured graphs: a profiled solve gives the same result as an
+    unprofiled one, with graphs (captured, then replayed) and without, and counts exactly the inner steps that built
+    a basis vector (the sum of k_j over the outer steps)."""
+    from paper_2506_18408_gb300 import Solver
+
+    mat = workloads.convdiff(64, (20.0, 10.0))
+    rhs = workloads.rhs(mat.n, seed=0)
+    sv = Solver(mat.n, mat.row_ptr, mat.col, mat.val, sketch_seed=1, max_outer=20)
+    bd = dev_vec(rhs)
+    x_ref, info_ref = sv.solve(bd, m=30, s=120, k=2, tol=1e-8)
+    assert info_ref["status"] == 0 and info_ref["n_inner_spmv"] == 0
+    for graph in (1, 1, 0):
+        sv.set("graph", graph)
+        sv.set("profile", 1)
+        x, info = sv.solve(bd, m=30, s=120, k=2, tol=1e-8)
+        sv.set("profile", 0)
+        assert info["status"] == 0
+        assert np.array_equal(x.cpu().numpy(), x_ref.cpu().numpy())
+        steps = int(sum(info["inner_k"]))
+        assert steps == info["total_inner"] == info_ref["total_inner"]
+        for key in ("inner_spmv", "inner_axpy", "qr"):
+            assert info["n_" + key] == steps
+            assert 0.0 < info["t_%s_ms" % key] < info["t_total_ms"]
