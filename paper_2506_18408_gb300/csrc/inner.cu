@@ -429,13 +429,33 @@ __global__ void __maxnreg__(sizeof(AT) == 8 ? 64 : 56) k_inner_spmv_grp(const Pl
 }
 
 // ---------------------------------------------------------------------------------------------------------------
+// Lane-strided sum of the per-block partials x[q * stride] for blocks q in [b0, b1) (lane l takes q = b0 + l,
+// b0 + l + 32, ... in increasing order, then a shuffle tree), with every load of a lane issued before the first add.
+template <typename AT>
+__device__ __forceinline__ AT block_partials_sum(const AT* __restrict__ x, int64_t stride, int b0, int b1, int lane) {
+    constexpr int U = 8;
+    AT a = AT(0);
+    for (int q0 = b0 + lane; q0 < b1; q0 += 32 * U) {
+        AT t[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) t[u] = (q0 + 32 * u < b1) ? x[(int64_t)(q0 + 32 * u) * stride] : AT(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (q0 + 32 * u < b1) a += t[u];
+    }
+    return warp_sum(a);
+}
+
 // Truncated-Arnoldi update (NW = window size).  Each thread first loads its first PF rows of w' and of the window
-// vectors (they do not depend on the scalars), then forms sigma_i, the coefficients and its share of the sketched
-// column of its problem, so the row data are already in flight while the reductions run.
+// vectors (they do not depend on the scalars); meanwhile warp 0 sums the problem's ||u_i||^2 partials and warps
+// 1..NW its window-dot partials, each with all loads in flight at once.  After one barrier thread 0 forms sigma_i
+// and the coefficients; after a second, the sketched column S A b_i (one warp per sketch row, rows spread over all
+// of the problem's blocks) and the row update.
 template <int NW, typename VT, typename AT>
-__global__ void __launch_bounds__(512) k_inner_axpy(const Plan P, int i, int last) {
-    constexpr int PF = 2;
+__global__ void __maxnreg__(56) k_inner_axpy(const Plan P, int i, int last) {
+    constexpr int PF = (sizeof(AT) == 8 && NW >= 5) ? 1 : 2;  // within 56 registers
     __shared__ AT coef_sh[kMaxTrunc];
+    __shared__ AT part_sh[kMaxTrunc + 1];
     __shared__ double sig_sh;
     __shared__ int stop_sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -459,69 +479,64 @@ __global__ void __launch_bounds__(512) k_inner_axpy(const Plan P, int i, int las
         }
     }
     if (threadIdx.x == 0) stop_sh = cycle_idle(P, p, i) ? 1 : 0;
+    const int b0 = P.prob_b0[p], b1 = P.prob_b0[p + 1];
+    // ||u_i||^2 (warp 0; sigma_0 is known at i = 0) and the window dots u_l^T w' (warp 1 + q) over the blocks
+    if (warp == 0 && i > 0) {
+        const AT a = block_partials_sum((const AT*)P.normpart, 1, b0, b1, lane);
+        if (lane == 0) part_sh[0] = a;
+    } else if (warp >= 1 && warp <= NW) {
+        const AT a = block_partials_sum((const AT*)P.hpart + (warp - 1), kMaxTrunc, b0, b1, lane);
+        if (lane == 0) part_sh[warp] = a;
+    }
     __syncthreads();
     if (stop_sh) return;
-    const int b0 = P.prob_b0[p], b1 = P.prob_b0[p + 1];
     const bool lead = (b == b0);  // the problem's first block writes its scalars
     double* sigma = P.sigma + (int64_t)p * (m + 1);
-    CycleState* cyc = P.cyc + p;
-    // sigma_i = 1/||u_i|| from the SpMV kernel's per-block partials
-    if (warp == 0) {
+    if (threadIdx.x == 0) {
+        // sigma_i = 1/||u_i||
         double sig = 1.0;
         bool bad = false;
         int why = 4;
         if (i == 0) {
             sig = sigma[0];
         } else {
-            AT a = AT(0);
-            const AT* np = (const AT*)P.normpart;
-            for (int q = b0 + lane; q < b1; q += 32) a += np[q];
-            a = warp_sum(a);
-            const double a2 = (double)a;
+            const double a2 = (double)part_sh[0];
             bad = !(a2 > 0.0) || !isfinite(a2);
             why = (a2 == 0.0) ? 4 : 6;
             sig = 1.0 / sqrt(a2);
         }
-        if (lane == 0) {
-            sig_sh = sig;
-            if (bad) {
-                stop_sh = 1;
-                if (lead) {
-                    cyc->brk_reason = why;
-                    atomicMin(&cyc->brk_step, i);
-                }
-            } else if (lead) {
-                sigma[i] = sig;
+        sig_sh = sig;
+        if (bad) {
+            stop_sh = 1;
+            if (lead) {
+                CycleState* cyc = P.cyc + p;
+                cyc->brk_reason = why;
+                atomicMin(&cyc->brk_step, i);
+            }
+        } else {
+            if (lead) sigma[i] = sig;
+            // h_l = sigma_l sigma_i (u_l^T w'); the stored update uses sigma_l^2 (u_l^T w')
+#pragma unroll
+            for (int q = 0; q < NW; ++q) {
+                const int l = lo + q;
+                const double a = (double)part_sh[1 + q];
+                const double sl = (l == i) ? sig : sigma[l];
+                coef_sh[q] = (AT)(sl * sl * a);
+                if (lead) P.hco[((int64_t)p * m + i) * kMaxTrunc + q] = sl * sig * a;
             }
         }
     }
     __syncthreads();
     if (stop_sh) return;
     const double sig_i = sig_sh;
-    // h_l = sigma_l sigma_i (u_l^T w'); the stored update uses sigma_l^2 (u_l^T w')
-    if (warp < NW) {
-        AT a = AT(0);
-        const AT* hp = (const AT*)P.hpart;
-        for (int q = b0 + lane; q < b1; q += 32) a += hp[(int64_t)q * kMaxTrunc + warp];
-        a = warp_sum(a);
-        if (lane == 0) {
-            const int l = lo + warp;
-            const double sl = (l == i) ? sig_i : sigma[l];
-            coef_sh[warp] = (AT)(sl * sl * (double)a);
-            if (lead) P.hco[((int64_t)p * m + i) * kMaxTrunc + warp] = sl * sig_i * (double)a;
-        }
-    }
-    // sketched column S A b_i = sigma_i S w': one warp per sketch row across the problem's blocks
+    // sketched column S A b_i = sigma_i S w': sketch row rr to warp rr / nb of the problem's block rr % nb
     const double csc = P.sk_scale * sig_i;
-    const AT* cp = (const AT*)P.cpart;
-    for (int rr = (b - b0) * nw + warp; rr < s; rr += (b1 - b0) * nw) {
-        AT a = AT(0);
-        for (int q = b0 + lane; q < b1; q += 32) a += cp[(int64_t)q * s + rr];
-        a = warp_sum(a);
+    const int nb = b1 - b0;
+    for (int rr = warp * nb + (b - b0); rr < s; rr += nw * nb) {
+        const AT a = block_partials_sum((const AT*)P.cpart + rr, s, b0, b1, lane);
         if (lane == 0) P.C[((int64_t)p * m + i) * s + rr] = csc * (double)a;
     }
     if (last) return;
-    __syncthreads();
     // u_{i+1} = 2^p2 (w' - sum_q coef_q u_{lo+q}), 2^p2 the power of two just below sigma_i
     int p2;
     frexp(sig_i, &p2);  // sigma_i = f * 2^p2, f in [0.5, 1)
