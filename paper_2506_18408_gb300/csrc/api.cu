@@ -73,13 +73,12 @@ struct sfgmres_ctx {
     double* valT = nullptr;
     float* val32T = nullptr;
     int maxlenT = 0, vecT = 8;
-    // SELL-32 copies of A ([0]) and A^T ([1]) for the one-thread-per-row inner SpMV, built on first use
+    // SELL-32 copies of A ([0]) and A^T ([1]) for the one-thread-per-row FP64 inner SpMV, built on first use
     struct Sell {
         int* off = nullptr;
         uint8_t* len = nullptr;
         int* col = nullptr;
         double* val = nullptr;
-        float* val32 = nullptr;
         int64_t total = 0;  // entries, padding included
     } sell[2];
     int sl_ns = 0;                 // slices (the same for A and A^T: block-diagonal with the same blocks)
@@ -526,9 +525,10 @@ int ensure_bins(sfgmres_ctx* h, bool transpose) {
     return 0;
 }
 
-// SELL-32 copy of A (or A^T) for the one-thread-per-row inner SpMV, with its FP32 values when need32; the list
-// blocks' first slices follow the row-block geometry.
-int ensure_sell(sfgmres_ctx* h, bool transpose, bool need32) {
+// SELL-32 copy of A (or A^T) for the one-thread-per-row FP64 inner SpMV (measured faster there; the FP32 inner
+// kernel keeps the CSR arrays, which measured as fast or faster); the list blocks' first slices follow the
+// row-block geometry.
+int ensure_sell(sfgmres_ctx* h, bool transpose) {
     sfgmres_ctx::Sell& S = h->sell[transpose ? 1 : 0];
     const int* rp = transpose ? h->rpT : h->rp;
     const int* col = transpose ? h->colT : h->col;
@@ -567,12 +567,6 @@ int ensure_sell(sfgmres_ctx* h, bool transpose, bool need32) {
         launch_sell_fill(ns, sl0, h->nsys, moff, rp, col, val, S.off, S.len, S.col, S.val, h->st);
         CK(cudaGetLastError());
     }
-    if (need32 && !S.val32) {
-        CK(cudaMalloc(&S.val32, std::max<int64_t>(S.total, 1) * sizeof(float)));
-        k_to_f32<<<grid_for(S.total), 256, 0, h->st>>>(S.total, S.val, S.val32);
-        ++g_launches;
-        CK(cudaGetLastError());
-    }
     if (h->sl_base_ver != h->geo_ver) {
         std::vector<int> hb((size_t)std::max(h->nl, 1), 0);
         int ns0 = 0;
@@ -601,12 +595,11 @@ void plan_geometry(sfgmres_ctx* h, const Geo* g, bool transpose, Plan& P) {
     P.perm = (P.vec == 0) ? h->perm[transpose ? 1 : 0] : nullptr;
     P.cls = (P.vec == 0) ? h->cls[transpose ? 1 : 0] : nullptr;
     const sfgmres_ctx::Sell& S = h->sell[transpose ? 1 : 0];
-    const bool sl = (P.vec == 1) && S.off && h->sl_base_ver == h->geo_ver;
+    const bool sl = (P.vec == 1) && h->prec == kFP64 && S.off && h->sl_base_ver == h->geo_ver;
     P.sl_off = sl ? S.off : nullptr;
     P.sl_len = sl ? S.len : nullptr;
     P.sl_col = sl ? S.col : nullptr;
     P.sl_val = sl ? S.val : nullptr;
-    P.sl_val32 = sl ? S.val32 : nullptr;
     P.sl_base = sl ? h->sl_base : nullptr;
     P.N = g->N;
     P.P = g->P;
@@ -671,7 +664,7 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     {
         const int v = transpose ? (h->vec_opt ? h->vec_opt : h->vecT) : h->vec;
         if (v == 0 && (rc = ensure_bins(h, transpose))) return rc;
-        if (v == 1 && (rc = ensure_sell(h, transpose, h->prec != kFP64))) return rc;
+        if (v == 1 && h->prec == kFP64 && (rc = ensure_sell(h, transpose))) return rc;
     }
     const size_t vt = (h->prec == kFP64) ? 8 : (h->prec == kFP32 ? 4 : 2);
     const size_t at = (h->prec == kFP64) ? 8 : 4;
@@ -886,7 +879,7 @@ std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
     for (const void* p : std::initializer_list<const void*>{(const void*)P.grp_b, (const void*)P.perm, (const void*)P.cls,
                                                             (const void*)P.rp, (const void*)P.col, (const void*)P.val, (const void*)P.val32,
                           (const void*)P.blk_v0, (const void*)P.seg, (const void*)P.sl_off, (const void*)P.sl_col,
-                          (const void*)P.sl_val, (const void*)P.sl_val32, (const void*)P.sl_base, (const void*)P.sl_len, (const void*)P.ent, P.U, P.W,
+                          (const void*)P.sl_val, (const void*)P.sl_base, (const void*)P.sl_len, (const void*)P.ent, P.U, P.W,
                           (const void*)P.sigma, P.normpart, P.hpart, P.cpart, (const void*)P.C, (const void*)P.Q,
                           (const void*)P.R, (const void*)P.d, (const void*)P.e, (const void*)P.c0,
                           (const void*)P.rho, (const void*)P.y, (const void*)P.coef, (const void*)P.hco,
@@ -1370,7 +1363,7 @@ int sfgmres_destroy(sfgmres_t h) {
     }
     if (h->lb) cudaFree(h->lb);
     for (auto& S : h->sell)
-        for (void* q : {(void*)S.off, (void*)S.len, (void*)S.col, (void*)S.val, (void*)S.val32})
+        for (void* q : {(void*)S.off, (void*)S.len, (void*)S.col, (void*)S.val})
             if (q) cudaFree(q);
     if (h->sl_sys) cudaFree(h->sl_sys);
     if (h->sl_base) cudaFree(h->sl_base);
@@ -1652,7 +1645,6 @@ int sfgmres_update_values(sfgmres_t h, const double* vals) {
         if (!S.off) continue;
         launch_sell_fill(h->sl_ns, h->sl_sys, h->nsys, h->sl_sys + h->nsys + 1, t ? h->rpT : h->rp, nullptr,
                          t ? h->valT : h->val, S.off, S.len, nullptr, S.val, h->st);
-        if (S.val32) k_to_f32<<<grid_for(S.total), 256, 0, h->st>>>(S.total, S.val, S.val32);
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->st));

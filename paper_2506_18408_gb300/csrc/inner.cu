@@ -27,6 +27,10 @@ namespace cg = cooperative_groups;
 
 namespace sfg {
 
+// Template value of k_inner_spmv's lanes-per-row parameter for one thread per row reading the SELL-32 copy of A
+// (the FP64 inner cycle); 1 is one thread per row reading the CSR arrays.
+constexpr int kVecSell = -1;
+
 __device__ __forceinline__ bool cycle_idle(const Plan& P, int p, int i) {
     const CycleState* c = P.cyc + p;
     return c->stopped || c->brk_step <= i || (P.pflag[p] & 1);
@@ -126,6 +130,67 @@ __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ sof
     return emax;
 }
 
+// ---------------------------------------------------------------------------------------------------------------
+// Phase 1, one thread per row: w' = A u_i over the block (vector rows v0 .. v0+len = matrix rows v0-cs ..) fused
+// with storing w' (global W and the shared block copy), the window dot products acc_q += u_{lo+q}[r] * w'[r] and
+// ||u_i||^2.  The window values and the next row group's extents are loaded before the row's SpMV, so they are in
+// flight together.  Returns the thread's largest exponent of w'.
+template <int NW, typename MT, typename VT, typename AT>
+__device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ rp, const int* __restrict__ col,
+                                                const MT* __restrict__ val, const VT* __restrict__ Ub, int i, int lo,
+                                                int v0, int len, int cs, AT* __restrict__ wblk, AT* __restrict__ W,
+                                                AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
+    const int lane = threadIdx.x & 31;
+    const VT* x = Ub + (int64_t)i * N;
+    const VT* xs = x + cs;                // gather base: vector index of matrix column c is c + cs
+    const int* rpm = rp + (v0 - cs);      // row pointers of the block's matrix rows
+    int emax = 1;
+    int kw = threadIdx.x & ~31;
+    int a = 0, rl = 0;
+    if (kw + lane < len) {
+        a = __ldg(rpm + kw + lane);
+        rl = __ldg(rpm + kw + lane + 1) - a;
+    }
+    for (; kw < len; kw += blockDim.x) {  // warp-uniform loop over the block's rows
+        const int k = kw + lane;
+        const bool ok = k < len;
+        const int r = v0 + k;
+        AT uw[NW > 0 ? NW : 1];
+#pragma unroll
+        for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
+        AT ui;  // u_i[r] (the last window vector when there is a window) for ||u_i||^2
+        if constexpr (NW > 0) ui = uw[NW - 1];
+        else ui = ok ? ld_plain(x + r) : AT(0);
+        const int kn = k + (int)blockDim.x;
+        int an = 0, rln = 0;
+        if (kn < len) {
+            an = __ldg(rpm + kn);
+            rln = __ldg(rpm + kn + 1) - an;
+        }
+        const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)rl);
+        AT sum = AT(0);
+        for (int pk = 0; pk < maxlen; pk += 4) {
+            switch (min(maxlen - pk, 4)) {
+                case 1: row_chunk<1>(col, val, xs, a, rl, pk, sum); break;
+                case 2: row_chunk<2>(col, val, xs, a, rl, pk, sum); break;
+                case 3: row_chunk<3>(col, val, xs, a, rl, pk, sum); break;
+                default: row_chunk<4>(col, val, xs, a, rl, pk, sum); break;
+            }
+        }
+        if (ok) {
+            W[r] = sum;
+            wblk[k] = sum;
+        }
+#pragma unroll
+        for (int q = 0; q < NW; ++q) acc[q] += uw[q] * sum;
+        nrm += ui * ui;
+        emax = max(emax, exp_of(sum));
+        a = an;
+        rl = rln;
+    }
+    return emax;
+}
+
 // Phase 1 tail for the sub-warp path (w' already in shared memory): store w', accumulate the window dots and
 // ||u_i||^2.
 template <int NW, typename VT, typename AT>
@@ -173,9 +238,11 @@ __global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __re
     for (int q = 0; q < NW; ++q) acc[q] = AT(0);
     int emax;
     AT nrm = AT(0);  // ||u_i||^2 over the block (the vector this step multiplies)
-    if constexpr (V == 1) {
+    if constexpr (V == kVecSell) {
         emax = spmv_dots_sell<NW>(N, P.sl_off, P.sl_len, P.sl_col, val, P.sl_base[bi.list], Ub, i, lo, bi.v0,
                                   bi.len, bi.cs, wblk, W, acc, nrm);
+    } else if constexpr (V == 1) {
+        emax = spmv_dots_scalar<NW>(N, P.rp, P.col, val, Ub, i, lo, bi.v0, bi.len, bi.cs, wblk, W, acc, nrm);
     } else {
         const int m0 = bi.v0 - bi.cs;
         int n0, n01;
@@ -433,7 +500,7 @@ __global__ void __maxnreg__(sizeof(AT) == 8 ? 64 : 56) k_inner_spmv_grp(const Pl
 // b0 + l + 32, ... in increasing order, then a shuffle tree), with every load of a lane issued before the first add.
 template <typename AT>
 __device__ __forceinline__ AT block_partials_sum(const AT* __restrict__ x, int64_t stride, int b0, int b1, int lane) {
-    constexpr int U = 8;
+    constexpr int U = 4;
     AT a = AT(0);
     for (int q0 = b0 + lane; q0 < b1; q0 += 32 * U) {
         AT t[U];
@@ -451,9 +518,11 @@ __device__ __forceinline__ AT block_partials_sum(const AT* __restrict__ x, int64
 // 1..NW its window-dot partials, each with all loads in flight at once.  After one barrier thread 0 forms sigma_i
 // and the coefficients; after a second, the sketched column S A b_i (one warp per sketch row, rows spread over all
 // of the problem's blocks) and the row update.
+// Three 512-thread CTAs per SM (at most 42 registers; batches run many waves of blocks) for windows up to 3, two
+// for wider windows, which would spill within 42.
 template <int NW, typename VT, typename AT>
-__global__ void __maxnreg__(56) k_inner_axpy(const Plan P, int i, int last) {
-    constexpr int PF = (sizeof(AT) == 8 && NW >= 5) ? 1 : 2;  // within 56 registers
+__global__ void __launch_bounds__(512, (NW <= 3) ? 3 : 2) k_inner_axpy(const Plan P, int i, int last) {
+    constexpr int PF = (sizeof(AT) == 8 && NW >= 5) ? 1 : 2;
     __shared__ AT coef_sh[kMaxTrunc];
     __shared__ AT part_sh[kMaxTrunc + 1];
     __shared__ double sig_sh;
@@ -852,15 +921,18 @@ static void inner_spmv_v(const Plan& p, int i, const MT* val) {
     k_inner_spmv<V, U, NW, MT, VT, AT><<<p.nblk, 512, sm, p.st>>>(p, i, val);
 }
 
-static const double* sell_values(const Plan& p, const double*) { return p.sl_val; }
-static const float* sell_values(const Plan& p, const float*) { return p.sl_val32; }
-
 template <int NW, typename MT, typename VT, typename AT>
 static void inner_spmv_nw(const Plan& p, int i, const MT* val) {
-    const MT* sv = sell_values(p, val);
     if (p.vec == 0) inner_spmv_v<0, 1, NW, MT, VT, AT>(p, i, val);
-    else if (p.vec == 1 && p.sl_off && sv) inner_spmv_v<1, 1, NW, MT, VT, AT>(p, i, sv);  // SELL-32 copy
-    else if (p.vec == 1) inner_spmv_v<8, 4, NW, MT, VT, AT>(p, i, val);  // (no SELL-32 copy in this plan)
+    else if (p.vec == 1) {
+        if constexpr (sizeof(MT) == 8) {
+            if (p.sl_off) {  // FP64 with the SELL-32 copy
+                inner_spmv_v<kVecSell, 1, NW, MT, VT, AT>(p, i, p.sl_val);
+                return;
+            }
+        }
+        inner_spmv_v<1, 1, NW, MT, VT, AT>(p, i, val);
+    }
     else if (p.vec <= 8) inner_spmv_v<8, 4, NW, MT, VT, AT>(p, i, val);
     else inner_spmv_v<32, 2, NW, MT, VT, AT>(p, i, val);
 }

@@ -29,13 +29,13 @@ struct Plan {
     const double* val = nullptr;
     const float* val32 = nullptr;  // FP32 copy (inner FP32/BF16 modes)
     int vec = 8;                   // SpMV lanes per row (1 = one thread per row, 0 = length-binned)
-    // SELL-32 copy for the one-thread-per-row SpMV (vec == 1): slice widths as prefix sums in units of 32 entries,
-    // per-lane row lengths, columns and values in slice order, and the first slice of every list block
+    // SELL-32 copy for the one-thread-per-row FP64 inner SpMV (vec == 1, FP64 inner cycles): slice widths as prefix
+    // sums in units of 32 entries, per-lane row lengths, columns and values in slice order, and the first slice of
+    // every list block
     const int* sl_off = nullptr;
     const uint8_t* sl_len = nullptr;
     const int* sl_col = nullptr;
     const double* sl_val = nullptr;
-    const float* sl_val32 = nullptr;
     const int* sl_base = nullptr;
     const uint16_t* perm = nullptr;  // length-binned SpMV: per matrix row block, its rows in length order
     const int* cls = nullptr;        // [2 * list blocks]: rows with <= 16 entries, rows with <= 64 entries
