@@ -92,6 +92,14 @@ extern "C" {
                                         GB300 for these sizes.  Both compute the method's sums; the order of the
                                         cross-block sums differs.  SFGMRES_OPT_PROFILE = 1 uses the per-step
                                         kernels. */
+#define SFGMRES_OPT_FUSED_STEP 13    /* 1 (default): where all row blocks of a plan fit on the GPU at once (one system
+                                        of up to about 2 x SMs blocks) and the truncation window is at most 4, each
+                                        inner step runs as one launch: the inner SpMV kernel's work, a grid-wide
+                                        arrival of every CTA, then the Arnoldi update of the CTA's own rows (the same
+                                        arithmetic in the same order, so results are identical).  The wait is bounded;
+                                        if it gives up the solve returns SFGMRES_ERR_CUDA.  With profiling on, the
+                                        fused launch is reported as the inner SpMV kernel (t_inner_spmv_ms) and the
+                                        update's fields stay 0.  0: two launches per step. */
 /* ---- sfgmres_solve_batch flags ---------------------------------------------------------------------------- */
 #define SFGMRES_SOLVE_TRANSPOSE 1    /* solve A_q^T x = b for every problem (see sfgmres_solve_transpose) */
 

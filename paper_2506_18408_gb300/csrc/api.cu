@@ -99,6 +99,8 @@ struct sfgmres_ctx {
     int use_graph = 1;
     int persistent = 0;  // 1: whole-cycle persistent kernel where the plan allows it
     int rhs_group = 1;  // right-hand sides per grouped inner-SpMV CTA (1: not grouped)
+    int fuse_step = 1;  // 1: one launch per inner step where the row blocks fit on the GPU at once
+    bool step_fused = false;  // the last cycle ran the fused inner step
     double cond_thr = 1e15;
 
     // list-block geometry (depends on the systems and the block-rows option; version bumps on change)
@@ -127,6 +129,7 @@ struct sfgmres_ctx {
     DevBuf Vb, Z, nu, Wo, opart, npart, npart2, h1, h2, H, cs, sn, g, yo, est_hist, ffom_hist, k_hist, reason_hist,
         ost;
     DevBuf bst, xst, x0st;  // staging / internal copies
+    DevBuf gsync;           // fused inner step: grid arrival counter and give-up flag (2 x u64)
 
     // pinned host mirrors of the per-problem device state
     HostBuf h_ost, h_cyc, h_pflag;
@@ -783,6 +786,13 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     P.k_hist = (int*)h->k_hist.p;
     P.reason_hist = (int*)h->reason_hist.p;
     P.ost = (OuterState*)h->ost.p;
+    P.sms = h->sms;
+    if (h->fuse_step) {
+        if ((rc = ensure(h, h->gsync, 2 * sizeof(unsigned long long)))) return rc;
+        P.gsync = (unsigned long long*)h->gsync.p;
+    } else {
+        P.gsync = nullptr;
+    }
     if (geo_out) *geo_out = g;
     return 0;
 }
@@ -852,14 +862,19 @@ int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const doubl
         return 0;
     }
     const bool prof = (ev != SIZE_MAX);
+    h->step_fused = false;
     for (int i = 0; i < P.m; ++i) {
         const bool last = (i == P.m - 1);
         if (prof) ev_rec(h->ev_spmv[ev + i].a, h->st, capturing);
-        launch_inner_spmv(P, i);
+        const bool fused = launch_inner_step(P, i, last);  // one launch, timed as the inner kernel
+        if (!fused) launch_inner_spmv(P, i);
         if (prof) ev_rec(h->ev_spmv[ev + i].b, h->st, capturing);
-        if (prof) ev_rec(h->ev_axpy[ev + i].a, h->st, capturing);
-        launch_inner_axpy(P, i, last);
-        if (prof) ev_rec(h->ev_axpy[ev + i].b, h->st, capturing);
+        if (!fused) {
+            if (prof) ev_rec(h->ev_axpy[ev + i].a, h->st, capturing);
+            launch_inner_axpy(P, i, last);
+            if (prof) ev_rec(h->ev_axpy[ev + i].b, h->st, capturing);
+        }
+        h->step_fused |= fused;
         CK(cudaEventRecord(h->ev_c, h->st));
         CK(cudaStreamWaitEvent(h->qst, h->ev_c, 0));
         if (prof) ev_rec(h->ev_qr[ev + i].a, h->qst, capturing);
@@ -888,7 +903,7 @@ std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
                           (const void*)P.h1, (const void*)P.h2, (const void*)P.H, (const void*)P.cs,
                           (const void*)P.sn, (const void*)P.g, (const void*)P.yo, (const void*)P.est_hist,
                           (const void*)P.ffom_hist, (const void*)P.k_hist, (const void*)P.reason_hist,
-                          (const void*)P.ost, (const void*)P.st, (const void*)h->qst})
+                          (const void*)P.ost, (const void*)P.st, (const void*)h->qst, (const void*)P.gsync})
         u(p);
     for (int64_t v : std::initializer_list<int64_t>{(int64_t)P.G, (int64_t)P.ngrp, (int64_t)P.nnz, (int64_t)P.vec, (int64_t)P.N, (int64_t)P.P, (int64_t)P.nblk, (int64_t)P.Bn,
                       (int64_t)P.s, (int64_t)P.zeta, (int64_t)P.kind, (int64_t)P.sk_headroom, (int64_t)P.prec,
@@ -989,7 +1004,7 @@ struct ProbOut {
     int status = SFGMRES_NOT_CONVERGED;
     int outer = 0;
     double rel_true = 0.0, rel_est = 0.0;
-    bool done = false, brk = false, nan_init = false;
+    bool done = false, brk = false, nan_init = false, sync_fail = false;
 };
 
 struct SolveOut {
@@ -999,12 +1014,14 @@ struct SolveOut {
 };
 
 int status_of(const std::vector<ProbOut>& pr) {
-    bool nc = false, brk = false, nan = false;
+    bool nc = false, brk = false, nan = false, cuda = false;
     for (const ProbOut& o : pr) {
+        cuda |= (o.status == SFGMRES_ERR_CUDA);
         nan |= (o.status == SFGMRES_ERR_NAN);
         nc |= (o.status == SFGMRES_NOT_CONVERGED);
         brk |= (o.status == SFGMRES_BREAKDOWN);
     }
+    if (cuda) return SFGMRES_ERR_CUDA;
     if (nan) return SFGMRES_ERR_NAN;
     if (nc) return SFGMRES_NOT_CONVERGED;
     if (brk) return SFGMRES_BREAKDOWN;
@@ -1098,7 +1115,8 @@ int solve_core(sfgmres_t h, bool transpose, int nrhs, const double* b, const dou
             if (o.done) continue;
             const OuterState& os = host_ost[p];
             if (os.nan) {
-                o.status = SFGMRES_ERR_NAN;
+                o.status = os.sync_fail ? SFGMRES_ERR_CUDA : SFGMRES_ERR_NAN;
+                o.sync_fail = os.sync_fail != 0;
                 o.done = true;
                 hflag[p] |= 1;
                 changed = true;
@@ -1167,6 +1185,7 @@ int solve_single(sfgmres_t h, bool transpose, const double* b, const double* x0,
     if ((rc = solve_core(h, transpose, 1, b, x0, x, m, s, k, tol, &so))) return rc;
     const ProbOut& o = so.pr[0];
     const int status = o.status;
+    if (status == SFGMRES_ERR_CUDA) return fail(h, SFGMRES_ERR_CUDA, "the fused inner step's grid-wide wait gave up");
     if (status == SFGMRES_ERR_NAN) {
         return fail(h, SFGMRES_ERR_NAN, o.nan_init ? "non-finite value in b or x0 (or in A x0)"
                                                    : "non-finite value during the iteration");
@@ -1210,10 +1229,12 @@ int solve_single(sfgmres_t h, bool transpose, const double* b, const double* x0,
                 if (js.first >= cnt) continue;
                 const size_t kw = (size_t)std::max(0, std::min(kh[js.first], P.m));
                 st->t_inner_spmv_ms += ev_sum(h->ev_spmv, js.second, kw);
-                st->t_inner_axpy_ms += ev_sum(h->ev_axpy, js.second, kw);
                 st->t_qr_ms += ev_sum(h->ev_qr, js.second, kw);
                 st->n_inner_spmv += (int64_t)kw;
-                st->n_inner_axpy += (int64_t)kw;
+                if (!h->step_fused) {
+                    st->t_inner_axpy_ms += ev_sum(h->ev_axpy, js.second, kw);
+                    st->n_inner_axpy += (int64_t)kw;
+                }
                 st->n_qr += (int64_t)kw;
             }
         } else {
@@ -1371,7 +1392,7 @@ int sfgmres_destroy(sfgmres_t h) {
                       &h->e, &h->c0, &h->rho, &h->y, &h->coef, &h->hco, &h->cyc, &h->Vb, &h->Z, &h->nu, &h->Wo,
                       &h->opart, &h->npart, &h->npart2, &h->h1, &h->h2, &h->H, &h->cs, &h->sn, &h->g, &h->yo,
                       &h->est_hist, &h->ffom_hist, &h->k_hist, &h->reason_hist, &h->ost, &h->bst, &h->xst,
-                      &h->x0st};
+                      &h->x0st, &h->gsync};
     for (DevBuf* b : bufs) release(*b);
     for (Geo& g : h->geos) {
         release(g.tab);
@@ -1451,6 +1472,10 @@ int sfgmres_set_option(sfgmres_t h, int32_t key, double v) {
                 set_list_geometry(h);
             }
             return 0;
+        case SFGMRES_OPT_FUSED_STEP:
+            if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "fused step must be 0 or 1");
+            h->fuse_step = iv;
+            return 0;
         case SFGMRES_OPT_GRAPH:
             if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "graph must be 0 or 1");
             h->use_graph = iv;
@@ -1483,6 +1508,7 @@ int sfgmres_get_option(sfgmres_t h, int32_t key, double* v) {
         case SFGMRES_OPT_GRAPH: *v = h->use_graph; return 0;
         case SFGMRES_OPT_RHS_GROUP: *v = h->rhs_group; return 0;
         case SFGMRES_OPT_PERSISTENT: *v = h->persistent; return 0;
+        case SFGMRES_OPT_FUSED_STEP: *v = h->fuse_step; return 0;
         default: return fail(h, SFGMRES_ERR_INVALID_ARG, "unknown option key");
     }
 }
@@ -1509,6 +1535,7 @@ int sfgmres_solve_batch(sfgmres_t h, int32_t nrhs, const double* b, const double
     SolveOut so;
     if ((rc = solve_core(h, (flags & SFGMRES_SOLVE_TRANSPOSE) != 0, nrhs, b, x0, x, m, s, k, tol, &so))) return rc;
     const int status = status_of(so.pr);
+    if (status == SFGMRES_ERR_CUDA) fail(h, SFGMRES_ERR_CUDA, "the fused inner step's grid-wide wait gave up");
     if (status == SFGMRES_ERR_NAN) {
         int first = 0;
         while (so.pr[first].status != SFGMRES_ERR_NAN) ++first;
@@ -1677,6 +1704,11 @@ int sfgmres_inner_cycle(sfgmres_t h, const double* v, double* z, int32_t m, int3
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
     const CycleState cs = *hc;
+    if (P.gsync) {
+        unsigned long long gave_up = 0;
+        CK(cudaMemcpy(&gave_up, P.gsync + 1, sizeof(gave_up), cudaMemcpyDeviceToHost));
+        if (gave_up) return fail(h, SFGMRES_ERR_CUDA, "the fused inner step's grid-wide wait gave up");
+    }
     *k_out = cs.k;
     if (reason_out) *reason_out = cs.reason;
     if (cs.reason == 6) return fail(h, SFGMRES_ERR_NAN, "non-finite value in the inner cycle");

@@ -258,6 +258,7 @@ struct OuterState {
     int conv_est;     // the Givens estimate met the tolerance at the last step
     int breakdown;    // h_{j+1,j} == 0 (exact) at the last step
     int nan;          // NaN/Inf seen in a reduction
+    int sync_fail;    // the fused inner step's grid-wide wait gave up during the last inner cycle
     double beta;      // ||r0||
     double bnorm;     // ||b||
     double est;       // |g_{j+1}|

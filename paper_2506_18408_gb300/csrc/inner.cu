@@ -217,17 +217,17 @@ __device__ __forceinline__ int dots_pass(int N, int v0, int len, const VT* __res
 // converted in place to its 64-bit fixed-point image before the sketch sums.
 // At most 56 registers per thread (registers are allocated in units of 8 per thread): two 512-thread CTAs per SM
 // then leave room for the sketched-QR cluster's CTAs to run beside them instead of displacing them.
+// Returns false (every thread of the CTA alike) when the block's problem has no step i to take.
 template <int V, int U, int NW, typename MT, typename VT, typename AT>
-__global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __restrict__ val) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    AT* wblk = reinterpret_cast<AT*>(smem_raw);
+__device__ __forceinline__ bool inner_spmv_block(const Plan& P, int i, const MT* __restrict__ val,
+                                                 AT* __restrict__ wblk) {
     __shared__ AT red[512];
     __shared__ int stop_sh, emax_sh[16];
     const int b = blockIdx.x;
     const BlockInfo bi = block_info(P, b);
     if (threadIdx.x == 0) stop_sh = cycle_idle(P, bi.prob, i) ? 1 : 0;
     __syncthreads();
-    if (stop_sh) return;
+    if (stop_sh) return false;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int s = P.s, Bn = P.Bn, N = P.N;
     const VT* Ub = (const VT*)P.U;
@@ -296,6 +296,13 @@ __global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __re
         for (int rr = threadIdx.x; rr < s; rr += blockDim.x)
             cpart[(int64_t)b * s + rr] = sum_list(P.ent, sg[rr], sg[rr + 1], wblk);
     }
+    return true;
+}
+
+template <int V, int U, int NW, typename MT, typename VT, typename AT>
+__global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __restrict__ val) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    inner_spmv_block<V, U, NW, MT, VT, AT>(P, i, val, reinterpret_cast<AT*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------------------------------------------
@@ -496,8 +503,25 @@ __global__ void __maxnreg__(sizeof(AT) == 8 ? 64 : 56) k_inner_spmv_grp(const Pl
 }
 
 // ---------------------------------------------------------------------------------------------------------------
+// Waits until the grid counter reaches target (acquire), polling with a growing sleep; after kGridWaitPolls polls it
+// gives up and sets *fail.
+constexpr int kGridWaitPolls = 1 << 22;  // >= 1 s at the 256 ns cap
+__device__ __forceinline__ void grid_wait(unsigned long long* ctr, unsigned long long target, unsigned long long* fail) {
+    unsigned ns = 32;
+    for (int it = 0; it < kGridWaitPolls; ++it) {
+        unsigned long long v;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+        if (v >= target) return;
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+    }
+    atomicOr(fail, 1ull);
+}
+
+// ---------------------------------------------------------------------------------------------------------------
 // Lane-strided sum of the per-block partials x[q * stride] for blocks q in [b0, b1) (lane l takes q = b0 + l,
 // b0 + l + 32, ... in increasing order, then a shuffle tree), with every load of a lane issued before the first add.
+// The loads bypass L1: in the fused step the partials come from other CTAs of the same launch.
 template <typename AT>
 __device__ __forceinline__ AT block_partials_sum(const AT* __restrict__ x, int64_t stride, int b0, int b1, int lane) {
     constexpr int U = 4;
@@ -505,7 +529,7 @@ __device__ __forceinline__ AT block_partials_sum(const AT* __restrict__ x, int64
     for (int q0 = b0 + lane; q0 < b1; q0 += 32 * U) {
         AT t[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) t[u] = (q0 + 32 * u < b1) ? x[(int64_t)(q0 + 32 * u) * stride] : AT(0);
+        for (int u = 0; u < U; ++u) t[u] = (q0 + 32 * u < b1) ? __ldcg(x + (int64_t)(q0 + 32 * u) * stride) : AT(0);
 #pragma unroll
         for (int u = 0; u < U; ++u)
             if (q0 + 32 * u < b1) a += t[u];
@@ -520,8 +544,12 @@ __device__ __forceinline__ AT block_partials_sum(const AT* __restrict__ x, int64
 // of the problem's blocks) and the row update.
 // Three 512-thread CTAs per SM (at most 42 registers; batches run many waves of blocks) for windows up to 3, two
 // for wider windows, which would spill within 42.
-template <int NW, typename VT, typename AT>
-__global__ void __launch_bounds__(512, (NW <= 3) ? 3 : 2) k_inner_axpy(const Plan P, int i, int last) {
+// wsm: the block of w' in shared memory (the fused step, FP32/BF16), else null (w' read from W).  FUSED: the block's
+// partials of this step come from other CTAs of the same launch; thread 0 waits for all of them (target arrivals
+// at the step's grid counter) after the prefetch.
+template <int NW, typename VT, typename AT, bool FUSED>
+__device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last, const AT* __restrict__ wsm,
+                                                 unsigned long long target) {
     constexpr int PF = (sizeof(AT) == 8 && NW >= 5) ? 1 : 2;
     __shared__ AT coef_sh[kMaxTrunc];
     __shared__ AT part_sh[kMaxTrunc + 1];
@@ -541,11 +569,15 @@ __global__ void __launch_bounds__(512, (NW <= 3) ? 3 : 2) k_inner_axpy(const Pla
         for (int u = 0; u < PF; ++u) {
             const int k = threadIdx.x + u * (int)blockDim.x;
             const int r = bi.v0 + k;
-            wv[u] = (k < bi.len) ? W[r] : AT(0);
+            wv[u] = (k < bi.len) ? (wsm ? wsm[k] : W[r]) : AT(0);
 #pragma unroll
             for (int q = 0; q < NW; ++q)
                 uv[u][q] = (k < bi.len) ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
         }
+    }
+    if constexpr (FUSED) {
+        if (threadIdx.x == 0) grid_wait(P.gsync, target, P.gsync + 1);
+        __syncthreads();
     }
     if (threadIdx.x == 0) stop_sh = cycle_idle(P, p, i) ? 1 : 0;
     const int b0 = P.prob_b0[p], b1 = P.prob_b0[p + 1];
@@ -633,8 +665,37 @@ __global__ void __launch_bounds__(512, (NW <= 3) ? 3 : 2) k_inner_axpy(const Pla
         AT uq[NW > 0 ? NW : 1];
 #pragma unroll
         for (int q = 0; q < NW; ++q) uq[q] = ld_plain(Ub + (int64_t)(lo + q) * N + r);
-        update(r, W[r], uq);
+        update(r, wsm ? wsm[k] : W[r], uq);
     }
+}
+
+template <int NW, typename VT, typename AT>
+__global__ void __launch_bounds__(512, (NW <= 3) ? 3 : 2) k_inner_axpy(const Plan P, int i, int last) {
+    inner_axpy_block<NW, VT, AT, false>(P, i, last, nullptr, 0);
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// One inner step in one launch, for plans whose row blocks all fit on the GPU at once (one wave): the fused SpMV +
+// dots + sketch partials, then a grid-wide arrival (every CTA, also one with no step to take), then, once all of the
+// launch's partials are written, the truncated-Arnoldi update of the CTA's own rows.  Every CTA of the launch is
+// resident at the same time (the host launches it only when the occupancy allows all blocks at once, beside the
+// sketched-QR cluster), so the wait ends; it gives up after a bounded number of polls and raises the plan's sync
+// flag, which the outer step turns into an error.  The arithmetic and its order are those of the two kernels.
+template <int V, int U, int NW, typename MT, typename VT, typename AT>
+__global__ void __maxnreg__(56) k_inner_step(const Plan P, int i, const MT* __restrict__ val, int last) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AT* wblk = reinterpret_cast<AT*>(smem_raw);
+    __shared__ unsigned long long target_sh;
+    const bool active = inner_spmv_block<V, U, NW, MT, VT, AT>(P, i, val, wblk);
+    __threadfence();  // this thread's partials are visible device-wide before the CTA arrives
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long old = atomicAdd(P.gsync, 1ull);
+        target_sh = (old / gridDim.x + 1) * (unsigned long long)gridDim.x;
+    }
+    if (!active) return;
+    // FP64: the shared block now holds the fixed-point image of w', so w' is read back from W
+    inner_axpy_block<NW, VT, AT, true>(P, i, last, sizeof(AT) == 8 ? nullptr : wblk, target_sh);
 }
 
 // ---------------------------------------------------------------------------------------------------------------
@@ -892,6 +953,10 @@ __global__ void k_cycle_reset(const Plan P, int j, int c3_on, double cond_thr) {
     cyc->dmin = INFINITY;
     cyc->rho = INFINITY;
     cyc->cond_thr = cond_thr;
+    if (p == 0 && P.gsync) {  // the fused step's grid counter and its give-up flag
+        P.gsync[0] = 0;
+        P.gsync[1] = 0;
+    }
     if (j >= 0) {
         const OuterState* ost = P.ost + p;
         const double sc = (j == 0) ? ost->beta : ost->ffom;
@@ -981,6 +1046,59 @@ void launch_inner_spmv(const Plan& p, int i) {
     else if (p.prec == kFP32) inner_spmv_t<float, float, float>(p, i, p.val32);
     else inner_spmv_t<float, __nv_bfloat16, float>(p, i, p.val32);
     ++g_launches;
+}
+
+// ---- fused step ----
+template <int V, int U, int NW, typename MT, typename VT, typename AT>
+static bool inner_step_v(const Plan& p, int i, const MT* val, bool last) {
+    const void* fn = (const void*)k_inner_step<V, U, NW, MT, VT, AT>;
+    const size_t sm = (size_t)(p.Bn + 1) * sizeof(AT);
+    set_smem(fn, sm);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 512, sm) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if ((int64_t)per_sm * p.sms < p.nblk) return false;  // not one wave: the two kernels
+    k_inner_step<V, U, NW, MT, VT, AT><<<p.nblk, 512, sm, p.st>>>(p, i, val, last ? 1 : 0);
+    return true;
+}
+
+template <int NW, typename MT, typename VT, typename AT>
+static bool inner_step_nw(const Plan& p, int i, const MT* val, bool last) {
+    if (p.vec == 0) return inner_step_v<0, 1, NW, MT, VT, AT>(p, i, val, last);
+    if (p.vec == 1) {
+        if constexpr (sizeof(MT) == 8) {  // FP64 one thread per row reads the SELL-32 copy
+            return p.sl_off ? inner_step_v<kVecSell, 1, NW, MT, VT, AT>(p, i, p.sl_val, last) : false;
+        } else {
+            return inner_step_v<1, 1, NW, MT, VT, AT>(p, i, val, last);
+        }
+    }
+    if (p.vec <= 8) return inner_step_v<8, 4, NW, MT, VT, AT>(p, i, val, last);
+    return inner_step_v<32, 2, NW, MT, VT, AT>(p, i, val, last);
+}
+
+template <typename MT, typename VT, typename AT>
+static bool inner_step_t(const Plan& p, int i, const MT* val, bool last) {
+    const int nwin = (p.t > 0) ? std::min(p.t, i + 1) : 0;
+    switch (nwin) {
+        case 0: return inner_step_nw<0, MT, VT, AT>(p, i, val, last);
+        case 1: return inner_step_nw<1, MT, VT, AT>(p, i, val, last);
+        case 2: return inner_step_nw<2, MT, VT, AT>(p, i, val, last);
+        case 3: return inner_step_nw<3, MT, VT, AT>(p, i, val, last);
+        case 4: return inner_step_nw<4, MT, VT, AT>(p, i, val, last);
+        default: return false;  // wider windows: the two kernels
+    }
+}
+
+bool launch_inner_step(const Plan& p, int i, bool last) {
+    if (p.G > 1 || !p.gsync) return false;
+    bool ok;
+    if (p.prec == kFP64) ok = inner_step_t<double, double, double>(p, i, p.val, last);
+    else if (p.prec == kFP32) ok = inner_step_t<float, float, float>(p, i, p.val32, last);
+    else ok = inner_step_t<float, __nv_bfloat16, float>(p, i, p.val32, last);
+    if (ok) ++g_launches;
+    return ok;
 }
 
 template <int NW, typename VT, typename AT>

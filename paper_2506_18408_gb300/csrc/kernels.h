@@ -56,6 +56,8 @@ struct Plan {
     // groups of row blocks that are the same matrix rows of G right-hand sides of one system (the grouped inner
     // SpMV reads A and the gather lists once per group): members grp_b[g] + j * grp_st[g], j < grp_n[g]
     int G = 1, ngrp = 0;
+    int sms = 0;                   // SMs of the device (one-wave test of the fused step)
+    unsigned long long* gsync = nullptr;  // fused step: [0] grid arrival counter (reset per cycle), [1] wait gave up
     const int* grp_b = nullptr;
     const int* grp_n = nullptr;
     const int* grp_st = nullptr;
@@ -160,6 +162,9 @@ void launch_sketch_reduce(const Plan& p, const void* part, double* out, double* 
 void launch_cycle_start(const Plan& p, int j, const double* v, const double* vscale, int vstride, int c3_on,
                         double cond_thr);
 void launch_inner_spmv(const Plan& p, int i);
+// The fused inner step (inner SpMV kernel and Arnoldi update in one launch with a grid-wide arrival in between) when
+// the plan's row blocks fit on the GPU at once and the window is at most 4; false (nothing launched) otherwise.
+bool launch_inner_step(const Plan& p, int i, bool last);
 void launch_inner_axpy(const Plan& p, int i, bool last);
 cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st);  // cluster launch on stream st
 void launch_inner_finish(const Plan& p, double* z);  // y = R^{-1} d, z = sum_l y_l b_l (FP64)

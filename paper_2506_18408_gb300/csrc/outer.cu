@@ -77,6 +77,7 @@ __global__ void k_init_state(const Plan P, double tol) {
         ost->conv_est = 0;
         ost->breakdown = 0;
         ost->nan = (!isfinite(a1) || !isfinite(a2)) ? 1 : 0;
+        ost->sync_fail = 0;
         ost->beta = beta;
         ost->bnorm = bn;
         ost->est = beta;
@@ -208,6 +209,10 @@ __global__ void k_outer_givens(const Plan P, int j) {
     OuterState* ost = P.ost + p;
     const CycleState* cyc = P.cyc + p;
     const int64_t oh = (int64_t)p * J, og = (int64_t)p * ldo;
+    if (P.gsync && P.gsync[1]) {  // the inner cycle's grid-wide wait gave up: its results are not valid
+        ost->sync_fail = 1;
+        ost->nan = 1;
+    }
     P.k_hist[oh + j] = cyc->k;
     P.reason_hist[oh + j] = cyc->reason;
     if (cyc->k == 0) {  // inner cycle produced no correction

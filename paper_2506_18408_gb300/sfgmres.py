@@ -23,7 +23,7 @@ OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NAN = -1, -2, -3, -4
 CSR_HOST = 1
 OPT_PRECISION, OPT_ZETA, OPT_COND_THRESHOLD, OPT_C3, OPT_MAX_OUTER, OPT_SKETCH_KIND, OPT_PROFILE, \
-    OPT_SPMV_VECTOR, OPT_BLOCK_ROWS, OPT_GRAPH, OPT_RHS_GROUP, OPT_PERSISTENT = range(1, 13)
+    OPT_SPMV_VECTOR, OPT_BLOCK_ROWS, OPT_GRAPH, OPT_RHS_GROUP, OPT_PERSISTENT, OPT_FUSED_STEP = range(1, 14)
 SOLVE_TRANSPOSE = 1
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SKETCH_KIND = {"sparse_sign": 0, "identity": 1}
@@ -238,7 +238,8 @@ class Solver:
     _KEYS = {"precision": OPT_PRECISION, "zeta": OPT_ZETA, "cond_threshold": OPT_COND_THRESHOLD, "c3": OPT_C3,
              "max_outer": OPT_MAX_OUTER, "sketch_kind": OPT_SKETCH_KIND, "profile": OPT_PROFILE,
              "spmv_vector": OPT_SPMV_VECTOR, "block_rows": OPT_BLOCK_ROWS, "graph": OPT_GRAPH,
-             "rhs_group": OPT_RHS_GROUP, "persistent": OPT_PERSISTENT}
+             "rhs_group": OPT_RHS_GROUP, "persistent": OPT_PERSISTENT,
+             "fused_step": OPT_FUSED_STEP}
 
     def __init__(self, n, row_ptr, col, val, sketch_seed: int = 1, stream=None, **options):
         import torch

@@ -279,6 +279,7 @@ def test_profiled_solves_time_the_working_launches_with_and_without_graphs():
     mat = workloads.convdiff(64, (20.0, 10.0))
     rhs = workloads.rhs(mat.n, seed=0)
     sv = Solver(mat.n, mat.row_ptr, mat.col, mat.val, sketch_seed=1, max_outer=20)
+    sv.set("fused_step", 0)  # the two kernels of a step, timed separately
     bd = dev_vec(rhs)
     x_ref, info_ref = sv.solve(bd, m=30, s=120, k=2, tol=1e-8)
     assert info_ref["status"] == 0 and info_ref["n_inner_spmv"] == 0
@@ -294,3 +295,36 @@ def test_profiled_solves_time_the_working_launches_with_and_without_graphs():
         for key in ("inner_spmv", "inner_axpy", "qr"):
             assert info["n_" + key] == steps
             assert 0.0 < info["t_%s_ms" % key] < info["t_total_ms"]
+
+
+def test_fused_inner_step_matches_the_two_kernel_step():
+    """One launch per inner step (the inner SpMV kernel's work, a grid-wide arrival, then the Arnoldi update of the
+    CTA's own rows) runs the same arithmetic in the same order as the two kernels: FP64 and FP32-inner solves agree
+    bit for bit with and without graphs, and profiling shows the fused path was taken (no separate update launches)."""
+    from paper_2506_18408_gb300 import Solver
+
+    mat = workloads.convdiff(64, (20.0, 10.0))
+    rhs = workloads.rhs(mat.n, seed=0)
+    bd = dev_vec(rhs)
+    for prec in ("fp64", "fp32"):
+        sv = Solver(mat.n, mat.row_ptr, mat.col, mat.val, sketch_seed=1, max_outer=20, precision=prec)
+        assert int(sv.get("fused_step")) == 1
+        sv.set("fused_step", 0)
+        x_two, info_two = sv.solve(bd, m=30, s=120, k=2, tol=1e-8)
+        assert info_two["status"] == 0
+        sv.set("fused_step", 1)
+        for graph in (1, 1, 0):
+            sv.set("graph", graph)
+            x, info = sv.solve(bd, m=30, s=120, k=2, tol=1e-8)
+            assert info["status"] == 0
+            assert np.array_equal(x.cpu().numpy(), x_two.cpu().numpy())
+            assert info["inner_k"] == info_two["inner_k"]
+        sv.set("profile", 1)
+        _, ip = sv.solve(bd, m=30, s=120, k=2, tol=1e-8)
+        assert ip["n_inner_axpy"] == 0 and ip["n_inner_spmv"] == ip["total_inner"] > 0
+        sv.set("profile", 0)
+        sv.set("fused_step", 0)
+        sv.set("profile", 1)
+        _, ip2 = sv.solve(bd, m=30, s=120, k=2, tol=1e-8)
+        assert ip2["n_inner_axpy"] == ip2["total_inner"]
+        sv.close()
