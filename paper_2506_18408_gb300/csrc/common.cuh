@@ -32,6 +32,40 @@ __device__ __forceinline__ double ld_plain(const double* p) { return *p; }
 __device__ __forceinline__ float ld_plain(const float* p) { return *p; }
 __device__ __forceinline__ float ld_plain(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 
+// Loads and stores with L2 eviction priority "last" (policy from l2_keep_policy): for vectors that a later phase or
+// step reads again (the Arnoldi window rows, w', the next basis vector), so that the matrix stream, read once per
+// step, is evicted before them.
+__device__ __forceinline__ unsigned long long l2_keep_policy() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ double ld_keep(const double* p, unsigned long long pol) {
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_keep(const float* p, unsigned long long pol) {
+    float v;
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_keep(const __nv_bfloat16* p, unsigned long long pol) {
+    unsigned short v;
+    asm volatile("ld.global.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+    return __bfloat162float(__ushort_as_bfloat16(v));
+}
+__device__ __forceinline__ void st_keep(double* p, double v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(float* p, float v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(__nv_bfloat16* p, float v, unsigned long long pol) {
+    const unsigned short b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(b), "l"(pol) : "memory");
+}
+
 // Value as it will read back after store_as (identity except for BF16 rounding).
 __device__ __forceinline__ double stored_value(double v, const double*) { return v; }
 __device__ __forceinline__ float stored_value(float v, const float*) { return v; }

@@ -69,6 +69,7 @@ __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ sof
                                               AT* __restrict__ wblk, AT* __restrict__ W, AT (&acc)[NW > 0 ? NW : 1],
                                               AT& nrm) {
     const int lane = threadIdx.x & 31;
+    const unsigned long long pol = l2_keep_policy();  // window rows and w' are read again by the update
     const VT* x = Ub + (int64_t)i * N;
     const VT* xs = x + cs;  // gather base: vector index of matrix column c is c + cs
     int emax = 1;
@@ -86,7 +87,7 @@ __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ sof
         const int r = v0 + k;
         AT uw[NW > 0 ? NW : 1];
 #pragma unroll
-        for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
+        for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_keep(Ub + (int64_t)(lo + q) * N + r, pol) : AT(0);
         AT ui;  // u_i[r] (the last window vector when there is a window) for ||u_i||^2
         if constexpr (NW > 0) ui = uw[NW - 1];
         else ui = ok ? ld_plain(x + r) : AT(0);
@@ -116,7 +117,7 @@ __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ sof
             }
         }
         if (ok) {
-            W[r] = sum;
+            st_keep(W + r, sum, pol);
             wblk[k] = sum;
         }
 #pragma unroll
@@ -141,6 +142,7 @@ __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ r
                                                 int v0, int len, int cs, AT* __restrict__ wblk, AT* __restrict__ W,
                                                 AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
     const int lane = threadIdx.x & 31;
+    const unsigned long long pol = l2_keep_policy();  // window rows and w' are read again by the update
     const VT* x = Ub + (int64_t)i * N;
     const VT* xs = x + cs;                // gather base: vector index of matrix column c is c + cs
     const int* rpm = rp + (v0 - cs);      // row pointers of the block's matrix rows
@@ -157,7 +159,7 @@ __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ r
         const int r = v0 + k;
         AT uw[NW > 0 ? NW : 1];
 #pragma unroll
-        for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
+        for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_keep(Ub + (int64_t)(lo + q) * N + r, pol) : AT(0);
         AT ui;  // u_i[r] (the last window vector when there is a window) for ||u_i||^2
         if constexpr (NW > 0) ui = uw[NW - 1];
         else ui = ok ? ld_plain(x + r) : AT(0);
@@ -178,7 +180,7 @@ __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ r
             }
         }
         if (ok) {
-            W[r] = sum;
+            st_keep(W + r, sum, pol);
             wblk[k] = sum;
         }
 #pragma unroll
@@ -197,17 +199,18 @@ template <int NW, typename VT, typename AT>
 __device__ __forceinline__ int dots_pass(int N, int v0, int len, const VT* __restrict__ Ub, int lo, int i,
                                          const AT* __restrict__ wblk, AT* __restrict__ W,
                                          AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
+    const unsigned long long pol = l2_keep_policy();  // window rows and w' are read again by the update
     int emax = 1;
 #pragma unroll 2
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
         const int r = v0 + k;
         const AT w = wblk[k];
-        W[r] = w;
+        st_keep(W + r, w, pol);
         emax = max(emax, exp_of(w));
-        const AT ui = ld_plain(Ub + (int64_t)i * N + r);
+        const AT ui = ld_keep(Ub + (int64_t)i * N + r, pol);
         nrm += ui * ui;
 #pragma unroll
-        for (int q = 0; q < NW; ++q) acc[q] += ld_plain(Ub + (int64_t)(lo + q) * N + r) * w;
+        for (int q = 0; q < NW; ++q) acc[q] += ld_keep(Ub + (int64_t)(lo + q) * N + r, pol) * w;
     }
     return emax;
 }
@@ -647,12 +650,13 @@ __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last,
 #pragma unroll
     for (int q = 0; q < NW; ++q) cf[q] = coef_sh[q];
     VT* un = Ub + (int64_t)(i + 1) * N;
+    const unsigned long long pol = l2_keep_policy();
     auto update = [&](int r, AT u, const AT (&uq)[NW > 0 ? NW : 1]) {
 #pragma unroll
         for (int q = 0; q < NW; ++q) u -= cf[q] * uq[q];
         if constexpr (sizeof(AT) == 8) u = mul_pow2((double)u, p2);
         else u = u * sc2;
-        store_as(un + r, u);
+        st_keep(un + r, u, pol);  // the next step gathers it and reads it as a window row
     };
 #pragma unroll
     for (int u = 0; u < PF; ++u) {
@@ -990,13 +994,12 @@ template <int NW, typename MT, typename VT, typename AT>
 static void inner_spmv_nw(const Plan& p, int i, const MT* val) {
     if (p.vec == 0) inner_spmv_v<0, 1, NW, MT, VT, AT>(p, i, val);
     else if (p.vec == 1) {
-        if constexpr (sizeof(MT) == 8) {
-            if (p.sl_off) {  // FP64 with the SELL-32 copy
-                inner_spmv_v<kVecSell, 1, NW, MT, VT, AT>(p, i, p.sl_val);
-                return;
-            }
+        if constexpr (sizeof(MT) == 8) {  // FP64 one thread per row reads the SELL-32 copy (always built for it)
+            if (p.sl_off) inner_spmv_v<kVecSell, 1, NW, MT, VT, AT>(p, i, p.sl_val);
+            else inner_spmv_v<8, 4, NW, MT, VT, AT>(p, i, val);
+        } else {
+            inner_spmv_v<1, 1, NW, MT, VT, AT>(p, i, val);
         }
-        inner_spmv_v<1, 1, NW, MT, VT, AT>(p, i, val);
     }
     else if (p.vec <= 8) inner_spmv_v<8, 4, NW, MT, VT, AT>(p, i, val);
     else inner_spmv_v<32, 2, NW, MT, VT, AT>(p, i, val);
