@@ -553,7 +553,11 @@ __device__ __forceinline__ AT block_partials_sum(const AT* __restrict__ x, int64
 template <int NW, typename VT, typename AT, bool FUSED>
 __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last, const AT* __restrict__ wsm,
                                                  unsigned long long target) {
-    constexpr int PF = (sizeof(AT) == 8 && NW >= 5) ? 1 : 2;
+    // rows per thread loaded before the scalars (PF) and per round of the row loop (UR; all loads of a round are
+    // issued before its stores): the fused step has the whole 56-register budget here, the update kernel 42
+    constexpr bool WIDE = (sizeof(AT) == 8 && NW >= 3);
+    constexpr int PF = FUSED ? (WIDE ? 2 : 4) : ((sizeof(AT) == 8 && NW >= 5) ? 1 : 2);
+    constexpr int UR = FUSED ? (WIDE ? 2 : 4) : ((sizeof(AT) == 8 && NW >= 4) ? 1 : 2);
     __shared__ AT coef_sh[kMaxTrunc];
     __shared__ AT part_sh[kMaxTrunc + 1];
     __shared__ double sig_sh;
@@ -663,13 +667,22 @@ __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last,
         const int k = threadIdx.x + u * (int)blockDim.x;
         if (k < bi.len) update(bi.v0 + k, wv[u], uv[u]);
     }
-#pragma unroll 2
-    for (int k = threadIdx.x + PF * (int)blockDim.x; k < bi.len; k += blockDim.x) {
-        const int r = bi.v0 + k;
-        AT uq[NW > 0 ? NW : 1];
+    for (int k0 = threadIdx.x + PF * (int)blockDim.x; k0 < bi.len; k0 += UR * (int)blockDim.x) {
+        AT wr[UR], uq[UR][NW > 0 ? NW : 1];
 #pragma unroll
-        for (int q = 0; q < NW; ++q) uq[q] = ld_plain(Ub + (int64_t)(lo + q) * N + r);
-        update(r, wsm ? wsm[k] : W[r], uq);
+        for (int u = 0; u < UR; ++u) {
+            const int k = k0 + u * (int)blockDim.x;
+            const bool ok = k < bi.len;
+            const int r = bi.v0 + k;
+            wr[u] = ok ? (wsm ? wsm[k] : W[r]) : AT(0);
+#pragma unroll
+            for (int q = 0; q < NW; ++q) uq[u][q] = ok ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < UR; ++u) {
+            const int k = k0 + u * (int)blockDim.x;
+            if (k < bi.len) update(bi.v0 + k, wr[u], uq[u]);
+        }
     }
 }
 
