@@ -93,13 +93,19 @@ extern "C" {
                                         cross-block sums differs.  SFGMRES_OPT_PROFILE = 1 uses the per-step
                                         kernels. */
 #define SFGMRES_OPT_FUSED_STEP 13    /* 1 (default): where all row blocks of a plan fit on the GPU at once (one system
-                                        of up to about 2 x SMs blocks) and the truncation window is at most 4, each
+                                        of up to about 2 x SMs blocks), the truncation window is at most 4 and the
+                                        SpMV is not the FP64 length-binned one (measured slower fused), each
                                         inner step runs as one launch: the inner SpMV kernel's work, a grid-wide
                                         arrival of every CTA, then the Arnoldi update of the CTA's own rows (the same
                                         arithmetic in the same order, so results are identical).  The wait is bounded;
                                         if it gives up the solve returns SFGMRES_ERR_CUDA.  With profiling on, the
                                         fused launch is reported as the inner SpMV kernel (t_inner_spmv_ms) and the
                                         update's fields stay 0.  0: two launches per step. */
+#define SFGMRES_OPT_STEP_WAIT_EXTRA 14 /* test of the fused step's give-up path: the grid-wide wait also waits for this
+                                        many arrivals that never come (default 0).  With a positive value the first
+                                        wait of a cycle gives up after its bounded polls (about a second), the later
+                                        ones return at once, and the solve returns SFGMRES_ERR_CUDA; the handle stays
+                                        usable. */
 /* ---- sfgmres_solve_batch flags ---------------------------------------------------------------------------- */
 #define SFGMRES_SOLVE_TRANSPOSE 1    /* solve A_q^T x = b for every problem (see sfgmres_solve_transpose) */
 

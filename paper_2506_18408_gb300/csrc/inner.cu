@@ -507,9 +507,12 @@ __global__ void __maxnreg__(sizeof(AT) == 8 ? 64 : 56) k_inner_spmv_grp(const Pl
 
 // ---------------------------------------------------------------------------------------------------------------
 // Waits until the grid counter reaches target (acquire), polling with a growing sleep; after kGridWaitPolls polls it
-// gives up and sets *fail.
-constexpr int kGridWaitPolls = 1 << 22;  // >= 1 s at the 256 ns cap
+// gives up and sets *fail.  Once a wait of the cycle has given up, later ones return at once.
+constexpr int kGridWaitPolls = 1 << 20;  // about a second of polls (256 ns sleeps plus an L2 round trip each)
 __device__ __forceinline__ void grid_wait(unsigned long long* ctr, unsigned long long target, unsigned long long* fail) {
+    unsigned long long f;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(f) : "l"(fail) : "memory");
+    if (f) return;
     unsigned ns = 32;
     for (int it = 0; it < kGridWaitPolls; ++it) {
         unsigned long long v;
@@ -708,7 +711,7 @@ __global__ void __maxnreg__(56) k_inner_step(const Plan P, int i, const MT* __re
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned long long old = atomicAdd(P.gsync, 1ull);
-        target_sh = (old / gridDim.x + 1) * (unsigned long long)gridDim.x;
+        target_sh = (old / gridDim.x + 1) * (unsigned long long)gridDim.x + (unsigned long long)P.gwait_extra;
     }
     if (!active) return;
     // FP64: the shared block now holds the fixed-point image of w', so w' is read back from W
@@ -1082,7 +1085,10 @@ static bool inner_step_v(const Plan& p, int i, const MT* val, bool last) {
 
 template <int NW, typename MT, typename VT, typename AT>
 static bool inner_step_nw(const Plan& p, int i, const MT* val, bool last) {
-    if (p.vec == 0) return inner_step_v<0, 1, NW, MT, VT, AT>(p, i, val, last);
+    if (p.vec == 0) {  // length-binned SpMV: fused in FP32 only (FP64 measured slower fused: 399 vs 380 ms, Zipf 2M)
+        if constexpr (sizeof(MT) == 8) return false;
+        else return inner_step_v<0, 1, NW, MT, VT, AT>(p, i, val, last);
+    }
     if (p.vec == 1) {
         if constexpr (sizeof(MT) == 8) {  // FP64 one thread per row reads the SELL-32 copy
             return p.sl_off ? inner_step_v<kVecSell, 1, NW, MT, VT, AT>(p, i, p.sl_val, last) : false;

@@ -58,6 +58,7 @@ struct Plan {
     int G = 1, ngrp = 0;
     int sms = 0;                   // SMs of the device (one-wave test of the fused step)
     unsigned long long* gsync = nullptr;  // fused step: [0] grid arrival counter (reset per cycle), [1] wait gave up
+    int gwait_extra = 0;           // fused step: arrivals waited for beyond the launch's blocks (0; > 0 tests give-up)
     const int* grp_b = nullptr;
     const int* grp_n = nullptr;
     const int* grp_st = nullptr;

@@ -328,3 +328,26 @@ def test_fused_inner_step_matches_the_two_kernel_step():
         _, ip2 = sv.solve(bd, m=30, s=120, k=2, tol=1e-8)
         assert ip2["n_inner_axpy"] == ip2["total_inner"]
         sv.close()
+
+
+def test_fused_step_wait_that_gives_up_is_reported_and_the_handle_stays_usable():
+    """The fused step's grid-wide wait is bounded: made to wait for one arrival that never comes, the first wait of
+    the cycle gives up after its polls (about a second), the later ones return at once, and the solve reports
+    SFGMRES_ERR_CUDA instead of hanging; with the hook off again the same handle solves normally, bit for bit as
+    before."""
+    from paper_2506_18408_gb300 import Solver
+    from paper_2506_18408_gb300.sfgmres import SFGMRESError
+
+    mat = workloads.convdiff(64, (20.0, 10.0))
+    bd = dev_vec(workloads.rhs(mat.n, seed=0))
+    sv = Solver(mat.n, mat.row_ptr, mat.col, mat.val, sketch_seed=1, max_outer=20)
+    x_ref, info_ref = sv.solve(bd, m=30, s=120, k=2, tol=1e-8)
+    assert info_ref["status"] == 0
+    sv.set("step_wait_extra", 1)
+    with pytest.raises(SFGMRESError) as ei:
+        sv.solve(bd, m=30, s=120, k=2, tol=1e-8)
+    assert ei.value.code == -2 and "gave up" in str(ei.value)
+    sv.set("step_wait_extra", 0)
+    x, info = sv.solve(bd, m=30, s=120, k=2, tol=1e-8)
+    assert info["status"] == 0 and np.array_equal(x.cpu().numpy(), x_ref.cpu().numpy())
+    sv.close()
