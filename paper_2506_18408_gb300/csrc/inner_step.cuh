@@ -1,0 +1,837 @@
+// Kernels of one inner step of a sketched-GMRES cycle (Section 3, Section 4.1) -- the fused inner SpMV (w' = A u_i,
+// truncated-Arnoldi window dots, ||u_i||^2, per-block sketch partials), the truncated-Arnoldi update and the fused
+// step that runs both in one launch -- as templates over the SpMV shape, the window size and the precision, with
+// their launch dispatch.  inner_f64.cu, inner_f32.cu and inner_bf16.cu instantiate them per precision (so they compile
+// in parallel); inner.cu holds the rest of the cycle.
+#pragma once
+
+#include "kernels.h"
+#include "spmv.cuh"
+
+#include <climits>
+#include <algorithm>
+
+namespace sfg {
+
+// Template value of k_inner_spmv's lanes-per-row parameter for one thread per row reading the SELL-32 copy of A
+// (the FP64 inner cycle); 1 is one thread per row reading the CSR arrays.
+constexpr int kVecSell = -1;
+
+__device__ __forceinline__ bool cycle_idle(const Plan& P, int p, int i) {
+    const CycleState* c = P.cyc + p;
+    return c->stopped || c->brk_step <= i || (P.pflag[p] & 1);
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// ---------------------------------------------------------------------------------------------------------------
+// Entries pk .. pk+CNT-1 of the thread's row in the SELL-32 copy (cp, vp: the lane's first entry; consecutive
+// entries 32 apart, so each load is coalesced across the warp); entries past the row's end (rl) are not gathered.
+template <int CNT, typename MT, typename XT, typename AT>
+__device__ __forceinline__ void sell_chunk(const int* __restrict__ cp, const MT* __restrict__ vp,
+                                           const XT* __restrict__ x, int rl, int pk, AT& sum) {
+    int c[CNT];
+    AT v[CNT];
+#pragma unroll
+    for (int q = 0; q < CNT; ++q) {
+        c[q] = __ldg(cp + (pk + q) * 32);
+        v[q] = (AT)__ldg(vp + (pk + q) * 32);
+    }
+#pragma unroll
+    for (int q = 0; q < CNT; ++q)
+        if (pk + q < rl) sum += v[q] * load_as(x + c[q], AT());
+}
+
+// Phase 1, one thread per row, from the SELL-32 copy of A: w' = A u_i over the block (vector rows v0 .. v0+len,
+// whose matrix rows start the list block's first slice sb; warp rows kw .. kw+31 are slice sb + kw/32), fused with
+// storing w' (global W and the shared block copy), the window dot products acc_q += u_{lo+q}[r] * w'[r] and
+// ||u_i||^2.  Each row is summed in entry order, the warp issuing as many FMAs as its slice is wide.  The window
+// values and the next slice's extent are loaded before the row's SpMV, so they are in flight together.  Returns
+// the thread's largest exponent of w'.
+template <int NW, typename MT, typename VT, typename AT>
+__device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ soff, const uint8_t* __restrict__ slen,
+                                              const int* __restrict__ scol, const MT* __restrict__ sval, int sb,
+                                              const VT* __restrict__ Ub, int i, int lo, int v0, int len, int cs,
+                                              AT* __restrict__ wblk, AT* __restrict__ W, AT (&acc)[NW > 0 ? NW : 1],
+                                              AT& nrm) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long pol = l2_keep_policy();  // window rows and w' are read again by the update
+    const VT* x = Ub + (int64_t)i * N;
+    const VT* xs = x + cs;  // gather base: vector index of matrix column c is c + cs
+    int emax = 1;
+    int kw = threadIdx.x & ~31;
+    int o0 = 0, o1 = 0, rl = 0;
+    if (kw < len) {
+        const int sid = sb + (kw >> 5);
+        o0 = __ldg(soff + sid);
+        o1 = __ldg(soff + sid + 1);
+        rl = __ldg(slen + (int64_t)sid * 32 + lane);
+    }
+    for (; kw < len; kw += blockDim.x) {  // warp-uniform loop over the block's slices
+        const int k = kw + lane;
+        const bool ok = k < len;
+        const int r = v0 + k;
+        AT uw[NW > 0 ? NW : 1];
+#pragma unroll
+        for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_keep(Ub + (int64_t)(lo + q) * N + r, pol) : AT(0);
+        AT ui;  // u_i[r] (the last window vector when there is a window) for ||u_i||^2
+        if constexpr (NW > 0) ui = uw[NW - 1];
+        else ui = ok ? ld_plain(x + r) : AT(0);
+        const int kn = kw + (int)blockDim.x;
+        int o0n = 0, o1n = 0, rln = 0;
+        if (kn < len) {
+            const int sid = sb + (kn >> 5);
+            o0n = __ldg(soff + sid);
+            o1n = __ldg(soff + sid + 1);
+            rln = __ldg(slen + (int64_t)sid * 32 + lane);
+        }
+        const int w = o1 - o0;
+        // every 128-byte line of the slice's columns and values requested at once (one line per lane; w <= 16
+        // entries, so at most 32 lines of FP64 values): the later chunks' loads then find their lines in flight
+        // instead of starting another round trip to memory each
+        if (lane < w) prefetch_l1(scol + (int64_t)(o0 + lane) * 32);
+        if (lane < w * (int)(sizeof(MT) / 4)) prefetch_l1(reinterpret_cast<const char*>(sval + (int64_t)o0 * 32) + lane * 128);
+        const int* cp = scol + (int64_t)o0 * 32 + lane;
+        const MT* vp = sval + (int64_t)o0 * 32 + lane;
+        AT sum = AT(0);
+        for (int pk = 0; pk < w; pk += 4) {
+            switch (min(w - pk, 4)) {
+                case 1: sell_chunk<1>(cp, vp, xs, rl, pk, sum); break;
+                case 2: sell_chunk<2>(cp, vp, xs, rl, pk, sum); break;
+                case 3: sell_chunk<3>(cp, vp, xs, rl, pk, sum); break;
+                default: sell_chunk<4>(cp, vp, xs, rl, pk, sum); break;
+            }
+        }
+        if (ok) {
+            st_keep(W + r, sum, pol);
+            wblk[k] = sum;
+        }
+#pragma unroll
+        for (int q = 0; q < NW; ++q) acc[q] += uw[q] * sum;
+        nrm += ui * ui;
+        emax = max(emax, exp_of(sum));
+        o0 = o0n;
+        o1 = o1n;
+        rl = rln;
+    }
+    return emax;
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// Phase 1, one thread per row: w' = A u_i over the block (vector rows v0 .. v0+len = matrix rows v0-cs ..) fused
+// with storing w' (global W and the shared block copy), the window dot products acc_q += u_{lo+q}[r] * w'[r] and
+// ||u_i||^2.  The window values and the next row group's extents are loaded before the row's SpMV, so they are in
+// flight together.  Returns the thread's largest exponent of w'.
+template <int NW, typename MT, typename VT, typename AT>
+__device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ rp, const int* __restrict__ col,
+                                                const MT* __restrict__ val, const VT* __restrict__ Ub, int i, int lo,
+                                                int v0, int len, int cs, AT* __restrict__ wblk, AT* __restrict__ W,
+                                                AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long pol = l2_keep_policy();  // window rows and w' are read again by the update
+    const VT* x = Ub + (int64_t)i * N;
+    const VT* xs = x + cs;                // gather base: vector index of matrix column c is c + cs
+    const int* rpm = rp + (v0 - cs);      // row pointers of the block's matrix rows
+    int emax = 1;
+    int kw = threadIdx.x & ~31;
+    int a = 0, rl = 0;
+    if (kw + lane < len) {
+        a = __ldg(rpm + kw + lane);
+        rl = __ldg(rpm + kw + lane + 1) - a;
+    }
+    for (; kw < len; kw += blockDim.x) {  // warp-uniform loop over the block's rows
+        const int k = kw + lane;
+        const bool ok = k < len;
+        const int r = v0 + k;
+        AT uw[NW > 0 ? NW : 1];
+#pragma unroll
+        for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_keep(Ub + (int64_t)(lo + q) * N + r, pol) : AT(0);
+        AT ui;  // u_i[r] (the last window vector when there is a window) for ||u_i||^2
+        if constexpr (NW > 0) ui = uw[NW - 1];
+        else ui = ok ? ld_plain(x + r) : AT(0);
+        const int kn = k + (int)blockDim.x;
+        int an = 0, rln = 0;
+        if (kn < len) {
+            an = __ldg(rpm + kn);
+            rln = __ldg(rpm + kn + 1) - an;
+        }
+        const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)rl);
+        AT sum = AT(0);
+        for (int pk = 0; pk < maxlen; pk += 4) {
+            switch (min(maxlen - pk, 4)) {
+                case 1: row_chunk<1>(col, val, xs, a, rl, pk, sum); break;
+                case 2: row_chunk<2>(col, val, xs, a, rl, pk, sum); break;
+                case 3: row_chunk<3>(col, val, xs, a, rl, pk, sum); break;
+                default: row_chunk<4>(col, val, xs, a, rl, pk, sum); break;
+            }
+        }
+        if (ok) {
+            st_keep(W + r, sum, pol);
+            wblk[k] = sum;
+        }
+#pragma unroll
+        for (int q = 0; q < NW; ++q) acc[q] += uw[q] * sum;
+        nrm += ui * ui;
+        emax = max(emax, exp_of(sum));
+        a = an;
+        rl = rln;
+    }
+    return emax;
+}
+
+// Phase 1 tail for the sub-warp path (w' already in shared memory): store w', accumulate the window dots and
+// ||u_i||^2.
+template <int NW, typename VT, typename AT>
+__device__ __forceinline__ int dots_pass(int N, int v0, int len, const VT* __restrict__ Ub, int lo, int i,
+                                         const AT* __restrict__ wblk, AT* __restrict__ W,
+                                         AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
+    const unsigned long long pol = l2_keep_policy();  // window rows and w' are read again by the update
+    int emax = 1;
+#pragma unroll 2
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+        const int r = v0 + k;
+        const AT w = wblk[k];
+        st_keep(W + r, w, pol);
+        emax = max(emax, exp_of(w));
+        const AT ui = ld_keep(Ub + (int64_t)i * N + r, pol);
+        nrm += ui * ui;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) acc[q] += ld_keep(Ub + (int64_t)(lo + q) * N + r, pol) * w;
+    }
+    return emax;
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// Shared memory: the block of w' (Bn + 1 slots of AT, slot Bn = 0 for the list padding).  FP64: the block is
+// converted in place to its 64-bit fixed-point image before the sketch sums.
+// At most 56 registers per thread (registers are allocated in units of 8 per thread): two 512-thread CTAs per SM
+// then leave room for the sketched-QR cluster's CTAs to run beside them instead of displacing them.
+// Returns false (every thread of the CTA alike) when the block's problem has no step i to take.
+template <int V, int U, int NW, typename MT, typename VT, typename AT>
+__device__ __forceinline__ bool inner_spmv_block(const Plan& P, int i, const MT* __restrict__ val,
+                                                 AT* __restrict__ wblk) {
+    __shared__ AT red[512];
+    __shared__ int stop_sh, emax_sh[16];
+    const int b = blockIdx.x;
+    const BlockInfo bi = block_info(P, b);
+    if (threadIdx.x == 0) stop_sh = cycle_idle(P, bi.prob, i) ? 1 : 0;
+    __syncthreads();
+    if (stop_sh) return false;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int s = P.s, Bn = P.Bn, N = P.N;
+    const VT* Ub = (const VT*)P.U;
+    AT* W = (AT*)P.W;
+    const int lo = i - NW + 1;  // window u_lo..u_i (NW = min(t, i+1))
+    AT acc[NW > 0 ? NW : 1];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) acc[q] = AT(0);
+    int emax;
+    AT nrm = AT(0);  // ||u_i||^2 over the block (the vector this step multiplies)
+    if constexpr (V == kVecSell) {
+        emax = spmv_dots_sell<NW>(N, P.sl_off, P.sl_len, P.sl_col, val, P.sl_base[bi.list], Ub, i, lo, bi.v0,
+                                  bi.len, bi.cs, wblk, W, acc, nrm);
+    } else if constexpr (V == 1) {
+        emax = spmv_dots_scalar<NW>(N, P.rp, P.col, val, Ub, i, lo, bi.v0, bi.len, bi.cs, wblk, W, acc, nrm);
+    } else {
+        const int m0 = bi.v0 - bi.cs;
+        int n0, n01;
+        block_bins(P, bi, n0, n01);
+        spmv_rows_to_smem<V, U, MT, VT, AT>(P.rp, P.col, val, Ub + (int64_t)i * N + bi.cs, m0, m0 + bi.len, wblk,
+                                            P.perm, n0, n01);
+        __syncthreads();
+        emax = dots_pass<NW>(N, bi.v0, bi.len, Ub, lo, i, wblk, W, acc, nrm);
+    }
+    if (threadIdx.x == 0) wblk[Bn] = AT(0);
+    // block sums of ||u_i||^2 and the window dots in one round: each warp's sums (shuffle trees), then the warps'
+    // partials in warp order; the block's largest exponent of w' with them
+    {
+        AT (*red2)[16] = reinterpret_cast<AT (*)[16]>(red);  // [NW + 1][16]
+        const AT v = warp_sum(nrm);
+        if (lane == 0) red2[0][warp] = v;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            const AT d = warp_sum(acc[q]);
+            if (lane == 0) red2[1 + q][warp] = d;
+        }
+        emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
+        if (lane == 0) emax_sh[warp] = emax;
+        __syncthreads();
+        if (threadIdx.x <= NW) {
+            AT t = AT(0);
+            for (int w = 0; w < nw; ++w) t += red2[threadIdx.x][w];
+            if (threadIdx.x == 0) ((AT*)P.normpart)[b] = t;
+            else ((AT*)P.hpart)[(int64_t)b * kMaxTrunc + threadIdx.x - 1] = t;
+        }
+    }
+    const int* sg = P.seg + (int64_t)bi.list * s;
+    AT* cpart = (AT*)P.cpart;
+    if constexpr (sizeof(AT) == 8) {
+        // exact fixed-point sketch sums (integer adds; the FP64 pipe stays with the SpMV)
+        int Eb = 1;
+        for (int q = 0; q < nw; ++q) Eb = max(Eb, emax_sh[q]);
+        const int H = P.sk_headroom;
+        long long* qblk = reinterpret_cast<long long*>(wblk);
+        for (int r = threadIdx.x; r <= Bn; r += blockDim.x)
+            qblk[r] = (r < bi.len) ? to_fixed((double)wblk[r], Eb, H) : 0;
+        __syncthreads();
+        const double unit = fixed_unit(0.0, Eb, H);
+        const bool bad = exp_nonfinite(0.0, Eb);
+        for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
+            const long long v = sum_list(P.ent, sg[rr], sg[rr + 1], qblk);
+            cpart[(int64_t)b * s + rr] = bad ? (AT)NAN : (AT)((double)v * unit);
+        }
+    } else {
+        __syncthreads();
+        for (int rr = threadIdx.x; rr < s; rr += blockDim.x)
+            cpart[(int64_t)b * s + rr] = sum_list(P.ent, sg[rr], sg[rr + 1], wblk);
+    }
+    return true;
+}
+
+template <int V, int U, int NW, typename MT, typename VT, typename AT>
+__global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __restrict__ val) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    inner_spmv_block<V, U, NW, MT, VT, AT>(P, i, val, reinterpret_cast<AT*>(smem_raw));
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// Grouped form of k_inner_spmv for matrices with short rows (one thread per row): one CTA serves the same row block
+// of up to G problems that are right-hand sides of one system (the group's member blocks), so the CSR entries, the
+// row pointers and the sketch gather lists are read once for all members.  Each member gets what k_inner_spmv
+// computes for its block: w' stored, window dots and ||u_i||^2 partials (block sums formed warp by warp), and the
+// per-block sketch partials.  Members whose cycle has stopped are skipped.
+template <int CNT, int G, typename MT, typename XT, typename AT>
+__device__ __forceinline__ void row_chunk_g(const int* __restrict__ col, const MT* __restrict__ val,
+                                            const XT* __restrict__ x, int dn, unsigned act, int a, int len, int pk,
+                                            AT (&sum)[G]) {
+    int c[CNT];
+    AT v[CNT];
+#pragma unroll
+    for (int q = 0; q < CNT; ++q) {
+        if (pk + q < len) {
+            c[q] = __ldg(col + a + pk + q);
+            v[q] = (AT)__ldg(val + a + pk + q);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        if (act & (1u << j)) {
+#pragma unroll
+            for (int q = 0; q < CNT; ++q)
+                if (pk + q < len) sum[j] += v[q] * load_as(x + j * dn + c[q], AT());
+        }
+    }
+}
+
+template <int G, int NW, typename MT, typename VT, typename AT>
+__global__ void __maxnreg__(sizeof(AT) == 8 ? 64 : 56) k_inner_spmv_grp(const Plan P, int i, const MT* __restrict__ val) {
+    constexpr int NV = NW + 1;  // reduced values per member: ||u_i||^2 and the window dots
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ AT red[G * NV][16];
+    __shared__ int emax_sh[G][16];
+    __shared__ int mb_sh[G], mv0_sh[G], mcs_sh[G];
+    __shared__ unsigned act_sh;
+    const int gi = blockIdx.x;
+    const int gb = P.grp_b[gi], gn = P.grp_n[gi], gst = P.grp_st[gi];
+    if (threadIdx.x < G) {
+        const int j = threadIdx.x;
+        const int b = gb + min(j, gn - 1) * gst;
+        mb_sh[j] = b;
+        mv0_sh[j] = P.blk_v0[b];
+        mcs_sh[j] = P.blk_cs[b];
+    }
+    if (threadIdx.x == 0) {
+        unsigned a = 0;
+        for (int j = 0; j < gn; ++j)
+            if (!cycle_idle(P, P.blk_prob[gb + j * gst], i)) a |= 1u << j;
+        act_sh = a;
+    }
+    __syncthreads();
+    const unsigned act = act_sh;
+    if (!act) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int s = P.s, Bn = P.Bn, N = P.N, SB = Bn + 1;
+    const int len = P.blk_len[gb], list = P.blk_list[gb];
+    const int m0 = mv0_sh[0] - mcs_sh[0];
+    const VT* Ub = (const VT*)P.U;
+    AT* W = (AT*)P.W;
+    AT* wb = reinterpret_cast<AT*>(smem_raw);  // member j: wb[j * SB .. j * SB + Bn]
+    const int lo = i - NW + 1;
+    // members are consecutive right-hand sides of one system: their vector rows are dn apart
+    const int dn = (gn > 1) ? mv0_sh[1] - mv0_sh[0] : 0;
+    const int v00 = mv0_sh[0];
+    const VT* xs = Ub + (int64_t)i * N + mcs_sh[0];
+    AT acc[G][NW > 0 ? NW : 1], nrm[G];
+    int emax[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        nrm[j] = AT(0);
+        emax[j] = 1;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) acc[j][q] = AT(0);
+    }
+    const int* rpm = P.rp + m0;
+    int kw = threadIdx.x & ~31;
+    int a = 0, rl = 0;
+    if (kw + lane < len) {
+        a = __ldg(rpm + kw + lane);
+        rl = __ldg(rpm + kw + lane + 1) - a;
+    }
+    for (; kw < len; kw += blockDim.x) {  // warp-uniform loop over the block's rows
+        const int k = kw + lane;
+        const bool ok = k < len;
+        const int kn = k + (int)blockDim.x;
+        int an = 0, rln = 0;
+        if (kn < len) {
+            an = __ldg(rpm + kn);
+            rln = __ldg(rpm + kn + 1) - an;
+        }
+        const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)rl);
+        AT sum[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) sum[j] = AT(0);
+        for (int pk = 0; pk < maxlen; pk += 4) {
+            switch (min(maxlen - pk, 4)) {
+                case 1: row_chunk_g<1, G>(P.col, val, xs, dn, act, a, rl, pk, sum); break;
+                case 2: row_chunk_g<2, G>(P.col, val, xs, dn, act, a, rl, pk, sum); break;
+                case 3: row_chunk_g<3, G>(P.col, val, xs, dn, act, a, rl, pk, sum); break;
+                default: row_chunk_g<4, G>(P.col, val, xs, dn, act, a, rl, pk, sum); break;
+            }
+        }
+        // window values after the SpMV (fewer live registers than prefetching them for every member)
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (act & (1u << j)) {
+                const int r = v00 + j * dn + k;
+                if (ok) {
+                    W[r] = sum[j];
+                    wb[j * SB + k] = sum[j];
+                }
+                AT ui = AT(0);
+#pragma unroll
+                for (int q = 0; q < NW; ++q) {
+                    const AT u = ok ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
+                    acc[j][q] += u * sum[j];
+                    ui = u;
+                }
+                if constexpr (NW == 0) ui = ok ? ld_plain(Ub + (int64_t)i * N + r) : AT(0);
+                nrm[j] += ui * ui;
+                emax[j] = max(emax[j], exp_of(sum[j]));
+            }
+        }
+        a = an;
+        rl = rln;
+    }
+    // block sums (warp by warp, then the warps' partials in order) of ||u_i||^2 and the window dots
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        if (act & (1u << j)) {
+            const AT v = warp_sum(nrm[j]);
+            if (lane == 0) red[j * NV][warp] = v;
+#pragma unroll
+            for (int q = 0; q < NW; ++q) {
+                const AT d = warp_sum(acc[j][q]);
+                if (lane == 0) red[j * NV + 1 + q][warp] = d;
+            }
+            if constexpr (sizeof(AT) == 8) {
+                const int e = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax[j]);
+                if (lane == 0) emax_sh[j][warp] = e;
+            }
+            if (threadIdx.x == 0) wb[j * SB + Bn] = AT(0);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < G * NV) {
+        const int j = threadIdx.x / NV, v = threadIdx.x % NV;
+        if (act & (1u << j)) {
+            AT t = AT(0);
+            for (int w = 0; w < nw; ++w) t += red[threadIdx.x][w];
+            const int b = mb_sh[j];
+            if (v == 0) ((AT*)P.normpart)[b] = t;
+            else ((AT*)P.hpart)[(int64_t)b * kMaxTrunc + v - 1] = t;
+        }
+    }
+    const int* sg = P.seg + (int64_t)list * s;
+    AT* cpart = (AT*)P.cpart;
+    if constexpr (sizeof(AT) == 8) {
+        // exact fixed-point sketch sums per member (relative to the member's block maximum)
+        long long* qb = reinterpret_cast<long long*>(wb);
+        const int H = P.sk_headroom;
+        int Eb[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            Eb[j] = 1;
+            if (act & (1u << j))
+                for (int q = 0; q < nw; ++q) Eb[j] = max(Eb[j], emax_sh[j][q]);
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+            if (act & (1u << j))
+                for (int r = threadIdx.x; r <= Bn; r += blockDim.x)
+                    qb[j * SB + r] = (r < len) ? to_fixed((double)wb[j * SB + r], Eb[j], H) : 0;
+        __syncthreads();
+        for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
+            long long sums[G];
+            sum_list_g<G>(P.ent, sg[rr], sg[rr + 1], qb, SB, act, sums);
+#pragma unroll
+            for (int j = 0; j < G; ++j)
+                if (act & (1u << j))
+                    cpart[(int64_t)mb_sh[j] * s + rr] =
+                        exp_nonfinite(0.0, Eb[j]) ? (AT)NAN : (AT)((double)sums[j] * fixed_unit(0.0, Eb[j], H));
+        }
+    } else {
+        __syncthreads();
+        for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
+            AT sums[G];
+            sum_list_g<G>(P.ent, sg[rr], sg[rr + 1], wb, SB, act, sums);
+#pragma unroll
+            for (int j = 0; j < G; ++j)
+                if (act & (1u << j)) cpart[(int64_t)mb_sh[j] * s + rr] = sums[j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// Waits until the grid counter reaches target (acquire), polling with a growing sleep; after kGridWaitPolls polls it
+// gives up and sets *fail.  Once a wait of the cycle has given up, later ones return at once.
+constexpr int kGridWaitPolls = 1 << 20;  // about a second of polls (256 ns sleeps plus an L2 round trip each)
+__device__ __forceinline__ void grid_wait(unsigned long long* ctr, unsigned long long target, unsigned long long* fail) {
+    unsigned long long f;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(f) : "l"(fail) : "memory");
+    if (f) return;
+    unsigned ns = 32;
+    for (int it = 0; it < kGridWaitPolls; ++it) {
+        unsigned long long v;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+        if (v >= target) return;
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+    }
+    atomicOr(fail, 1ull);
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// Lane-strided sum of the per-block partials x[q * stride] for blocks q in [b0, b1) (lane l takes q = b0 + l,
+// b0 + l + 32, ... in increasing order, then a shuffle tree), with every load of a lane issued before the first add.
+// The loads bypass L1: in the fused step the partials come from other CTAs of the same launch.
+template <typename AT>
+__device__ __forceinline__ AT block_partials_sum(const AT* __restrict__ x, int64_t stride, int b0, int b1, int lane) {
+    constexpr int U = 4;
+    AT a = AT(0);
+    for (int q0 = b0 + lane; q0 < b1; q0 += 32 * U) {
+        AT t[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) t[u] = (q0 + 32 * u < b1) ? __ldcg(x + (int64_t)(q0 + 32 * u) * stride) : AT(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (q0 + 32 * u < b1) a += t[u];
+    }
+    return warp_sum(a);
+}
+
+// Truncated-Arnoldi update (NW = window size).  Each thread first loads its first PF rows of w' and of the window
+// vectors (they do not depend on the scalars); meanwhile warp 0 sums the problem's ||u_i||^2 partials and warps
+// 1..NW its window-dot partials, each with all loads in flight at once.  After one barrier thread 0 forms sigma_i
+// and the coefficients; after a second, the sketched column S A b_i (one warp per sketch row, rows spread over all
+// of the problem's blocks) and the row update.
+// Three 512-thread CTAs per SM (at most 42 registers; batches run many waves of blocks) for windows up to 3, two
+// for wider windows, which would spill within 42.
+// wsm: the block of w' in shared memory (the fused step, FP32/BF16), else null (w' read from W).  FUSED: the block's
+// partials of this step come from other CTAs of the same launch; thread 0 waits for all of them (target arrivals
+// at the step's grid counter) after the prefetch.
+template <int NW, typename VT, typename AT, bool FUSED>
+__device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last, const AT* __restrict__ wsm,
+                                                 unsigned long long target) {
+    // rows per thread loaded before the scalars (PF) and per round of the row loop (UR; all loads of a round are
+    // issued before its stores): the fused step has the whole 56-register budget here, the update kernel 42
+    constexpr bool WIDE = (sizeof(AT) == 8 && NW >= 3);
+    constexpr int PF = FUSED ? (WIDE ? 2 : 4) : ((sizeof(AT) == 8 && NW >= 5) ? 1 : 2);
+    constexpr int UR = FUSED ? (WIDE ? 2 : 4) : ((sizeof(AT) == 8 && NW >= 4) ? 1 : 2);
+    __shared__ AT coef_sh[kMaxTrunc];
+    __shared__ AT part_sh[kMaxTrunc + 1];
+    __shared__ double sig_sh;
+    __shared__ int stop_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int b = blockIdx.x;
+    const BlockInfo bi = block_info(P, b);
+    const int p = bi.prob;
+    const int N = P.N, s = P.s, m = P.m;
+    VT* Ub = (VT*)P.U;
+    const AT* W = (const AT*)P.W;
+    const int lo = i - NW + 1;
+    AT wv[PF], uv[PF][NW > 0 ? NW : 1];
+    if (!last) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int k = threadIdx.x + u * (int)blockDim.x;
+            const int r = bi.v0 + k;
+            wv[u] = (k < bi.len) ? (wsm ? wsm[k] : W[r]) : AT(0);
+#pragma unroll
+            for (int q = 0; q < NW; ++q)
+                uv[u][q] = (k < bi.len) ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
+        }
+    }
+    if constexpr (FUSED) {
+        if (threadIdx.x == 0) grid_wait(P.gsync, target, P.gsync + 1);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) stop_sh = cycle_idle(P, p, i) ? 1 : 0;
+    const int b0 = P.prob_b0[p], b1 = P.prob_b0[p + 1];
+    // ||u_i||^2 (warp 0; sigma_0 is known at i = 0) and the window dots u_l^T w' (warp 1 + q) over the blocks
+    if (warp == 0 && i > 0) {
+        const AT a = block_partials_sum((const AT*)P.normpart, 1, b0, b1, lane);
+        if (lane == 0) part_sh[0] = a;
+    } else if (warp >= 1 && warp <= NW) {
+        const AT a = block_partials_sum((const AT*)P.hpart + (warp - 1), kMaxTrunc, b0, b1, lane);
+        if (lane == 0) part_sh[warp] = a;
+    }
+    __syncthreads();
+    if (stop_sh) return;
+    const bool lead = (b == b0);  // the problem's first block writes its scalars
+    double* sigma = P.sigma + (int64_t)p * (m + 1);
+    if (threadIdx.x == 0) {
+        // sigma_i = 1/||u_i||
+        double sig = 1.0;
+        bool bad = false;
+        int why = 4;
+        if (i == 0) {
+            sig = sigma[0];
+        } else {
+            const double a2 = (double)part_sh[0];
+            bad = !(a2 > 0.0) || !isfinite(a2);
+            why = (a2 == 0.0) ? 4 : 6;
+            sig = 1.0 / sqrt(a2);
+        }
+        sig_sh = sig;
+        if (bad) {
+            stop_sh = 1;
+            if (lead) {
+                CycleState* cyc = P.cyc + p;
+                cyc->brk_reason = why;
+                atomicMin(&cyc->brk_step, i);
+            }
+        } else {
+            if (lead) sigma[i] = sig;
+            // h_l = sigma_l sigma_i (u_l^T w'); the stored update uses sigma_l^2 (u_l^T w')
+#pragma unroll
+            for (int q = 0; q < NW; ++q) {
+                const int l = lo + q;
+                const double a = (double)part_sh[1 + q];
+                const double sl = (l == i) ? sig : sigma[l];
+                coef_sh[q] = (AT)(sl * sl * a);
+                if (lead) P.hco[((int64_t)p * m + i) * kMaxTrunc + q] = sl * sig * a;
+            }
+        }
+    }
+    __syncthreads();
+    if (stop_sh) return;
+    const double sig_i = sig_sh;
+    // sketched column S A b_i = sigma_i S w': sketch row rr to warp rr / nb of the problem's block rr % nb
+    const double csc = P.sk_scale * sig_i;
+    const int nb = b1 - b0;
+    for (int rr = warp * nb + (b - b0); rr < s; rr += nw * nb) {
+        const AT a = block_partials_sum((const AT*)P.cpart + rr, s, b0, b1, lane);
+        if (lane == 0) P.C[((int64_t)p * m + i) * s + rr] = csc * (double)a;
+    }
+    if (last) return;
+    // u_{i+1} = 2^p2 (w' - sum_q coef_q u_{lo+q}), 2^p2 the power of two just below sigma_i
+    int p2;
+    frexp(sig_i, &p2);  // sigma_i = f * 2^p2, f in [0.5, 1)
+    p2 -= 1;
+    const AT sc2 = (AT)ldexp(1.0, p2);
+    AT cf[NW > 0 ? NW : 1];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) cf[q] = coef_sh[q];
+    VT* un = Ub + (int64_t)(i + 1) * N;
+    const unsigned long long pol = l2_keep_policy();
+    auto update = [&](int r, AT u, const AT (&uq)[NW > 0 ? NW : 1]) {
+#pragma unroll
+        for (int q = 0; q < NW; ++q) u -= cf[q] * uq[q];
+        if constexpr (sizeof(AT) == 8) u = mul_pow2((double)u, p2);
+        else u = u * sc2;
+        st_keep(un + r, u, pol);  // the next step gathers it and reads it as a window row
+    };
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+        const int k = threadIdx.x + u * (int)blockDim.x;
+        if (k < bi.len) update(bi.v0 + k, wv[u], uv[u]);
+    }
+    for (int k0 = threadIdx.x + PF * (int)blockDim.x; k0 < bi.len; k0 += UR * (int)blockDim.x) {
+        AT wr[UR], uq[UR][NW > 0 ? NW : 1];
+#pragma unroll
+        for (int u = 0; u < UR; ++u) {
+            const int k = k0 + u * (int)blockDim.x;
+            const bool ok = k < bi.len;
+            const int r = bi.v0 + k;
+            wr[u] = ok ? (wsm ? wsm[k] : W[r]) : AT(0);
+#pragma unroll
+            for (int q = 0; q < NW; ++q) uq[u][q] = ok ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < UR; ++u) {
+            const int k = k0 + u * (int)blockDim.x;
+            if (k < bi.len) update(bi.v0 + k, wr[u], uq[u]);
+        }
+    }
+}
+
+template <int NW, typename VT, typename AT>
+__global__ void __launch_bounds__(512, (NW <= 3) ? 3 : 2) k_inner_axpy(const Plan P, int i, int last) {
+    inner_axpy_block<NW, VT, AT, false>(P, i, last, nullptr, 0);
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// One inner step in one launch, for plans whose row blocks all fit on the GPU at once (one wave): the fused SpMV +
+// dots + sketch partials, then a grid-wide arrival (every CTA, also one with no step to take), then, once all of the
+// launch's partials are written, the truncated-Arnoldi update of the CTA's own rows.  Every CTA of the launch is
+// resident at the same time (the host launches it only when the occupancy allows all blocks at once, beside the
+// sketched-QR cluster), so the wait ends; it gives up after a bounded number of polls and raises the plan's sync
+// flag, which the outer step turns into an error.  The arithmetic and its order are those of the two kernels.
+template <int V, int U, int NW, typename MT, typename VT, typename AT>
+__global__ void __maxnreg__(56) k_inner_step(const Plan P, int i, const MT* __restrict__ val, int last) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AT* wblk = reinterpret_cast<AT*>(smem_raw);
+    __shared__ unsigned long long target_sh;
+    const bool active = inner_spmv_block<V, U, NW, MT, VT, AT>(P, i, val, wblk);
+    __threadfence();  // this thread's partials are visible device-wide before the CTA arrives
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long old = atomicAdd(P.gsync, 1ull);
+        target_sh = (old / gridDim.x + 1) * (unsigned long long)gridDim.x + (unsigned long long)P.gwait_extra;
+    }
+    if (!active) return;
+    // FP64: the shared block now holds the fixed-point image of w', so w' is read back from W
+    inner_axpy_block<NW, VT, AT, true>(P, i, last, sizeof(AT) == 8 ? nullptr : wblk, target_sh);
+}
+
+template <int V, int U, int NW, typename MT, typename VT, typename AT>
+static void inner_spmv_v(const Plan& p, int i, const MT* val) {
+    const size_t sm = (size_t)(p.Bn + 1) * sizeof(AT);
+    set_smem((const void*)k_inner_spmv<V, U, NW, MT, VT, AT>, sm);
+    k_inner_spmv<V, U, NW, MT, VT, AT><<<p.nblk, 512, sm, p.st>>>(p, i, val);
+}
+
+template <int NW, typename MT, typename VT, typename AT>
+static void inner_spmv_nw(const Plan& p, int i, const MT* val) {
+    if (p.vec == 0) inner_spmv_v<0, 1, NW, MT, VT, AT>(p, i, val);
+    else if (p.vec == 1) {
+        if constexpr (sizeof(MT) == 8) {  // FP64 one thread per row reads the SELL-32 copy (always built for it)
+            if (p.sl_off) inner_spmv_v<kVecSell, 1, NW, MT, VT, AT>(p, i, p.sl_val);
+            else inner_spmv_v<8, 4, NW, MT, VT, AT>(p, i, val);
+        } else {
+            inner_spmv_v<1, 1, NW, MT, VT, AT>(p, i, val);
+        }
+    }
+    else if (p.vec <= 8) inner_spmv_v<8, 4, NW, MT, VT, AT>(p, i, val);
+    else inner_spmv_v<32, 2, NW, MT, VT, AT>(p, i, val);
+}
+
+template <int G, int NW, typename MT, typename VT, typename AT>
+static void inner_spmv_g(const Plan& p, int i, const MT* val) {
+    const size_t sm = (size_t)G * (p.Bn + 1) * sizeof(AT);
+    set_smem((const void*)k_inner_spmv_grp<G, NW, MT, VT, AT>, sm);
+    k_inner_spmv_grp<G, NW, MT, VT, AT><<<p.ngrp, 512, sm, p.st>>>(p, i, val);
+}
+
+template <int NW, typename MT, typename VT, typename AT>
+static void inner_spmv_gsel(const Plan& p, int i, const MT* val) {
+    if (p.G == 2) inner_spmv_g<2, NW, MT, VT, AT>(p, i, val);
+    else inner_spmv_g<4, NW, MT, VT, AT>(p, i, val);
+}
+
+template <typename MT, typename VT, typename AT>
+static void inner_spmv_t(const Plan& p, int i, const MT* val) {
+    const int nwin = (p.t > 0) ? std::min(p.t, i + 1) : 0;
+    if (p.G > 1) {  // grouped right-hand sides (one thread per row); windows above 4 are not grouped
+        switch (nwin) {
+            case 0: inner_spmv_gsel<0, MT, VT, AT>(p, i, val); return;
+            case 1: inner_spmv_gsel<1, MT, VT, AT>(p, i, val); return;
+            case 2: inner_spmv_gsel<2, MT, VT, AT>(p, i, val); return;
+            case 3: inner_spmv_gsel<3, MT, VT, AT>(p, i, val); return;
+            case 4: inner_spmv_gsel<4, MT, VT, AT>(p, i, val); return;
+            default: break;
+        }
+    }
+    switch (nwin) {
+        case 0: inner_spmv_nw<0, MT, VT, AT>(p, i, val); break;
+        case 1: inner_spmv_nw<1, MT, VT, AT>(p, i, val); break;
+        case 2: inner_spmv_nw<2, MT, VT, AT>(p, i, val); break;
+        case 3: inner_spmv_nw<3, MT, VT, AT>(p, i, val); break;
+        case 4: inner_spmv_nw<4, MT, VT, AT>(p, i, val); break;
+        case 5: inner_spmv_nw<5, MT, VT, AT>(p, i, val); break;
+        case 6: inner_spmv_nw<6, MT, VT, AT>(p, i, val); break;
+        case 7: inner_spmv_nw<7, MT, VT, AT>(p, i, val); break;
+        default: inner_spmv_nw<8, MT, VT, AT>(p, i, val); break;
+    }
+}
+
+
+// ---- fused step ----
+template <int V, int U, int NW, typename MT, typename VT, typename AT>
+static bool inner_step_v(const Plan& p, int i, const MT* val, bool last) {
+    const void* fn = (const void*)k_inner_step<V, U, NW, MT, VT, AT>;
+    const size_t sm = (size_t)(p.Bn + 1) * sizeof(AT);
+    set_smem(fn, sm);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 512, sm) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if ((int64_t)per_sm * p.sms < p.nblk) return false;  // not one wave: the two kernels
+    k_inner_step<V, U, NW, MT, VT, AT><<<p.nblk, 512, sm, p.st>>>(p, i, val, last ? 1 : 0);
+    return true;
+}
+
+template <int NW, typename MT, typename VT, typename AT>
+static bool inner_step_nw(const Plan& p, int i, const MT* val, bool last) {
+    if (p.vec == 0) {  // length-binned SpMV: fused in FP32 only (FP64 measured slower fused: 399 vs 380 ms, Zipf 2M)
+        if constexpr (sizeof(MT) == 8) return false;
+        else return inner_step_v<0, 1, NW, MT, VT, AT>(p, i, val, last);
+    }
+    if (p.vec == 1) {
+        if constexpr (sizeof(MT) == 8) {  // FP64 one thread per row reads the SELL-32 copy
+            return p.sl_off ? inner_step_v<kVecSell, 1, NW, MT, VT, AT>(p, i, p.sl_val, last) : false;
+        } else {
+            return inner_step_v<1, 1, NW, MT, VT, AT>(p, i, val, last);
+        }
+    }
+    if (p.vec <= 8) return inner_step_v<8, 4, NW, MT, VT, AT>(p, i, val, last);
+    return inner_step_v<32, 2, NW, MT, VT, AT>(p, i, val, last);
+}
+
+template <typename MT, typename VT, typename AT>
+static bool inner_step_t(const Plan& p, int i, const MT* val, bool last) {
+    const int nwin = (p.t > 0) ? std::min(p.t, i + 1) : 0;
+    switch (nwin) {
+        case 0: return inner_step_nw<0, MT, VT, AT>(p, i, val, last);
+        case 1: return inner_step_nw<1, MT, VT, AT>(p, i, val, last);
+        case 2: return inner_step_nw<2, MT, VT, AT>(p, i, val, last);
+        case 3: return inner_step_nw<3, MT, VT, AT>(p, i, val, last);
+        case 4: return inner_step_nw<4, MT, VT, AT>(p, i, val, last);
+        default: return false;  // wider windows: the two kernels
+    }
+}
+
+
+template <int NW, typename VT, typename AT>
+static void inner_axpy_nw(const Plan& p, int i, bool last) {
+    k_inner_axpy<NW, VT, AT><<<p.nblk, 512, 0, p.st>>>(p, i, last ? 1 : 0);
+}
+
+template <typename VT, typename AT>
+static void inner_axpy_t(const Plan& p, int i, bool last) {
+    const int nwin = (p.t > 0) ? std::min(p.t, i + 1) : 0;
+    switch (nwin) {
+        case 0: inner_axpy_nw<0, VT, AT>(p, i, last); break;
+        case 1: inner_axpy_nw<1, VT, AT>(p, i, last); break;
+        case 2: inner_axpy_nw<2, VT, AT>(p, i, last); break;
+        case 3: inner_axpy_nw<3, VT, AT>(p, i, last); break;
+        case 4: inner_axpy_nw<4, VT, AT>(p, i, last); break;
+        case 5: inner_axpy_nw<5, VT, AT>(p, i, last); break;
+        case 6: inner_axpy_nw<6, VT, AT>(p, i, last); break;
+        case 7: inner_axpy_nw<7, VT, AT>(p, i, last); break;
+        default: inner_axpy_nw<8, VT, AT>(p, i, last); break;
+    }
+}
+
+}  // namespace sfg

@@ -166,6 +166,17 @@ void launch_inner_spmv(const Plan& p, int i);
 // The fused inner step (inner SpMV kernel and Arnoldi update in one launch with a grid-wide arrival in between) when
 // the plan's row blocks fit on the GPU at once and the window is at most 4; false (nothing launched) otherwise.
 bool launch_inner_step(const Plan& p, int i, bool last);
+// Per-precision instances behind launch_inner_spmv, launch_inner_step and launch_inner_axpy (inner_f64.cu: FP64;
+// inner_f32.cu: FP32 inner; inner_bf16.cu: BF16 basis); they launch but do not count.
+void inner_spmv_f64(const Plan& p, int i);
+void inner_spmv_f32(const Plan& p, int i);
+void inner_spmv_bf16(const Plan& p, int i);
+bool inner_step_f64(const Plan& p, int i, bool last);
+bool inner_step_f32(const Plan& p, int i, bool last);
+bool inner_step_bf16(const Plan& p, int i, bool last);
+void inner_axpy_f64(const Plan& p, int i, bool last);
+void inner_axpy_f32(const Plan& p, int i, bool last);
+void inner_axpy_bf16(const Plan& p, int i, bool last);
 void launch_inner_axpy(const Plan& p, int i, bool last);
 cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st);  // cluster launch on stream st
 void launch_inner_finish(const Plan& p, double* z);  // y = R^{-1} d, z = sum_l y_l b_l (FP64)
