@@ -103,3 +103,24 @@ def test_convdiff_batch_recipe():
     assert b.shape == (4 * A.n,)
     cfg = workloads.CONFIGS["batch_512"]
     assert (cfg.nrhs, cfg.m, cfg.t, cfg.s, cfg.precision) == (4, 40, 2, 160, "fp32")
+
+
+def test_roofline_byte_counts_match_the_per_step_figures():
+    """bench.py's algorithmic bytes per inner step (A once with column indices and row pointers; b_i read, w written
+    and read back, the t window vectors for the update and t - 1 of them again for the dots, b_{i+1} written; the
+    sketch hashed, so no bytes for S) give, for the 3D convection-diffusion 128^3 workload with t = 2, about 301 MB
+    per FP64 step and 184 MB per FP32 step; the fused inner kernel's own count (gather lists and block partials
+    instead of the update's vectors) is 268.6 MB in FP64."""
+    import bench
+
+    cfg = workloads.CONFIGS["cd3d_128"]
+    n, nnz = 128 ** 3, 14_581_760
+    assert cfg.t == 2
+    fp64 = bench.alg_bytes_inner_step(n, nnz, cfg.t, 8)
+    fp32 = bench.alg_bytes_inner_step(n, nnz, cfg.t, 4)
+    assert fp64 == nnz * 12 + 4 * (n + 1) + 7 * n * 8
+    assert abs(fp64 / 1e6 - 300.8) < 0.1 and abs(fp32 / 1e6 - 183.8) < 0.1
+    nblk = -(-n // 7296)
+    assert nblk == 288
+    k1 = bench.alg_bytes_inner_spmv(n, nnz, cfg.t, cfg.zeta, cfg.s, nblk, 8)
+    assert abs(k1 / 1e6 - 268.6) < 0.1
