@@ -18,6 +18,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -56,7 +57,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"sfgmres_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -103,7 +104,9 @@ class ClockSampler:
 
 
 def alg_bytes_inner_spmv(n, nnz, t, zeta, s, nblk, sv):
-    """Compulsory bytes of one fused inner SpMV + dots + sketch launch (stated in the design doc)."""
+    """Compulsory bytes of one fused inner SpMV + dots + sketch launch: A (values, column indices, row pointers), b_i
+    gathered once, the t - 1 older window vectors, w written, the sketch gather lists and segment table, and the
+    per-block partials."""
     a = nnz * (sv + 4) + 4 * (n + 1)          # CSR values + column indices + row pointers
     vec = n * sv * (1 + max(t - 1, 0)) + n * sv  # b_i (gathered once) + older window vectors + w written
     sk = 2 * n * zeta + 4 * (nblk * s + 1) + sv * nblk * (s + t)  # gather lists, segment table, partials
@@ -113,7 +116,7 @@ def alg_bytes_inner_spmv(n, nnz, t, zeta, s, nblk, sv):
 def alg_bytes_inner_step(n, nnz, t, sv):
     """Compulsory bytes of one whole inner step (fused SpMV + dots + sketch, Arnoldi update; the sketch hashed, so no
     bytes for S): A once, b_i read, w written and read back, t window vectors read for the update, t - 1 of them
-    again for the dots, b_{i+1} written (stated in the design doc)."""
+    again for the dots, b_{i+1} written."""
     return nnz * (sv + 4) + 4 * (n + 1) + (2 * t + 3) * n * sv
 
 
