@@ -1,15 +1,23 @@
 """Pins for the oracle's sparse-sign embedding (Eq. 1; Clarkson-Woodruff sketch of Section 4.1)."""
+import os
+
 import numpy as np
 import pytest
 
 from oracle import sketch as sk
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
 def test_splitmix64_published_outputs():
-    # First outputs of SplitMix64 started at state 0, as printed by the published reference implementation
-    # (Vigna, splitmix64.c, after Steele, Lea & Flood, OOPSLA 2014).
-    got = sk.splitmix64_sequence(0, 3)
-    assert [int(x) for x in got] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    # First outputs of SplitMix64 started at state 0, as printed by the published reference implementation (the
+    # fixture cites it).
+    with open(os.path.join(GOLDEN, "splitmix64_state0.txt")) as f:
+        want = [int(line, 16) for line in f if line.strip() and not line.startswith("#")]
+    assert len(want) == 3
+    got = sk.splitmix64_sequence(0, len(want))
+    assert [int(x) for x in got] == want
 
 
 @pytest.mark.parametrize("seed", [0, 1, 12345, 2**63 + 17])
