@@ -40,6 +40,13 @@ __device__ __forceinline__ unsigned long long l2_keep_policy() {
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
+// Eviction priority "first", for the last read of such a vector (it then leaves L2 before the ones still needed).
+__device__ __forceinline__ unsigned long long l2_drop_policy() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// ld_keep(p, pol) loads with the L2 policy pol (from l2_keep_policy or l2_drop_policy).
 __device__ __forceinline__ double ld_keep(const double* p, unsigned long long pol) {
     double v;
     asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));

@@ -560,15 +560,23 @@ __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last,
     const AT* W = (const AT*)P.W;
     const int lo = i - NW + 1;
     AT wv[PF], uv[PF][NW > 0 ? NW : 1];
+    // last reads of w' and of the oldest window vector (the next step's window starts one later): L2 may drop them
+    // (FP64 and FP32 bases; measured slower with a BF16 basis, which keeps plain loads)
+    constexpr bool DROP = sizeof(VT) >= 4;
+    const unsigned long long drop = l2_drop_policy();
+    auto win = [&](int q, int r) -> AT {
+        const VT* a = Ub + (int64_t)(lo + q) * N + r;
+        return (DROP && q == 0 && NW > 1) ? ld_keep(a, drop) : ld_plain(a);
+    };
+    auto wrd = [&](int r) -> AT { return DROP ? ld_keep(W + r, drop) : W[r]; };
     if (!last) {
 #pragma unroll
         for (int u = 0; u < PF; ++u) {
             const int k = threadIdx.x + u * (int)blockDim.x;
             const int r = bi.v0 + k;
-            wv[u] = (k < bi.len) ? (wsm ? wsm[k] : W[r]) : AT(0);
+            wv[u] = (k < bi.len) ? (wsm ? wsm[k] : wrd(r)) : AT(0);
 #pragma unroll
-            for (int q = 0; q < NW; ++q)
-                uv[u][q] = (k < bi.len) ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
+            for (int q = 0; q < NW; ++q) uv[u][q] = (k < bi.len) ? win(q, r) : AT(0);
         }
     }
     if constexpr (FUSED) {
@@ -663,9 +671,9 @@ __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last,
             const int k = k0 + u * (int)blockDim.x;
             const bool ok = k < bi.len;
             const int r = bi.v0 + k;
-            wr[u] = ok ? (wsm ? wsm[k] : W[r]) : AT(0);
+            wr[u] = ok ? (wsm ? wsm[k] : wrd(r)) : AT(0);
 #pragma unroll
-            for (int q = 0; q < NW; ++q) uq[u][q] = ok ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
+            for (int q = 0; q < NW; ++q) uq[u][q] = ok ? win(q, r) : AT(0);
         }
 #pragma unroll
         for (int u = 0; u < UR; ++u) {
