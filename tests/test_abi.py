@@ -70,3 +70,19 @@ def test_product_path_does_not_import_the_oracle():
             if fn.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dp, fn)).read()
                 assert "oracle" not in re.findall(r"(?:import|from)\s+(\w+)", text), fn
+
+
+def test_binding_constants_match_the_header():
+    """Every SFGMRES_OPT_* key and status code the header defines has the same value in the binding, and every
+    option key has a name in Solver.set/get."""
+    from paper_2506_18408_gb300 import sfgmres as py
+
+    text = open(os.path.join(ROOT, "include", "sfgmres.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+SFGMRES_(\w+)\s+\(?(-?\d+)\)?", text)}
+    opts = {k[4:]: v for k, v in defs.items() if k.startswith("OPT_")}
+    assert len(opts) >= 14
+    for name, value in opts.items():
+        assert getattr(py, "OPT_" + name) == value, name
+    assert sorted(py.Solver._KEYS.values()) == sorted(opts.values())
+    for name in ("OK", "NOT_CONVERGED", "BREAKDOWN", "ERR_INVALID_ARG", "ERR_CUDA", "ERR_OOM", "ERR_NAN"):
+        assert getattr(py, name) == defs[name], name
