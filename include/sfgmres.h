@@ -259,6 +259,21 @@ SFGMRES_API int sfgmres_pattern_outer(sfgmres_t h, const double* u, const double
 SFGMRES_API int sfgmres_inner_cycle(sfgmres_t h, const double* v, double* z, int32_t m, int32_t s, int32_t k, double* basis,
                         double* y, int32_t* k_out, int32_t* reason_out);
 
+/* Restarted sGMRES (Algorithm 2, with one sGMRES cycle as the variable preconditioner M_c): starting from x_0,
+ * r_c = b - A x_c, z_c = M_c^{-1} r_c (one cycle on r_c / ||r_c|| with rules C1 and C2, rescaled by ||r_c||) and
+ * x_{c+1} = x_c + z_c, until ||r_c|| <= tol * ||b|| or max_cycles cycles have run.  The comparison method of the
+ * paper's experiments: no outer minimisation, so its residuals may stagnate where FGMRES keeps decreasing.
+ * Single-system handles only; the precision option applies to the cycles (x and r stay FP64).
+ *   b, x0, x      n float64, device or host pointers (x0 may be NULL: zero; x may alias x0)
+ *   m, s, k, tol  as for sfgmres_solve; max_cycles >= 0
+ *   res_hist      optional host float64[max_cycles + 1]: ||r_c|| / ||b|| for c = 0 .. cycles_out
+ *   cycles_out    optional host int32: cycles run
+ * Returns SFGMRES_OK (converged), SFGMRES_NOT_CONVERGED (max_cycles reached), SFGMRES_BREAKDOWN (a cycle accepted
+ * no column; x is the last iterate), or an error code. */
+SFGMRES_API int sfgmres_solve_restarted(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m, int32_t s,
+                                        int32_t k, double tol, int32_t max_cycles, double* res_hist,
+                                        int32_t* cycles_out);
+
 /* c = S v for the handle's embedding with s rows (Eq. 1).  v: device float64[n], c: device float64[s].
  * Single-system handles only. */
 SFGMRES_API int sfgmres_sketch_apply(sfgmres_t h, int32_t s, const double* v, double* c);

@@ -333,6 +333,12 @@ __global__ void k_fill(int64_t n, double v, double* __restrict__ b) {
         b[i] = v;
 }
 
+// x += a z
+__global__ void k_axpy_scalar(int64_t n, double a, const double* __restrict__ z, double* __restrict__ x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += a * z[i];
+}
+
 // x = 0 over the rows of the problems whose flag has bit 2 set (right-hand side zero).
 __global__ void k_zero_flagged(const Plan P, double* __restrict__ x) {
     const BlockInfo bi = block_info(P, blockIdx.x);
@@ -1729,6 +1735,84 @@ int sfgmres_inner_cycle(sfgmres_t h, const double* v, double* z, int32_t m, int3
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
     return cs.k == 0 ? SFGMRES_BREAKDOWN : SFGMRES_OK;
+}
+
+int sfgmres_solve_restarted(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m, int32_t s,
+                            int32_t k, double tol, int32_t max_cycles, double* res_hist, int32_t* cycles_out) {
+    if (!h) return SFGMRES_ERR_INVALID_ARG;
+    if (h->nsys != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "sfgmres_solve_restarted needs a single-system handle");
+    if (max_cycles < 0) return fail(h, SFGMRES_ERR_INVALID_ARG, "max_cycles must be >= 0");
+    int rc = check_solve_args(h, b, x, m, s, k, tol);
+    if (rc) return rc;
+    CK(cudaSetDevice(h->dev));
+    Plan P;
+    // one outer slot: Vb holds r, nu its scale 1/||r||, Z the cycle's z (nothing else of the outer state is used)
+    if ((rc = prepare(h, 1, m, s, k, 1, &P, nullptr))) return rc;
+    const size_t nbytes = (size_t)P.N * sizeof(double);
+    if ((rc = ensure(h, h->bst, nbytes))) return rc;
+    if ((rc = ensure(h, h->xst, nbytes))) return rc;
+    double* db = (double*)h->bst.p;
+    double* dx = (double*)h->xst.p;
+    double* dz = P.Z;
+    CK(cudaMemcpyAsync(db, b, nbytes, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    if (x0) {
+        CK(cudaMemcpyAsync(dx, x0, nbytes, is_device_ptr(x0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           h->st));
+    } else {
+        k_fill<<<grid_for(P.N), 256, 0, h->st>>>(P.N, 0.0, dx);
+        ++g_launches;
+    }
+    OuterState* host_ost = (OuterState*)h->h_ost.p;
+    CycleState* hc = (CycleState*)h->h_cyc.p;
+    int status = SFGMRES_NOT_CONVERGED, c = 0;
+    std::string msg;
+    for (;; ++c) {
+        // r_c = b - A x_c into the outer slot, beta = ||r_c||, ||b||, nu = 1/beta
+        launch_residual(P, db, dx, P.Vb, false);
+        launch_init_state(P, tol);
+        CK(cudaMemcpyAsync(host_ost, P.ost, sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        CK(cudaGetLastError());
+        const OuterState os = host_ost[0];
+        if (!std::isfinite(os.beta) || !std::isfinite(os.bnorm) || os.nan) {
+            status = SFGMRES_ERR_NAN;
+            msg = "non-finite value in the residual";
+            break;
+        }
+        if (res_hist) res_hist[c] = (os.bnorm > 0.0) ? os.beta / os.bnorm : 0.0;
+        if (os.beta <= os.tol_abs) {
+            status = SFGMRES_OK;
+            break;
+        }
+        if (c == max_cycles) break;
+        // z_c: one sGMRES cycle (rules C1, C2) on r_c / beta; x_{c+1} = x_c + beta z_c
+        if ((rc = run_cycle(h, P, -1, P.Vb, P.nu, P.jmax + 1, 0, dz))) return rc;
+        CK(cudaMemcpyAsync(hc, P.cyc, sizeof(CycleState), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        CK(cudaGetLastError());
+        if (P.gsync) {
+            unsigned long long gave_up = 0;
+            CK(cudaMemcpy(&gave_up, P.gsync + 1, sizeof(gave_up), cudaMemcpyDeviceToHost));
+            if (gave_up) return fail(h, SFGMRES_ERR_CUDA, "the fused inner step's grid-wide wait gave up");
+        }
+        if (hc->reason == 6) {
+            status = SFGMRES_ERR_NAN;
+            msg = "non-finite value in the inner cycle";
+            break;
+        }
+        if (hc->k == 0) {  // the cycle accepted no column: x stays
+            status = SFGMRES_BREAKDOWN;
+            break;
+        }
+        k_axpy_scalar<<<grid_for(P.N), 256, 0, h->st>>>(P.N, os.beta, dz, dx);
+        ++g_launches;
+    }
+    CK(cudaMemcpyAsync(x, dx, nbytes, is_device_ptr(x) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    if (cycles_out) *cycles_out = c;
+    if (status == SFGMRES_ERR_NAN) return fail(h, SFGMRES_ERR_NAN, msg);
+    return status;
 }
 
 int sfgmres_sketch_apply(sfgmres_t h, int32_t s, const double* v, double* c) {

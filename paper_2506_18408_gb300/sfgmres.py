@@ -30,7 +30,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SKETCH_KIND = {"sparse_sign": 0, "identity": 1}
 
 EXPORTED = ["sfgmres_create", "sfgmres_create_batch", "sfgmres_set_option", "sfgmres_get_option", "sfgmres_solve",
-            "sfgmres_solve_transpose", "sfgmres_solve_batch", "sfgmres_autotune", "sfgmres_update_values", "sfgmres_pattern_outer", "sfgmres_inner_cycle",
+            "sfgmres_solve_transpose", "sfgmres_solve_batch", "sfgmres_solve_restarted", "sfgmres_autotune", "sfgmres_update_values", "sfgmres_pattern_outer", "sfgmres_inner_cycle",
             "sfgmres_sketch_apply", "sfgmres_sketch_apply_noalloc", "sfgmres_sketch_pattern", "sfgmres_spmv",
             "sfgmres_destroy", "sfgmres_last_error", "sfgmres_version"]
 
@@ -72,6 +72,7 @@ def load():
     lib.sfgmres_solve_transpose.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, C.POINTER(Stats)]
     lib.sfgmres_solve_batch.argtypes = [vp, i32, vp, vp, vp, i32, i32, i32, f64, i32, C.POINTER(BatchStats)]
     lib.sfgmres_autotune.argtypes = [vp, i32, i32, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(f64)]
+    lib.sfgmres_solve_restarted.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, i32, vp, C.POINTER(i32)]
     lib.sfgmres_update_values.argtypes = [vp, vp]
     lib.sfgmres_pattern_outer.argtypes = [vp, vp, vp, f64, vp]
     lib.sfgmres_inner_cycle.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, C.POINTER(i32), C.POINTER(i32)]
@@ -188,6 +189,15 @@ def sfgmres_update_values(h: int, vals) -> None:
 
 def sfgmres_pattern_outer(h: int, u, v, alpha: float, out) -> None:
     _check(h, load().sfgmres_pattern_outer(h, _ptr(u), _ptr(v), float(alpha), _ptr(out)), allow_positive=False)
+
+
+def sfgmres_solve_restarted(h: int, b, x0, x, m: int, s: int, k: int, tol: float, max_cycles: int,
+                            res_hist=None) -> tuple:
+    """Returns ``(status, cycles)``; ``res_hist`` (NumPy float64[max_cycles + 1]) receives ||r_c|| / ||b||."""
+    cyc = C.c_int32()
+    rc = _check(h, load().sfgmres_solve_restarted(h, _ptr(b), _ptr(x0), _ptr(x), m, s, k, tol, max_cycles,
+                                                  _ptr(res_hist), C.byref(cyc)))
+    return rc, cyc.value
 
 
 def sfgmres_inner_cycle(h: int, v, z, m: int, s: int, k: int, basis=None, y=None):
@@ -344,6 +354,18 @@ class Solver:
     def pattern_outer(self, u, v, alpha: float, out) -> None:
         """out[p] += alpha * u[row(p)] * v[col(p)] over the stored entries of A."""
         sfgmres_pattern_outer(self.h, u, v, alpha, out)
+
+    def solve_restarted(self, b, x0=None, *, m: int, s: int, k: int, tol: float = 1e-8, max_cycles: int = 50,
+                        out=None):
+        """Restarted sGMRES (Algorithm 2) on ``b`` (CUDA tensor or NumPy array); returns ``(x, info)`` with the
+        residual history ``||r_c|| / ||b||`` for c = 0 .. cycles."""
+        import torch
+
+        if out is None:
+            out = torch.empty_like(b) if hasattr(b, "data_ptr") else np.empty_like(b)
+        hist = np.zeros(max_cycles + 1, dtype=np.float64)
+        rc, cycles = sfgmres_solve_restarted(self.h, b, x0, out, m, s, k, tol, max_cycles, hist)
+        return out, {"status": rc, "cycles": cycles, "rel_res_hist": list(hist[:cycles + 1])}
 
     def inner_cycle(self, v, *, m: int, s: int, k: int, basis: bool = True):
         """One sGMRES cycle on the unit CUDA vector ``v``; returns ``(z, k, reason, basis[(m+1), n] or None, y)``."""

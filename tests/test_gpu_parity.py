@@ -237,3 +237,23 @@ def test_repeat_solves_are_bitwise_reproducible():
     x1, _ = sv.solve(dev_vec(b), m=30, s=120, k=4)
     x2, _ = sv.solve(dev_vec(b), m=30, s=120, k=4)
     assert torch.equal(x1, x2)
+
+
+def test_restarted_sgmres_follows_algorithm_2():
+    """Restarted sGMRES (Algorithm 2: x_{c+1} = x_c + z_c, z_c one sGMRES cycle on r_c with rules C1 and C2) through
+    the C ABI follows the oracle's cycle by cycle: the same residual history to 1e-6 relative (each cycle accepts all
+    m = 30 columns here, far below the 1e15 condition threshold, so the two differ by rounding only) and the same
+    iterate."""
+    A = workloads.CONFIGS["cd2d_64"].build_matrix()
+    b = workloads.rhs(A.n, seed=0)
+    m, s, t, cycles = 30, 120, 2, 8
+    sv = _solver(A)
+    x, info = sv.solve_restarted(dev_vec(b), m=m, s=s, k=t, tol=1e-12, max_cycles=cycles)
+    xr, hist, _ = ofg.restarted(A.to_scipy(), b, m=m, s=s, t=t, tol=1e-12, max_outer=cycles)
+    assert info["status"] == 1 and info["cycles"] == cycles and len(hist) == cycles
+    gh = info["rel_res_hist"]
+    assert abs(gh[0] - 1.0) <= 1e-12  # x_0 = 0: r_0 = b
+    for c in range(cycles):
+        assert abs(gh[c + 1] - hist[c]) <= 1e-6 * hist[c] + 1e-15, (c, gh[c + 1], hist[c])
+    xh = x.cpu().numpy()
+    assert np.abs(xh - xr).max() <= 1e-6 * np.abs(xr).max()
