@@ -106,6 +106,11 @@ extern "C" {
                                         wait of a cycle gives up after its bounded polls (about a second), the later
                                         ones return at once, and the solve returns SFGMRES_ERR_CUDA; the handle stays
                                         usable. */
+#define SFGMRES_OPT_OUTER_VARIANT 15  /* 0 (default): FGMRES, the iterate minimises the residual over x0 + span Z
+                                        (Algorithm 1).  1: FFOM, the iterate solves the square Hessenberg system
+                                        (Galerkin condition), its residual given by Eq. 4; the convergence test and
+                                        res_est use that residual, and a step whose square system is singular ends
+                                        the solve with SFGMRES_BREAKDOWN keeping the previous iterate. */
 /* ---- sfgmres_solve_batch flags ---------------------------------------------------------------------------- */
 #define SFGMRES_SOLVE_TRANSPOSE 1    /* solve A_q^T x = b for every problem (see sfgmres_solve_transpose) */
 

@@ -100,6 +100,7 @@ struct sfgmres_ctx {
     int persistent = 0;  // 1: whole-cycle persistent kernel where the plan allows it
     int rhs_group = 1;  // right-hand sides per grouped inner-SpMV CTA (1: not grouped)
     int fuse_step = 1;  // 1: one launch per inner step where the row blocks fit on the GPU at once
+    int outer_variant = 0;  // 0: FGMRES; 1: FFOM
     int wait_extra = 0;  // fused step: arrivals waited for beyond the launch's blocks (test of the give-up path)
     bool step_fused = false;  // the last cycle ran the fused inner step
     double cond_thr = 1e15;
@@ -795,6 +796,7 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     P.ost = (OuterState*)h->ost.p;
     P.sms = h->sms;
     P.gwait_extra = h->wait_extra;
+    P.outer_variant = h->outer_variant;
     if (h->fuse_step) {
         if ((rc = ensure(h, h->gsync, 2 * sizeof(unsigned long long)))) return rc;
         P.gsync = (unsigned long long*)h->gsync.p;
@@ -916,7 +918,7 @@ std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
     for (int64_t v : std::initializer_list<int64_t>{(int64_t)P.G, (int64_t)P.ngrp, (int64_t)P.nnz, (int64_t)P.vec, (int64_t)P.N, (int64_t)P.P, (int64_t)P.nblk, (int64_t)P.Bn,
                       (int64_t)P.s, (int64_t)P.zeta, (int64_t)P.kind, (int64_t)P.sk_headroom, (int64_t)P.prec,
                       (int64_t)P.m, (int64_t)P.t, (int64_t)P.qr_cluster, (int64_t)P.jmax, (int64_t)h->c3,
-                      (int64_t)h->profile, (int64_t)P.gwait_extra})
+                      (int64_t)h->profile, (int64_t)P.gwait_extra, (int64_t)P.outer_variant})
         k.push_back((uint64_t)v);
     uint64_t bits;
     std::memcpy(&bits, &P.sk_scale, 8);
@@ -1488,6 +1490,10 @@ int sfgmres_set_option(sfgmres_t h, int32_t key, double v) {
             if (iv != v || iv < 0 || iv > 1024) return fail(h, SFGMRES_ERR_INVALID_ARG, "step wait extra must be 0..1024");
             h->wait_extra = iv;
             return 0;
+        case SFGMRES_OPT_OUTER_VARIANT:
+            if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "outer variant must be 0 or 1");
+            h->outer_variant = iv;
+            return 0;
         case SFGMRES_OPT_GRAPH:
             if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "graph must be 0 or 1");
             h->use_graph = iv;
@@ -1522,6 +1528,7 @@ int sfgmres_get_option(sfgmres_t h, int32_t key, double* v) {
         case SFGMRES_OPT_PERSISTENT: *v = h->persistent; return 0;
         case SFGMRES_OPT_FUSED_STEP: *v = h->fuse_step; return 0;
         case SFGMRES_OPT_STEP_WAIT_EXTRA: *v = h->wait_extra; return 0;
+        case SFGMRES_OPT_OUTER_VARIANT: *v = h->outer_variant; return 0;
         default: return fail(h, SFGMRES_ERR_INVALID_ARG, "unknown option key");
     }
 }

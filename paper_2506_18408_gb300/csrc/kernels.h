@@ -93,6 +93,7 @@ struct Plan {
 
     // outer FGMRES
     int jmax = 0;
+    int outer_variant = 0;     // 0: FGMRES (least squares, Algorithm 1); 1: FFOM (square system, residual of Eq. 4)
     double* Vb = nullptr;      // [(jmax+1) * N] unnormalised outer basis, v_l = nu[p][l] Vb_l
     double* Z = nullptr;       // [jmax * N]
     double* nu = nullptr;      // [P][jmax+1]

@@ -251,13 +251,18 @@ __global__ void k_outer_givens(const Plan P, int j) {
     const double est = fabs(g[j + 1]);
     const double ffom = (c != 0.0) ? est / fabs(c) : INFINITY;
     P.nu[og + j + 1] = (hn > 0.0) ? 1.0 / hn : 0.0;
+    if (P.outer_variant == 1 && c == 0.0) {  // FFOM: the square system of this step is singular; keep step j's x
+        ost->breakdown = 2;
+        return;
+    }
+    const double e = (P.outer_variant == 1) ? ffom : est;  // the variant's residual estimate
     ost->j = j + 1;
-    ost->est = est;
+    ost->est = e;
     ost->ffom = ffom;
     ost->breakdown = (hn == 0.0) ? 1 : 0;
-    ost->conv_est = (est <= ost->tol_abs) ? 1 : 0;
+    ost->conv_est = (e <= ost->tol_abs) ? 1 : 0;
     if (!isfinite(est) || !isfinite(hn) || !isfinite(r)) ost->nan = 1;
-    P.est_hist[oh + j] = est / ost->bnorm;
+    P.est_hist[oh + j] = e / ost->bnorm;
     P.ffom_hist[oh + j] = ffom / ost->bnorm;
 }
 
@@ -288,10 +293,13 @@ __global__ void k_final_y(const Plan P) {
     const double* g = P.g + (int64_t)p * ldo;
     double* y = P.yo + (int64_t)p * P.jmax;
     const int lane = threadIdx.x;
-    for (int l = lane; l < J; l += 32) rhs[l] = g[l];
+    // FFOM: the square system before the last rotation (c, s) has last diagonal c r_JJ and last right-hand side
+    // g_J / c; the rows above are those of R
+    const double cl = (P.outer_variant == 1 && J > 0) ? P.cs[(int64_t)p * P.jmax + J - 1] : 1.0;
+    for (int l = lane; l < J; l += 32) rhs[l] = (l == J - 1) ? g[l] / cl : g[l];
     __syncwarp();
     for (int l = J - 1; l >= 0; --l) {
-        const double yl = rhs[l] / H[(int64_t)l * ldo + l];
+        const double yl = rhs[l] / (H[(int64_t)l * ldo + l] * ((l == J - 1) ? cl : 1.0));
         for (int q = lane; q < l; q += 32) rhs[q] -= H[(int64_t)l * ldo + q] * yl;
         if (lane == 0) y[l] = yl;
         __syncwarp();

@@ -24,7 +24,7 @@ ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NAN = -1, -2, -3, -4
 CSR_HOST = 1
 OPT_PRECISION, OPT_ZETA, OPT_COND_THRESHOLD, OPT_C3, OPT_MAX_OUTER, OPT_SKETCH_KIND, OPT_PROFILE, \
     OPT_SPMV_VECTOR, OPT_BLOCK_ROWS, OPT_GRAPH, OPT_RHS_GROUP, OPT_PERSISTENT, OPT_FUSED_STEP, \
-    OPT_STEP_WAIT_EXTRA = range(1, 15)
+    OPT_STEP_WAIT_EXTRA, OPT_OUTER_VARIANT = range(1, 16)
 SOLVE_TRANSPOSE = 1
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SKETCH_KIND = {"sparse_sign": 0, "identity": 1}
@@ -250,7 +250,8 @@ class Solver:
              "max_outer": OPT_MAX_OUTER, "sketch_kind": OPT_SKETCH_KIND, "profile": OPT_PROFILE,
              "spmv_vector": OPT_SPMV_VECTOR, "block_rows": OPT_BLOCK_ROWS, "graph": OPT_GRAPH,
              "rhs_group": OPT_RHS_GROUP, "persistent": OPT_PERSISTENT,
-             "fused_step": OPT_FUSED_STEP, "step_wait_extra": OPT_STEP_WAIT_EXTRA}
+             "fused_step": OPT_FUSED_STEP, "step_wait_extra": OPT_STEP_WAIT_EXTRA,
+             "outer_variant": OPT_OUTER_VARIANT}
 
     def __init__(self, n, row_ptr, col, val, sketch_seed: int = 1, stream=None, **options):
         import torch

@@ -257,3 +257,30 @@ def test_restarted_sgmres_follows_algorithm_2():
         assert abs(gh[c + 1] - hist[c]) <= 1e-6 * hist[c] + 1e-15, (c, gh[c + 1], hist[c])
     xh = x.cpu().numpy()
     assert np.abs(xh - xr).max() <= 1e-6 * np.abs(xr).max()
+
+
+def test_ffom_outer_variant_follows_the_oracle():
+    """The FFOM outer variant (the iterate solves the square Hessenberg system; its residual is the one of Eq. 4)
+    through the C ABI converges like the oracle's: outer iteration counts within 1, per-step FFOM residuals within
+    1e-6 relative, true residual <= 1e-8.  The Arnoldi process is the FGMRES one, so an FGMRES solve on the same
+    handle reports the same FFOM residuals (bit for bit) and least-squares estimates no larger than them."""
+    A = workloads.CONFIGS["cd2d_64"].build_matrix()
+    b = workloads.rhs(A.n, seed=0)
+    m, s, t = 30, 120, 2
+    sv = _solver(A, max_outer=30)
+    sv.set("outer_variant", 1)
+    x, info = sv.solve(dev_vec(b), m=m, s=s, k=t, tol=1e-8)
+    ref = ofg.fgmres(A.to_scipy(), b, None, m=m, s=s, t=t, tol=1e-8, max_outer=30, variant="ffom")
+    assert info["status"] == 0 and ref.status == 0
+    xh = x.cpu().numpy()
+    assert np.linalg.norm(b - A.to_scipy() @ xh) / np.linalg.norm(b) <= 1e-8
+    assert abs(info["outer_iters"] - ref.outer_iters) <= 1
+    est = info["res_est"]
+    assert est == info["ffom_res"]
+    for j in range(min(len(est), len(ref.est_hist)) - 1):
+        assert abs(est[j] - ref.est_hist[j]) <= 1e-6 * ref.est_hist[j] + 1e-13, (j, est[j], ref.est_hist[j])
+    sv.set("outer_variant", 0)
+    _, info0 = sv.solve(dev_vec(b), m=m, s=s, k=t, tol=1e-8)
+    common = min(len(info0["ffom_res"]), len(est))
+    assert info0["ffom_res"][:common] == info["ffom_res"][:common]
+    assert all(a <= f for a, f in zip(info0["res_est"][:common], info["ffom_res"][:common]))
