@@ -1,0 +1,76 @@
+"""Zero-fill incomplete LU (ILU(0)), the preconditioner of the paper's "-p" experiments (Section 4, Table 1).
+TEST INFRASTRUCTURE ONLY.
+
+:func:`ilu0` factors a sparse A into a unit lower triangular L and an upper triangular U whose nonzeros lie in the
+pattern of A, by Gaussian elimination in row order (the IKJ form) in which every update that would create an entry
+outside that pattern is dropped.  Consequently (L U)_ij = A_ij for every (i, j) in the pattern of A, and when the
+pattern of A admits no fill (a tridiagonal matrix, for instance) L U is the exact LU factorisation without pivoting.
+:func:`ilu0_solve` applies M^{-1} = (L U)^{-1} by forward and back substitution.  Plain Python loops over the rows:
+for the small matrices of the pins only.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def ilu0(A):
+    """Returns ``(L, U)`` as SciPy CSR matrices: L unit lower triangular (its unit diagonal stored), U upper
+    triangular, both with their nonzeros in the pattern of A.  Raises ``ZeroDivisionError`` on a zero pivot."""
+    A = sp.csr_matrix(A, dtype=np.float64)
+    A.sort_indices()
+    n = A.shape[0]
+    rows = []
+    for i in range(n):
+        a, e = A.indptr[i], A.indptr[i + 1]
+        rows.append(dict(zip(A.indices[a:e].tolist(), A.data[a:e].tolist())))
+    for i in range(n):
+        ri = rows[i]
+        for k in sorted(c for c in ri if c < i):  # eliminate with rows k < i in increasing order
+            ukk = rows[k].get(k, 0.0)
+            if ukk == 0.0:
+                raise ZeroDivisionError(f"zero pivot in row {k}")
+            lik = ri[k] / ukk
+            ri[k] = lik
+            for j, ukj in rows[k].items():
+                if j > k and j in ri:  # updates outside the pattern of A are dropped
+                    ri[j] -= lik * ukj
+    li, lj, lv, ui, uj, uv = [], [], [], [], [], []
+    for i, ri in enumerate(rows):
+        li.append(i), lj.append(i), lv.append(1.0)
+        for j, v in ri.items():
+            if j < i:
+                li.append(i), lj.append(j), lv.append(v)
+            else:
+                ui.append(i), uj.append(j), uv.append(v)
+    L = sp.csr_matrix((lv, (li, lj)), shape=(n, n))
+    U = sp.csr_matrix((uv, (ui, uj)), shape=(n, n))
+    return L, U
+
+
+def ilu0_solve(L, U, v: np.ndarray) -> np.ndarray:
+    """z = (L U)^{-1} v: forward substitution with the unit lower L, then back substitution with U."""
+    n = v.shape[0]
+    L = sp.csr_matrix(L)
+    U = sp.csr_matrix(U)
+    y = np.array(v, dtype=np.float64)
+    for i in range(n):
+        a, e = L.indptr[i], L.indptr[i + 1]
+        for p in range(a, e):
+            j = L.indices[p]
+            if j < i:
+                y[i] -= L.data[p] * y[j]
+    z = y
+    for i in range(n - 1, -1, -1):
+        a, e = U.indptr[i], U.indptr[i + 1]
+        d = 0.0
+        for p in range(a, e):
+            j = U.indices[p]
+            if j > i:
+                z[i] -= U.data[p] * z[j]
+            elif j == i:
+                d = U.data[p]
+        if d == 0.0:
+            raise ZeroDivisionError(f"zero diagonal of U in row {i}")
+        z[i] /= d
+    return z

@@ -1,0 +1,75 @@
+"""Pins for the oracle's zero-fill incomplete LU (the ILU(0) preconditioner of the paper's "-p" runs)."""
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import workloads
+from oracle import ilu
+
+
+def _pattern(M):
+    M = sp.coo_matrix(M)
+    return set(zip(M.row.tolist(), M.col.tolist()))
+
+
+def test_tridiagonal_has_no_fill_so_ilu0_is_the_exact_lu():
+    rng = np.random.default_rng(0)
+    n = 40
+    A = sp.diags([rng.uniform(-1, 1, n - 1), rng.uniform(4, 5, n), rng.uniform(-1, 1, n - 1)], [-1, 0, 1]).tocsr()
+    L, U = ilu.ilu0(A)
+    np.testing.assert_allclose((L @ U).toarray(), A.toarray(), rtol=0, atol=1e-14)
+    # against the textbook LU without pivoting (Doolittle), written out densely
+    D = A.toarray()
+    Ld, Ud = np.eye(n), D.copy()
+    for k in range(n - 1):
+        for i in range(k + 1, n):
+            Ld[i, k] = Ud[i, k] / Ud[k, k]
+            Ud[i, k:] -= Ld[i, k] * Ud[k, k:]
+    np.testing.assert_allclose(L.toarray(), Ld, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(U.toarray(), np.triu(Ud), rtol=0, atol=1e-13)
+    v = rng.standard_normal(n)
+    np.testing.assert_allclose(ilu.ilu0_solve(L, U, v), np.linalg.solve(D, v), rtol=1e-12, atol=1e-12)
+
+
+def test_product_matches_a_on_its_pattern_and_factors_stay_in_it():
+    A = workloads.convdiff(12, (20.0, 10.0)).to_scipy().tocsr()  # 5-point upwind: fill would appear in exact LU
+    L, U = ilu.ilu0(A)
+    pa = _pattern(A)
+    assert _pattern(sp.tril(L, -1)) <= pa and _pattern(U) <= pa
+    assert np.all(sp.triu(L, 1).toarray() == 0) and np.all(sp.tril(U, -1).toarray() == 0)
+    np.testing.assert_array_equal(L.diagonal(), np.ones(A.shape[0]))
+    P = (L @ U).tocsr()
+    Ad = A.toarray()
+    for i, j in pa:
+        assert abs(P[i, j] - Ad[i, j]) <= 1e-12 * max(1.0, abs(Ad[i, j])), (i, j)
+    # the exact LU does fill in: ILU(0) drops those entries, so L U differs from A off the pattern
+    assert np.abs((P - A).toarray()).max() > 1e-6
+    Lx, Ux = sla.lu(Ad, permute_l=False)[1:]
+    assert np.count_nonzero(np.abs(Ux) > 1e-14) > U.nnz
+
+
+def test_solve_inverts_the_product_and_diagonal_special_case():
+    rng = np.random.default_rng(1)
+    A = workloads.convdiff(10, (5.0, 3.0)).to_scipy().tocsr()
+    L, U = ilu.ilu0(A)
+    v = rng.standard_normal(A.shape[0])
+    z = ilu.ilu0_solve(L, U, v)
+    np.testing.assert_allclose((L @ U) @ z, v, rtol=0, atol=1e-12 * np.abs(v).max())
+    d = rng.uniform(1, 2, 25)
+    L2, U2 = ilu.ilu0(sp.diags(d).tocsr())
+    np.testing.assert_array_equal(L2.toarray(), np.eye(25))
+    np.testing.assert_array_equal(U2.diagonal(), d)
+    np.testing.assert_allclose(ilu.ilu0_solve(L2, U2, v[:25]), v[:25] / d, rtol=1e-15)
+
+
+def test_preconditioned_operator_is_much_better_conditioned():
+    """M^{-1} A (M = L U from ILU(0)) is far better conditioned than A scaled by its diagonal on the convection-
+    diffusion matrices (the reason for the paper's preconditioned runs): measured 2-5 against 23-48 for the 2D
+    100-point matrices below, so a factor of 4 is a safe margin."""
+    for beta in ((20.0, 10.0), (5.0, 3.0), (0.0, 0.0), (50.0, 30.0)):
+        A = workloads.convdiff(10, beta).to_scipy().tocsr()
+        L, U = ilu.ilu0(A)
+        n = A.shape[0]
+        Minv_A = np.column_stack([ilu.ilu0_solve(L, U, A[:, [k]].toarray().ravel()) for k in range(n)])
+        Dinv_A = A.toarray() / A.diagonal()[:, None]
+        assert np.linalg.cond(Minv_A) < 0.25 * np.linalg.cond(Dinv_A), beta
