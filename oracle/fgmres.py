@@ -23,6 +23,7 @@ import dataclasses
 from typing import Callable, List, Optional
 
 import numpy as np
+from scipy.sparse.linalg import LinearOperator
 
 from .sgmres import CycleResult, sgmres_cycle
 from .sketch import sketch_matrix
@@ -60,11 +61,15 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
            max_outer: int = 50, sketch_seed: int = 1, zeta: int = 8, sketch_kind: str = "sparse_sign",
            cond_thr: float = 1e15, c3: bool = True, outer_orth: str = "mgs", variant: str = "fgmres",
            inner: str = "fp64", precond: Optional[Callable[[np.ndarray], np.ndarray]] = None,
-           record: bool = False, track_true: bool = False) -> FGMRESResult:
+           record: bool = False, track_true: bool = False,
+           right_precond: Optional[Callable[[np.ndarray], np.ndarray]] = None) -> FGMRESResult:
     """Solve ``A x = b`` by FGMRES (or FFOM) preconditioned with sGMRES cycles (Algorithm 1 + Section 3).
 
     ``A``: scipy sparse (FP64).  ``m``: inner basis size (C1, the paper's ``k_max``); ``t``: Arnoldi truncation;
     ``s``: sketch rows.  ``precond`` replaces the sGMRES cycle by an arbitrary ``v -> z`` (used by the pins).
+    ``right_precond`` (``u -> M^{-1} u``, e.g. ILU(0) from :mod:`oracle.ilu`) right-preconditions the inner solver:
+    each sGMRES cycle approximates ``(A M^{-1})^{-1} v_j`` and ``z_j`` is ``M^{-1}`` of its result, so the outer
+    FGMRES still minimises the residual of ``A x = b`` (FP64 inner cycles only).
     """
     n = b.shape[0]
     b = np.asarray(b, dtype=np.float64)
@@ -84,6 +89,10 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
         dt = INNER_DTYPES[inner]
         A_in = A if dt == np.float64 else A.astype(dt)
         S_in = S if dt == np.float64 else S.astype(dt)
+        if right_precond is not None:
+            if dt != np.float64:
+                raise ValueError("right preconditioning needs FP64 inner cycles")
+            A_in = LinearOperator((n, n), matvec=lambda u: A @ right_precond(u), dtype=np.float64)
 
     V = np.zeros((n, max_outer + 1))
     Z = np.zeros((n, max_outer))
@@ -103,9 +112,9 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
         v = V[:, j]
         if precond is None:
             scale = ffom_prev if (c3 and np.isfinite(ffom_prev)) else None
-            cyc = sgmres_cycle(A, v, S, m, t, cond_thr, bound_scale=scale, bound_tol=tol * nb,
-                               inner=inner, A_inner=A_in, S_inner=S_in, record=record)
-            z = cyc.z
+            cyc = sgmres_cycle(A if right_precond is None else A_in, v, S, m, t, cond_thr, bound_scale=scale,
+                               bound_tol=tol * nb, inner=inner, A_inner=A_in, S_inner=S_in, record=record)
+            z = cyc.z if right_precond is None else np.asarray(right_precond(cyc.z), dtype=np.float64)
             ks.append(cyc.k)
             reasons.append(cyc.reason)
             if cycles is not None:

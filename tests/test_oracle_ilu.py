@@ -73,3 +73,28 @@ def test_preconditioned_operator_is_much_better_conditioned():
         Minv_A = np.column_stack([ilu.ilu0_solve(L, U, A[:, [k]].toarray().ravel()) for k in range(n)])
         Dinv_A = A.toarray() / A.diagonal()[:, None]
         assert np.linalg.cond(Minv_A) < 0.25 * np.linalg.cond(Dinv_A), beta
+
+
+def test_right_preconditioned_fgmres_special_cases_and_ilu0_gain():
+    """FGMRES with the inner sGMRES cycles on A M^{-1} and z_j = M^{-1} (their result): with M = I it is the
+    unpreconditioned run bit for bit; with M = A (exact solves) A M^{-1} = I, so one outer step with a one-column
+    cycle solves the system to rounding; with M = ILU(0) it converges in far fewer outer and inner steps on the
+    convection-diffusion matrix (measured 5 outer / 36 inner against 13 / 122)."""
+    import scipy.sparse.linalg as spl
+    from oracle import fgmres as ofg
+
+    A = workloads.convdiff(32, (20.0, 10.0)).to_scipy().tocsr()
+    b = workloads.rhs(A.shape[0], seed=0)
+    kw = dict(m=10, s=40, t=2, tol=1e-8, max_outer=60)
+    plain = ofg.fgmres(A, b, None, **kw)
+    ident = ofg.fgmres(A, b, None, right_precond=lambda u: np.array(u, dtype=np.float64), **kw)
+    assert ident.est_hist == plain.est_hist and ident.inner_k == plain.inner_k
+    Ac = A.tocsc()
+    exact = ofg.fgmres(A, b, None, right_precond=lambda u: spl.spsolve(Ac, u), **kw)
+    assert exact.status == 0 and exact.outer_iters == 1 and exact.inner_k == [1]
+    assert exact.rel_res_true <= 1e-14
+    L, U = ilu.ilu0(A)
+    pre = ofg.fgmres(A, b, None, right_precond=lambda u: ilu.ilu0_solve(L, U, u), **kw)
+    assert plain.status == 0 and pre.status == 0 and pre.rel_res_true <= 1e-8
+    assert pre.outer_iters <= 0.6 * plain.outer_iters
+    assert sum(pre.inner_k) <= 0.5 * sum(plain.inner_k)
