@@ -131,3 +131,23 @@ def test_fig1_setting_restarted_stagnates_fgmres_converges():
     res = ofg.fgmres(A, b, m=100, s=n, t=100, tol=1e-8, max_outer=40, sketch_kind="identity", c3=False)
     assert res.status == ofg.CONVERGED
     assert hist[-1] > 1e-3
+
+
+def test_truncation_sweep_lengthens_c2_driven_cycles():
+    """Section 4's observation on the truncation parameter t, with a large k_max and rule C2 alone deciding the
+    cycle length (C3 off): larger t gives better-conditioned bases and so longer cycles; t = 0 (a power basis, no
+    orthogonalisation) ends every cycle by C2 well before k_max, yet FGMRES still converges; from t = 2 on this 2D
+    convection-diffusion matrix the first cycle reaches k_max (C1)."""
+    A = workloads.convdiff(32, (20.0, 10.0)).to_scipy().tocsr()
+    b = workloads.rhs(A.shape[0], seed=0)
+    m = 300
+    first = []
+    for t in range(6):
+        r = ofg.fgmres(A, b, None, m=m, s=600, t=t, tol=1e-8, max_outer=40, c3=False)
+        assert r.status == 0 and r.rel_res_true <= 1e-8, t
+        first.append(r.inner_k[0])
+        if t == 0:
+            assert all(k < m for k in r.inner_k) and set(r.inner_reason) == {2} and r.outer_iters > 3
+        if t >= 2:
+            assert r.inner_k[0] == m and r.inner_reason[0] == 1
+    assert all(a <= b2 for a, b2 in zip(first, first[1:])), first
