@@ -120,6 +120,18 @@ def alg_bytes_inner_step(n, nnz, t, sv):
     return nnz * (sv + 4) + 4 * (n + 1) + (2 * t + 3) * n * sv
 
 
+def max_over_ranks(dist, value: float, device) -> float:
+    """The largest of every rank's ``value`` (each rank calls it with one float); ``value`` itself without a
+    process group."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
 
@@ -202,11 +214,7 @@ def run_ours(args):
         tp, ip = timed("fp64", max(3, args.steps // 2), 1, profile=True)
     t32, i32 = timed("fp32", args.steps, max(3, args.warmup // 2))
     t16, i16 = timed("bf16", args.steps, max(3, args.warmup // 2))
-    sec = statistics.mean(t64)
-    if dist is not None:
-        tt = torch.tensor([sec], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        sec = float(tt.item())
+    sec = max_over_ranks(dist, statistics.mean(t64), dev)
 
     # end to end through the public API with pinned host buffers (copies inside the timed region)
     solver.set("precision", "fp64")
