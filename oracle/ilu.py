@@ -5,8 +5,11 @@ TEST INFRASTRUCTURE ONLY.
 pattern of A, by Gaussian elimination in row order (the IKJ form) in which every update that would create an entry
 outside that pattern is dropped.  Consequently (L U)_ij = A_ij for every (i, j) in the pattern of A, and when the
 pattern of A admits no fill (a tridiagonal matrix, for instance) L U is the exact LU factorisation without pivoting.
-:func:`ilu0_solve` applies M^{-1} = (L U)^{-1} by forward and back substitution.  Plain Python loops over the rows:
-for the small matrices of the pins only.
+:func:`ilu0_solve` applies M^{-1} = (L U)^{-1} by forward and back substitution.  :func:`colouring` orders the
+rows colour by colour (a greedy colouring of the symmetrised pattern: no two coupled rows share a colour), so that
+ILU(0) of the symmetrically permuted matrix P A P^T has diagonal colour blocks in both factors and each colour's rows
+of a triangular solve are independent of one another.  Plain Python loops over the rows: for the small matrices of
+the pins only.
 """
 from __future__ import annotations
 
@@ -74,3 +77,24 @@ def ilu0_solve(L, U, v: np.ndarray) -> np.ndarray:
             raise ZeroDivisionError(f"zero diagonal of U in row {i}")
         z[i] /= d
     return z
+
+
+def colouring(A):
+    """Greedy colouring of the pattern of A + A^T (each row, in natural order, takes the smallest colour not used by
+    an already coloured neighbour).  Returns ``(perm, colours, starts)``: ``perm`` lists the rows colour by colour
+    (natural order within a colour), ``colours[i]`` is row i's colour, and colour c occupies positions
+    ``starts[c] .. starts[c + 1]`` of ``perm``."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    G = (A + A.T).tocsr()
+    colours = np.full(n, -1, dtype=np.int64)
+    for i in range(n):
+        used = {int(colours[j]) for j in G.indices[G.indptr[i]:G.indptr[i + 1]] if j != i and colours[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        colours[i] = c
+    nc = int(colours.max()) + 1 if n else 0
+    perm = np.concatenate([np.flatnonzero(colours == c) for c in range(nc)]) if n else np.zeros(0, np.int64)
+    starts = np.concatenate([[0], np.cumsum([np.count_nonzero(colours == c) for c in range(nc)])])
+    return perm, colours, starts

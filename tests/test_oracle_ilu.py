@@ -98,3 +98,30 @@ def test_right_preconditioned_fgmres_special_cases_and_ilu0_gain():
     assert plain.status == 0 and pre.status == 0 and pre.rel_res_true <= 1e-8
     assert pre.outer_iters <= 0.6 * plain.outer_iters
     assert sum(pre.inner_k) <= 0.5 * sum(plain.inner_k)
+
+
+def test_colouring_makes_each_colour_independent():
+    """The greedy colouring gives the 7-point stencil two colours (red-black: i + j + k even / odd); no two rows of a
+    colour are coupled, so ILU(0) of the permuted matrix has diagonal colour blocks in L and U (each colour's rows of
+    a triangular solve are independent), and it still solves the permuted system exactly up to the dropped fill."""
+    A = workloads.convdiff(6, (20.0, 10.0, 5.0)).to_scipy().tocsr()
+    n = A.shape[0]
+    perm, colours, starts = ilu.colouring(A)
+    assert len(starts) == 3 and sorted(perm.tolist()) == list(range(n))
+    ijk = np.array([(i, j, k) for k in range(6) for j in range(6) for i in range(6)])
+    parity = ijk.sum(axis=1) % 2
+    assert np.array_equal(colours, parity) or np.array_equal(colours, 1 - parity)
+    G = (A + A.T).tocoo()
+    assert all(colours[r] != colours[c] for r, c in zip(G.row, G.col) if r != c)
+    Pm = A[perm][:, perm].tocsr()
+    L, U = ilu.ilu0(Pm)
+    for c in range(2):
+        a, e = starts[c], starts[c + 1]
+        assert sp.tril(L[a:e, a:e], -1).nnz == 0 and sp.triu(U[a:e, a:e], 1).nnz == 0
+    v = np.random.default_rng(3).standard_normal(n)
+    z = ilu.ilu0_solve(L, U, v)
+    np.testing.assert_allclose((L @ U) @ z, v, rtol=0, atol=1e-12 * np.abs(v).max())
+    P = (L @ U).tocsr()
+    pa = _pattern(Pm)
+    Pd, Ad = P.toarray(), Pm.toarray()
+    assert all(abs(Pd[i, j] - Ad[i, j]) <= 1e-12 * max(1.0, abs(Ad[i, j])) for i, j in pa)
