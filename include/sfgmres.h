@@ -305,9 +305,11 @@ SFGMRES_API int sfgmres_sketch_pattern(sfgmres_t h, int32_t s, int32_t* rows, in
  * Scratch: a fixed 8 MiB static device array (2^20 doubles) in the library, held on every GPU that loads the
  * library until the process exits.  All calls share it and it keeps the last call's contents; every call overwrites
  * the part it reads, so nothing needs to start at zero.  Calls whose work overlaps on the GPU (different streams,
- * different host threads) race on it and must be serialised by the caller.  The first call on a device looks up the
- * array's device address with that device current; make that first call before any stream capture.  Errors:
- * SFGMRES_ERR_INVALID_ARG (sizes, NULL), SFGMRES_ERR_CUDA (launch); sfgmres_last_error(NULL) describes them. */
+ * different host threads) race on it and must be serialised by the caller.  The first call on a device does a
+ * one-time set-up with that device current (it looks up the array's device address and raises the kernel's
+ * shared-memory limit to what s = 4096 needs); make that first call before any stream capture.  Errors:
+ * SFGMRES_ERR_INVALID_ARG (sizes, NULL), SFGMRES_ERR_CUDA (set-up or a launch of this call; an error left by
+ * unrelated earlier work is not reported); sfgmres_last_error(NULL) describes them. */
 SFGMRES_API int sfgmres_sketch_apply_noalloc(int64_t n, int32_t s, int32_t zeta, uint64_t sketch_seed,
                                              const double* v, double* c, void* stream);
 

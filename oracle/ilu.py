@@ -80,13 +80,15 @@ def ilu0_solve(L, U, v: np.ndarray) -> np.ndarray:
 
 
 def colouring(A):
-    """Greedy colouring of the pattern of A + A^T (each row, in natural order, takes the smallest colour not used by
+    """Greedy colouring of the pattern of A + A^T (every stored entry of A is an edge, whatever its value; each row, in natural order, takes the smallest colour not used by
     an already coloured neighbour).  Returns ``(perm, colours, starts)``: ``perm`` lists the rows colour by colour
     (natural order within a colour), ``colours[i]`` is row i's colour, and colour c occupies positions
     ``starts[c] .. starts[c + 1]`` of ``perm``."""
     A = sp.csr_matrix(A)
     n = A.shape[0]
-    G = (A + A.T).tocsr()
+    P = A.copy()
+    P.data = np.ones_like(P.data)  # the stored pattern alone: a pair a_ij = -a_ji must not cancel in A + A^T
+    G = (P + P.T).tocsr()
     colours = np.full(n, -1, dtype=np.int64)
     for i in range(n):
         used = {int(colours[j]) for j in G.indices[G.indptr[i]:G.indptr[i + 1]] if j != i and colours[j] >= 0}

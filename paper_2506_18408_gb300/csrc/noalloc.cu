@@ -93,9 +93,14 @@ __global__ void k_noalloc_reduce(int nblk, int s, double scale, const double* __
     c[r] = scale * a;
 }
 
-// Device address of the scratch array on the current device, looked up once per device (cudaGetSymbolAddress with
-// that device current) and cached.
-static cudaError_t scratch_address(double** out) {
+// Dynamic shared memory of k_noalloc_partials for s sketch rows: one 64-bit accumulator and one counter per row.
+static size_t partials_smem(int s) { return (size_t)s * (sizeof(long long) + sizeof(int)); }
+
+// Once per device, with that device current: look up the device address of the scratch array (cudaGetSymbolAddress;
+// in host code the array's name is only a host-side stand-in) and allow k_noalloc_partials the dynamic shared memory
+// of the largest sketch (4096 rows need 48 KiB, which with the kernel's static shared memory is above the default
+// limit).  Both results are cached per device.
+static cudaError_t device_setup(double** out) {
     static std::mutex mu;
     static double* cache[64] = {nullptr};
     int dev = 0;
@@ -104,6 +109,9 @@ static cudaError_t scratch_address(double** out) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
     if (!cache[dev]) {
+        e = cudaFuncSetAttribute((const void*)k_noalloc_partials, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)partials_smem(kMaxS));
+        if (e != cudaSuccess) return e;
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
@@ -111,6 +119,21 @@ static cudaError_t scratch_address(double** out) {
     }
     *out = cache[dev];
     return cudaSuccess;
+}
+
+// Launch with the error of this launch alone as the result (the launch API returns it; an error left behind by
+// unrelated earlier work is neither reported nor cleared here).  A failed launch's own error is cleared.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                          Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
 }
 
 }  // namespace sfg
@@ -138,9 +161,10 @@ extern "C" int sfgmres_sketch_apply_noalloc(int64_t n, int32_t s, int32_t zeta, 
         return SFGMRES_ERR_INVALID_ARG;
     }
     double* part = nullptr;
-    cudaError_t e = scratch_address(&part);
+    cudaError_t e = device_setup(&part);
     if (e != cudaSuccess) {
-        set_global_error(std::string("sfgmres_sketch_apply_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        set_global_error(std::string("sfgmres_sketch_apply_noalloc: device set-up (cudaFuncSetAttribute / "
+                                     "cudaGetSymbolAddress): ") + cudaGetErrorString(e));
         return SFGMRES_ERR_CUDA;
     }
     int64_t nblk = (n + kNoallocMinCols - 1) / kNoallocMinCols;
@@ -149,12 +173,18 @@ extern "C" int sfgmres_sketch_apply_noalloc(int64_t n, int32_t s, int32_t zeta, 
     Bn = ((Bn + 31) / 32) * 32;
     nblk = (n + Bn - 1) / Bn;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t sm = (size_t)s * (sizeof(long long) + sizeof(int));
-    k_noalloc_partials<<<(unsigned)nblk, 512, sm, st>>>(n, (int)Bn, s, zeta, sketch_seed, v, part);
-    k_noalloc_reduce<<<(s + 127) / 128, 128, 0, st>>>((int)nblk, s, 1.0 / std::sqrt((double)zeta), part, c);
-    e = cudaGetLastError();
+    e = launch(k_noalloc_partials, (unsigned)nblk, 512, partials_smem(s), st, n, (int)Bn, (int)s, (int)zeta,
+               sketch_seed, v, part);
     if (e != cudaSuccess) {
-        set_global_error(std::string("sfgmres_sketch_apply_noalloc: launch: ") + cudaGetErrorString(e));
+        set_global_error(std::string("sfgmres_sketch_apply_noalloc: launch of the block partials kernel: ") +
+                         cudaGetErrorString(e));
+        return SFGMRES_ERR_CUDA;
+    }
+    e = launch(k_noalloc_reduce, (unsigned)((s + 127) / 128), 128, 0, st, (int)nblk, (int)s,
+               1.0 / std::sqrt((double)zeta), (const double*)part, c);
+    if (e != cudaSuccess) {
+        set_global_error(std::string("sfgmres_sketch_apply_noalloc: launch of the reduction kernel: ") +
+                         cudaGetErrorString(e));
         return SFGMRES_ERR_CUDA;
     }
     return SFGMRES_OK;

@@ -125,3 +125,18 @@ def test_colouring_makes_each_colour_independent():
     pa = _pattern(Pm)
     Pd, Ad = P.toarray(), Pm.toarray()
     assert all(abs(Pd[i, j] - Ad[i, j]) <= 1e-12 * max(1.0, abs(Ad[i, j])) for i, j in pa)
+
+
+def test_colouring_uses_the_pattern_not_the_values():
+    """Two rows coupled by a skew-symmetric pair (a_01 = 1, a_10 = -1) are coupled in the pattern of A + A^T even
+    though the values of A + A^T cancel there; they must get different colours, or the multicolour triangular solves
+    would treat dependent rows as independent.  A stored zero is an edge too (it is part of ILU(0)'s pattern)."""
+    A = sp.csr_matrix(np.array([[2.0, 1.0, 0.0, 0.0],
+                                [-1.0, 2.0, 0.0, 0.0],
+                                [0.0, 0.0, 2.0, 0.0],
+                                [0.0, 0.0, 0.0, 2.0]]))
+    _, colours, starts = ilu.colouring(A)
+    assert colours[0] != colours[1] and len(starts) == 3
+    Z = sp.csr_matrix((np.array([2.0, 0.0, 2.0, 2.0]), np.array([0, 2, 1, 2]), np.array([0, 2, 3, 4])), shape=(3, 3))
+    _, cz, _ = ilu.colouring(Z)  # a_02 is a stored zero
+    assert cz[0] != cz[2]
