@@ -139,6 +139,12 @@ typedef struct {
     double t_qr_ms;          /* total device time of the sketched-QR update kernel */
     int64_t n_qr;
     double t_total_ms;       /* device time of the whole solve (first to last kernel) */
+    /* per outer step j (arrays of length hist_cap, caller-owned, may be NULL), for tracing the bound of Eq. 5,
+       ||r_j|| <= ||r~_{j-1}|| ||r_hat_j|| (r~ the FFOM residual, ||r~_{-1}|| = beta): */
+    double* inner_res;       /* ||r_hat_j|| = ||v_j - A z_j||, the true residual of inner cycle j (v_j has unit
+                                norm, so this is also its relative residual) */
+    double* inner_rho;       /* the sketched residual rho_k = ||S v_j - S A B_k y_k|| the cycle ended with, its
+                                estimate of ||r_hat_j|| (used by rule C3) */
 } sfgmres_stats;
 
 /* Filled by sfgmres_solve_batch when a non-NULL pointer is passed.  The arrays are caller-owned host arrays of

@@ -51,6 +51,7 @@ class FGMRESResult:
     beta: float = 0.0
     cycles: Optional[List[CycleResult]] = None
     rhat_hist: Optional[List[float]] = None  # ||v_j - A z_j|| per step (if requested)
+    rho_hist: Optional[List[float]] = None  # sketched residual rho_k each cycle ended with (if requested)
 
 
 def _sketch_for(n, s, zeta, seed, kind):
@@ -62,7 +63,7 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
            cond_thr: float = 1e15, c3: bool = True, outer_orth: str = "mgs", variant: str = "fgmres",
            inner: str = "fp64", precond: Optional[Callable[[np.ndarray], np.ndarray]] = None,
            record: bool = False, track_true: bool = False,
-           right_precond: Optional[Callable[[np.ndarray], np.ndarray]] = None) -> FGMRESResult:
+           right_precond: Optional[Callable[[np.ndarray], np.ndarray]] = None, trace: bool = False) -> FGMRESResult:
     """Solve ``A x = b`` by FGMRES (or FFOM) preconditioned with sGMRES cycles (Algorithm 1 + Section 3).
 
     ``A``: scipy sparse (FP64).  ``m``: inner basis size (C1, the paper's ``k_max``); ``t``: Arnoldi truncation;
@@ -70,6 +71,9 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
     ``right_precond`` (``u -> M^{-1} u``, e.g. ILU(0) from :mod:`oracle.ilu`) right-preconditions the inner solver:
     each sGMRES cycle approximates ``(A M^{-1})^{-1} v_j`` and ``z_j`` is ``M^{-1}`` of its result, so the outer
     FGMRES still minimises the residual of ``A x = b`` (FP64 inner cycles only).
+    ``trace`` records, per outer step, the true inner residual ``||v_j - A z_j||`` and the sketched residual the
+    cycle ended with (the two sides of the Eq. 5 bound and its estimate) without keeping the bases that ``record``
+    keeps.
     """
     n = b.shape[0]
     b = np.asarray(b, dtype=np.float64)
@@ -103,7 +107,8 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
     ffom_prev = beta  # first-step bound ||r_1|| <= beta ||rhat_1||
     est_hist, ffom_hist, ks, reasons = [], [], [], []
     true_hist = [] if track_true else None
-    rhat_hist = [] if record else None
+    rhat_hist = [] if (record or trace) else None
+    rho_hist = [] if (record or trace) else None
     cycles = [] if record else None
     status = NOT_CONVERGED
     x = x0.copy()
@@ -117,6 +122,8 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
             z = cyc.z if right_precond is None else np.asarray(right_precond(cyc.z), dtype=np.float64)
             ks.append(cyc.k)
             reasons.append(cyc.reason)
+            if rho_hist is not None:
+                rho_hist.append(float(cyc.rho[-1]) if cyc.rho else float("inf"))
             if cycles is not None:
                 cycles.append(cyc)
             if cyc.k == 0:
@@ -180,7 +187,7 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
         ffom_prev = ffom
     rel_true = float(np.linalg.norm(b - A @ x)) / nb
     res = FGMRESResult(x, status, j_done, rel_true, est_hist, ffom_hist, ks, reasons, true_hist, beta=beta,
-                       rhat_hist=rhat_hist, cycles=cycles)
+                       rhat_hist=rhat_hist, rho_hist=rho_hist, cycles=cycles)
     if record:
         res.V = V[:, : j_done + 1]
         res.Z = Z[:, :j_done]

@@ -128,10 +128,11 @@ struct sfgmres_ctx {
 
     // workspaces
     DevBuf U, W, sigma, normpart, hpart, cpart, C, Q, R, d, e, c0, rho, y, coef, hco, cyc;
-    DevBuf Vb, Z, nu, Wo, opart, npart, npart2, h1, h2, H, cs, sn, g, yo, est_hist, ffom_hist, k_hist, reason_hist,
+    DevBuf Vb, Z, nu, Wo, opart, npart, npart2, h1, h2, H, cs, sn, g, yo, est_hist, ffom_hist, ires_hist, rho_hist,
+        k_hist, reason_hist,
         ost;
     DevBuf bst, xst, x0st;  // staging / internal copies
-    DevBuf gsync;           // fused inner step: grid arrival counter and give-up flag (2 x u64)
+    DevBuf gsync;           // fused inner step: grid arrival counters [0], [2] and give-up flag [1] (u64)
 
     // pinned host mirrors of the per-problem device state
     HostBuf h_ost, h_cyc, h_pflag;
@@ -716,6 +717,8 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
         if ((rc = ensure(h, h->yo, Pn * J * 8))) return rc;
         if ((rc = ensure(h, h->est_hist, Pn * J * 8))) return rc;
         if ((rc = ensure(h, h->ffom_hist, Pn * J * 8))) return rc;
+        if ((rc = ensure(h, h->ires_hist, Pn * J * 8))) return rc;
+        if ((rc = ensure(h, h->rho_hist, Pn * J * 8))) return rc;
         if ((rc = ensure(h, h->k_hist, Pn * J * 4))) return rc;
         if ((rc = ensure(h, h->reason_hist, Pn * J * 4))) return rc;
     }
@@ -791,6 +794,8 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     P.yo = (double*)h->yo.p;
     P.est_hist = (double*)h->est_hist.p;
     P.ffom_hist = (double*)h->ffom_hist.p;
+    P.ires_hist = (double*)h->ires_hist.p;
+    P.rho_hist = (double*)h->rho_hist.p;
     P.k_hist = (int*)h->k_hist.p;
     P.reason_hist = (int*)h->reason_hist.p;
     P.ost = (OuterState*)h->ost.p;
@@ -798,7 +803,7 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     P.gwait_extra = h->wait_extra;
     P.outer_variant = h->outer_variant;
     if (h->fuse_step) {
-        if ((rc = ensure(h, h->gsync, 2 * sizeof(unsigned long long)))) return rc;
+        if ((rc = ensure(h, h->gsync, 4 * sizeof(unsigned long long)))) return rc;
         P.gsync = (unsigned long long*)h->gsync.p;
     } else {
         P.gsync = nullptr;
@@ -912,7 +917,8 @@ std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
                           (const void*)P.Wo, (const void*)P.opart, (const void*)P.npart, (const void*)P.npart2,
                           (const void*)P.h1, (const void*)P.h2, (const void*)P.H, (const void*)P.cs,
                           (const void*)P.sn, (const void*)P.g, (const void*)P.yo, (const void*)P.est_hist,
-                          (const void*)P.ffom_hist, (const void*)P.k_hist, (const void*)P.reason_hist,
+                          (const void*)P.ffom_hist, (const void*)P.ires_hist, (const void*)P.rho_hist,
+                          (const void*)P.k_hist, (const void*)P.reason_hist,
                           (const void*)P.ost, (const void*)P.st, (const void*)h->qst, (const void*)P.gsync})
         u(p);
     for (int64_t v : std::initializer_list<int64_t>{(int64_t)P.G, (int64_t)P.ngrp, (int64_t)P.nnz, (int64_t)P.vec, (int64_t)P.N, (int64_t)P.P, (int64_t)P.nblk, (int64_t)P.Bn,
@@ -1209,12 +1215,14 @@ int solve_single(sfgmres_t h, bool transpose, const double* b, const double* x0,
         st->rel_res_est = o.rel_est;
         const int cnt = std::min(o.outer + (status == SFGMRES_BREAKDOWN ? 1 : 0), jmax);
         std::vector<int> kh(std::max(cnt, 1)), rh(std::max(cnt, 1));
-        std::vector<double> eh(std::max(cnt, 1)), fh(std::max(cnt, 1));
+        std::vector<double> eh(std::max(cnt, 1)), fh(std::max(cnt, 1)), ih(std::max(cnt, 1)), qh(std::max(cnt, 1));
         if (cnt > 0) {
             CK(cudaMemcpy(kh.data(), P.k_hist, cnt * sizeof(int), cudaMemcpyDeviceToHost));
             CK(cudaMemcpy(rh.data(), P.reason_hist, cnt * sizeof(int), cudaMemcpyDeviceToHost));
             CK(cudaMemcpy(eh.data(), P.est_hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));
             CK(cudaMemcpy(fh.data(), P.ffom_hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(ih.data(), P.ires_hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(qh.data(), P.rho_hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));
         }
         int tot = 0;
         for (int q = 0; q < cnt; ++q) tot += kh[q];
@@ -1225,6 +1233,8 @@ int solve_single(sfgmres_t h, bool transpose, const double* b, const double* x0,
             if (st->inner_reason) st->inner_reason[q] = rh[q];
             if (st->res_est && q < o.outer) st->res_est[q] = eh[q];
             if (st->ffom_res && q < o.outer) st->ffom_res[q] = fh[q];
+            if (st->inner_res && q < o.outer) st->inner_res[q] = ih[q];
+            if (st->inner_rho && q < o.outer) st->inner_rho[q] = qh[q];
         }
         st->kernel_launches = g_launches - launches0;
         float tms = 0.f;
@@ -1401,7 +1411,7 @@ int sfgmres_destroy(sfgmres_t h) {
     DevBuf* bufs[] = {&h->U, &h->W, &h->sigma, &h->normpart, &h->hpart, &h->cpart, &h->C, &h->Q, &h->R, &h->d,
                       &h->e, &h->c0, &h->rho, &h->y, &h->coef, &h->hco, &h->cyc, &h->Vb, &h->Z, &h->nu, &h->Wo,
                       &h->opart, &h->npart, &h->npart2, &h->h1, &h->h2, &h->H, &h->cs, &h->sn, &h->g, &h->yo,
-                      &h->est_hist, &h->ffom_hist, &h->k_hist, &h->reason_hist, &h->ost, &h->bst, &h->xst,
+                      &h->est_hist, &h->ffom_hist, &h->ires_hist, &h->rho_hist, &h->k_hist, &h->reason_hist, &h->ost, &h->bst, &h->xst,
                       &h->x0st, &h->gsync};
     for (DevBuf* b : bufs) release(*b);
     for (Geo& g : h->geos) {

@@ -57,7 +57,7 @@ struct Plan {
     // SpMV reads A and the gather lists once per group): members grp_b[g] + j * grp_st[g], j < grp_n[g]
     int G = 1, ngrp = 0;
     int sms = 0;                   // SMs of the device (one-wave test of the fused step)
-    unsigned long long* gsync = nullptr;  // fused step: [0] grid arrival counter (reset per cycle), [1] wait gave up
+    unsigned long long* gsync = nullptr;  // fused step: [0], [2] grid arrival counters (reset per cycle), [1] a wait gave up
     int gwait_extra = 0;           // fused step: arrivals waited for beyond the launch's blocks (0; > 0 tests give-up)
     const int* grp_b = nullptr;
     const int* grp_n = nullptr;
@@ -110,6 +110,8 @@ struct Plan {
     double* yo = nullptr;      // [P][jmax]
     double* est_hist = nullptr;   // [P][jmax]
     double* ffom_hist = nullptr;  // [P][jmax]
+    double* ires_hist = nullptr;  // [P][jmax] ||v_j - A z_j|| (true residual of inner cycle j, v_j a unit vector)
+    double* rho_hist = nullptr;   // [P][jmax] the cycle's sketched residual rho_k (its estimate of that norm)
     int* k_hist = nullptr;        // [P][jmax]
     int* reason_hist = nullptr;   // [P][jmax]
     OuterState* ost = nullptr;    // [P]

@@ -138,8 +138,21 @@ __global__ void __launch_bounds__(512, 2) k_outer_spmv(const Plan P, int j) {
     spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, z + bi.cs, m0, m0 + bi.len, wb, P.perm, n0,
                                                     n01);
     __syncthreads();
-    for (int k = threadIdx.x; k < bi.len; k += blockDim.x) P.Wo[bi.v0 + k] = wb[k];
+    // the true residual of inner cycle j, r_hat_j = v_j - A z_j (v_j = nu_j Vb_j), for the bound of Eq. 5: its
+    // block partial of ||r_hat_j||^2 goes to npart2 (free during outer steps)
+    const double nuj = P.nu[(int64_t)bi.prob * (P.jmax + 1) + j];
+    const double* vj = P.Vb + (int64_t)j * P.N;
+    double r2 = 0.0;
+    for (int k = threadIdx.x; k < bi.len; k += blockDim.x) {
+        const double w = wb[k];
+        P.Wo[bi.v0 + k] = w;
+        const double rr = nuj * vj[bi.v0 + k] - w;
+        r2 += rr * rr;
+    }
     block_dots(P, bi, b, j, wb);
+    __shared__ double red[32];
+    r2 = block_sum(r2, red);
+    if (threadIdx.x == 0) P.npart2[b] = r2;
 }
 
 // out[p*ldo + l] = nu[p][l] * sum over the blocks of problem p of opart[b*ldo + l]  (one warp per (p, l)).
@@ -202,13 +215,19 @@ __global__ void k_outer_givens(const Plan P, int j) {
     const int p = blockIdx.x, lane = threadIdx.x;
     if (outer_idle(P, p)) return;
     const int ldo = P.jmax + 1, J = P.jmax;
-    double a = 0.0;
-    for (int q = P.prob_b0[p] + lane; q < P.prob_b0[p + 1]; q += 32) a += P.npart[q];
+    double a = 0.0, ar = 0.0;
+    for (int q = P.prob_b0[p] + lane; q < P.prob_b0[p + 1]; q += 32) {
+        a += P.npart[q];
+        ar += P.npart2[q];
+    }
     a = warp_sum(a);
+    ar = warp_sum(ar);
     if (lane != 0) return;
     OuterState* ost = P.ost + p;
     const CycleState* cyc = P.cyc + p;
     const int64_t oh = (int64_t)p * J, og = (int64_t)p * ldo;
+    P.ires_hist[oh + j] = sqrt(ar);  // ||v_j - A z_j||: the factor ||r_hat_j|| of the bound of Eq. 5
+    P.rho_hist[oh + j] = cyc->rho;   // the cycle's sketched estimate of it (rule C3)
     if (P.gsync && P.gsync[1]) {  // the inner cycle's grid-wide wait gave up: its results are not valid
         ost->sync_fail = 1;
         ost->nan = 1;

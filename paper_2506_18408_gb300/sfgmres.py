@@ -42,7 +42,8 @@ class Stats(C.Structure):
                 ("rel_res_true", C.c_double), ("rel_res_est", C.c_double), ("kernel_launches", C.c_int64),
                 ("t_inner_spmv_ms", C.c_double), ("n_inner_spmv", C.c_int64), ("t_inner_axpy_ms", C.c_double),
                 ("n_inner_axpy", C.c_int64), ("t_qr_ms", C.c_double), ("n_qr", C.c_int64),
-                ("t_total_ms", C.c_double)]
+                ("t_total_ms", C.c_double), ("inner_res", C.POINTER(C.c_double)),
+                ("inner_rho", C.POINTER(C.c_double))]
 
 
 class BatchStats(C.Structure):
@@ -301,7 +302,11 @@ class Solver:
         rh = (C.c_int32 * hist_cap)()
         eh = (C.c_double * hist_cap)()
         fh = (C.c_double * hist_cap)()
+        ih = (C.c_double * hist_cap)()
+        qh = (C.c_double * hist_cap)()
         st.hist_cap = hist_cap
+        st.inner_res = C.cast(ih, C.POINTER(C.c_double))
+        st.inner_rho = C.cast(qh, C.POINTER(C.c_double))
         st.inner_k = C.cast(kh, C.POINTER(C.c_int32))
         st.inner_reason = C.cast(rh, C.POINTER(C.c_int32))
         st.res_est = C.cast(eh, C.POINTER(C.c_double))
@@ -312,6 +317,7 @@ class Solver:
         info = {"status": rc, "outer_iters": J, "total_inner": st.total_inner, "rel_res_true": st.rel_res_true,
                 "rel_res_est": st.rel_res_est, "inner_k": list(kh[:cnt]), "inner_reason": list(rh[:cnt]),
                 "res_est": list(eh[: min(J, hist_cap)]), "ffom_res": list(fh[: min(J, hist_cap)]),
+                "inner_res": list(ih[: min(J, hist_cap)]), "inner_rho": list(qh[: min(J, hist_cap)]),
                 "kernel_launches": st.kernel_launches, "t_total_ms": st.t_total_ms,
                 "t_inner_spmv_ms": st.t_inner_spmv_ms, "n_inner_spmv": st.n_inner_spmv,
                 "t_inner_axpy_ms": st.t_inner_axpy_ms, "n_inner_axpy": st.n_inner_axpy, "t_qr_ms": st.t_qr_ms,

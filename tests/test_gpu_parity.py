@@ -284,3 +284,31 @@ def test_ffom_outer_variant_follows_the_oracle():
     common = min(len(info0["ffom_res"]), len(est))
     assert info0["ffom_res"][:common] == info["ffom_res"][:common]
     assert all(a <= f for a, f in zip(info0["res_est"][:common], info["ffom_res"][:common]))
+
+
+@pytest.mark.parametrize("name,make,m,s,t", [
+    ("cd2d_64", workloads.CONFIGS["cd2d_64"].build_matrix, 30, 120, 2),
+    ("zipf_20011", lambda: workloads.random_zipf(20_011, seed=0), 30, 120, 4),
+], ids=["cd2d_64", "zipf_20011"])
+def test_eq5_bound_traced_along_the_gpu_iteration(name, make, m, s, t):
+    """Eq. 5 along the GPU's own iteration: ||r_j|| <= ||r~_{j-1}|| ||r_hat_j|| at every outer step j, with r_j the
+    FGMRES residual (its Givens estimate), r~_{j-1} the FFOM residual of Eq. 4 of the previous step (beta at the first,
+    Section 2.1) and r_hat_j = v_j - A z_j the true residual of inner cycle j, which the solver reports per step
+    (inner_res) beside the sketched residual rho_k the cycle ended with (inner_rho, the estimate rule C3 uses).  Both
+    per-step quantities follow the oracle's to 1e-6 relative while the two runs take the same steps."""
+    A = make()
+    b = workloads.rhs(A.n, seed=0, dist="uniform" if name.startswith("zipf") else "normal")
+    sv = _solver(A, max_outer=50)
+    _, info = sv.solve(dev_vec(b), m=m, s=s, k=t, tol=1e-8)
+    ref = ofg.fgmres(A.to_scipy(), b, m=m, s=s, t=t, tol=1e-8, max_outer=50, trace=True)
+    est, ffom, ir, rho = info["res_est"], info["ffom_res"], info["inner_res"], info["inner_rho"]
+    J = info["outer_iters"]
+    assert info["status"] == 0 and len(ir) == len(rho) == J
+    prev = 1.0  # ||r~_0|| / ||b|| = beta / ||b|| = 1 with x0 = 0
+    for j in range(J):
+        assert 0.0 < ir[j] < 1.0 and 0.0 < rho[j] < np.inf
+        assert est[j] <= prev * ir[j] * (1 + 1e-10) + 1e-15, (j, est[j], prev, ir[j])
+        prev = ffom[j]
+    for j in range(min(J, ref.outer_iters) - 1):
+        assert abs(ir[j] - ref.rhat_hist[j]) <= 1e-6 * ref.rhat_hist[j], (j, ir[j], ref.rhat_hist[j])
+        assert abs(rho[j] - ref.rho_hist[j]) <= 1e-6 * ref.rho_hist[j], (j, rho[j], ref.rho_hist[j])
