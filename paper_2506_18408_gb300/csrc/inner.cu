@@ -282,9 +282,10 @@ __global__ void k_cycle_reset(const Plan P, int j, int c3_on, double cond_thr) {
     cyc->dmin = INFINITY;
     cyc->rho = INFINITY;
     cyc->cond_thr = cond_thr;
-    if (p == 0 && P.gsync) {  // the fused step's grid counter and its give-up flag
+    if (p == 0 && P.gsync) {  // the fused step's grid counters (0: phase-1 partials, 2: sketch partials), give-up flag
         P.gsync[0] = 0;
         P.gsync[1] = 0;
+        P.gsync[2] = 0;
     }
     if (j >= 0) {
         const OuterState* ost = P.ost + p;

@@ -202,14 +202,13 @@ __device__ __forceinline__ int dots_pass(int N, int v0, int len, const VT* __res
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// Shared memory: the block of w' (Bn + 1 slots of AT, slot Bn = 0 for the list padding).  FP64: the block is
-// converted in place to its 64-bit fixed-point image before the sketch sums.
-// At most 56 registers per thread (registers are allocated in units of 8 per thread): two 512-thread CTAs per SM
-// then leave room for the sketched-QR cluster's CTAs to run beside them instead of displacing them.
-// Returns false (every thread of the CTA alike) when the block's problem has no step i to take.
+// Phase 1 of an inner step for the CTA's row block: w' = A u_i (stored to W and kept in the shared block), the
+// block partials of ||u_i||^2 and of the window dots (normpart, hpart), and Eb, the block's largest exponent of w'
+// (the reference exponent of the FP64 fixed-point sketch sums).  Returns false (every thread of the CTA alike) when
+// the block's problem has no step i to take.
 template <int V, int U, int NW, typename MT, typename VT, typename AT>
-__device__ __forceinline__ bool inner_spmv_block(const Plan& P, int i, const MT* __restrict__ val,
-                                                 AT* __restrict__ wblk) {
+__device__ __forceinline__ bool inner_spmv_part(const Plan& P, int i, const MT* __restrict__ val,
+                                                AT* __restrict__ wblk, int& Eb) {
     __shared__ AT red[512];
     __shared__ int stop_sh, emax_sh[16];
     const int b = blockIdx.x;
@@ -218,7 +217,7 @@ __device__ __forceinline__ bool inner_spmv_block(const Plan& P, int i, const MT*
     __syncthreads();
     if (stop_sh) return false;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int s = P.s, Bn = P.Bn, N = P.N;
+    const int Bn = P.Bn, N = P.N;
     const VT* Ub = (const VT*)P.U;
     AT* W = (AT*)P.W;
     const int lo = i - NW + 1;  // window u_lo..u_i (NW = min(t, i+1))
@@ -263,35 +262,58 @@ __device__ __forceinline__ bool inner_spmv_block(const Plan& P, int i, const MT*
             else ((AT*)P.hpart)[(int64_t)b * kMaxTrunc + threadIdx.x - 1] = t;
         }
     }
-    const int* sg = P.seg + (int64_t)bi.list * s;
-    AT* cpart = (AT*)P.cpart;
+    Eb = 1;
+    for (int q = 0; q < nw; ++q) Eb = max(Eb, emax_sh[q]);
+    return true;
+}
+
+// Prepares the shared block of w' for the sketch gathers: FP64, converted in place to its 64-bit fixed-point image
+// relative to 2^Eb (exact integer sums, independent of order; the FP64 pipe stays with the SpMV), with the zero slot
+// at Bn; FP32, as it is.  Ends with a block barrier.
+template <typename AT>
+__device__ __forceinline__ void sketch_prepare(const Plan& P, int len, AT* __restrict__ wblk, int Eb) {
     if constexpr (sizeof(AT) == 8) {
-        // exact fixed-point sketch sums (integer adds; the FP64 pipe stays with the SpMV)
-        int Eb = 1;
-        for (int q = 0; q < nw; ++q) Eb = max(Eb, emax_sh[q]);
         const int H = P.sk_headroom;
         long long* qblk = reinterpret_cast<long long*>(wblk);
-        for (int r = threadIdx.x; r <= Bn; r += blockDim.x)
-            qblk[r] = (r < bi.len) ? to_fixed((double)wblk[r], Eb, H) : 0;
-        __syncthreads();
-        const double unit = fixed_unit(0.0, Eb, H);
+        for (int r = threadIdx.x; r <= P.Bn; r += blockDim.x) qblk[r] = (r < len) ? to_fixed((double)wblk[r], Eb, H) : 0;
+    }
+    __syncthreads();
+}
+
+// Per-block sketch partials of w' for sketch rows r0, r0 + rstep, ... < s: cpart[b*s + r] = sum over the block's list
+// for row r (in list order) of +-w'.  FP64: from the fixed-point image, converted to FP64 once per row.
+template <typename AT>
+__device__ __forceinline__ void sketch_rows(const Plan& P, int b, int list, const AT* __restrict__ wblk, int Eb, int r0,
+                                            int rstep) {
+    const int s = P.s;
+    const int* sg = P.seg + (int64_t)list * s;
+    AT* cpart = (AT*)P.cpart;
+    if constexpr (sizeof(AT) == 8) {
+        const long long* qblk = reinterpret_cast<const long long*>(wblk);
+        const double unit = fixed_unit(0.0, Eb, P.sk_headroom);
         const bool bad = exp_nonfinite(0.0, Eb);
-        for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
+        for (int rr = r0; rr < s; rr += rstep) {
             const long long v = sum_list(P.ent, sg[rr], sg[rr + 1], qblk);
             cpart[(int64_t)b * s + rr] = bad ? (AT)NAN : (AT)((double)v * unit);
         }
     } else {
-        __syncthreads();
-        for (int rr = threadIdx.x; rr < s; rr += blockDim.x)
-            cpart[(int64_t)b * s + rr] = sum_list(P.ent, sg[rr], sg[rr + 1], wblk);
+        for (int rr = r0; rr < s; rr += rstep) cpart[(int64_t)b * s + rr] = sum_list(P.ent, sg[rr], sg[rr + 1], wblk);
     }
-    return true;
 }
 
+// The inner SpMV kernel of the two-launch step: phase 1, then the block's sketch partials for every sketch row.
+// Shared memory: the block of w' (Bn + 1 slots of AT, slot Bn = 0 for the list padding).
+// At most 56 registers per thread (registers are allocated in units of 8 per thread): two 512-thread CTAs per SM
+// then leave room for the sketched-QR cluster's CTAs to run beside them instead of displacing them.
 template <int V, int U, int NW, typename MT, typename VT, typename AT>
 __global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __restrict__ val) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    inner_spmv_block<V, U, NW, MT, VT, AT>(P, i, val, reinterpret_cast<AT*>(smem_raw));
+    AT* wblk = reinterpret_cast<AT*>(smem_raw);
+    int Eb = 1;
+    if (!inner_spmv_part<V, U, NW, MT, VT, AT>(P, i, val, wblk, Eb)) return;
+    const int b = blockIdx.x;
+    sketch_prepare(P, P.blk_len[b], wblk, Eb);
+    sketch_rows(P, b, P.blk_list[b], wblk, Eb, threadIdx.x, blockDim.x);
 }
 
 // ---------------------------------------------------------------------------------------------------------------
@@ -529,24 +551,19 @@ __device__ __forceinline__ AT block_partials_sum(const AT* __restrict__ x, int64
     return warp_sum(a);
 }
 
-// Truncated-Arnoldi update (NW = window size).  Each thread first loads its first PF rows of w' and of the window
-// vectors (they do not depend on the scalars); meanwhile warp 0 sums the problem's ||u_i||^2 partials and warps
-// 1..NW its window-dot partials, each with all loads in flight at once.  After one barrier thread 0 forms sigma_i
-// and the coefficients; after a second, the sketched column S A b_i (one warp per sketch row, rows spread over all
-// of the problem's blocks) and the row update.
+// Truncated-Arnoldi update kernel of the two-launch step (NW = window size).  Each thread first loads its first PF
+// rows of w' and of the window vectors (they do not depend on the scalars); meanwhile warp 0 sums the problem's
+// ||u_i||^2 partials and warps 1..NW its window-dot partials, each with all loads in flight at once.  After one
+// barrier thread 0 forms sigma_i and the coefficients; after a second, the sketched column S A b_i (one warp per
+// sketch row, rows spread over all of the problem's blocks) and the row update.
 // Three 512-thread CTAs per SM (at most 42 registers; batches run many waves of blocks) for windows up to 3, two
 // for wider windows, which would spill within 42.
-// wsm: the block of w' in shared memory (the fused step, FP32/BF16), else null (w' read from W).  FUSED: the block's
-// partials of this step come from other CTAs of the same launch; thread 0 waits for all of them (target arrivals
-// at the step's grid counter) after the prefetch.
-template <int NW, typename VT, typename AT, bool FUSED>
-__device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last, const AT* __restrict__ wsm,
-                                                 unsigned long long target) {
+template <int NW, typename VT, typename AT>
+__device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last) {
     // rows per thread loaded before the scalars (PF) and per round of the row loop (UR; all loads of a round are
-    // issued before its stores): the fused step has the whole 56-register budget here, the update kernel 42
-    constexpr bool WIDE = (sizeof(AT) == 8 && NW >= 3);
-    constexpr int PF = FUSED ? (WIDE ? 2 : 4) : ((sizeof(AT) == 8 && NW >= 5) ? 1 : 2);
-    constexpr int UR = FUSED ? (WIDE ? 2 : 4) : ((sizeof(AT) == 8 && NW >= 4) ? 1 : 2);
+    // issued before its stores)
+    constexpr int PF = (sizeof(AT) == 8 && NW >= 5) ? 1 : 2;
+    constexpr int UR = (sizeof(AT) == 8 && NW >= 4) ? 1 : 2;
     __shared__ AT coef_sh[kMaxTrunc];
     __shared__ AT part_sh[kMaxTrunc + 1];
     __shared__ double sig_sh;
@@ -574,14 +591,10 @@ __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last,
         for (int u = 0; u < PF; ++u) {
             const int k = threadIdx.x + u * (int)blockDim.x;
             const int r = bi.v0 + k;
-            wv[u] = (k < bi.len) ? (wsm ? wsm[k] : wrd(r)) : AT(0);
+            wv[u] = (k < bi.len) ? wrd(r) : AT(0);
 #pragma unroll
             for (int q = 0; q < NW; ++q) uv[u][q] = (k < bi.len) ? win(q, r) : AT(0);
         }
-    }
-    if constexpr (FUSED) {
-        if (threadIdx.x == 0) grid_wait(P.gsync, target, P.gsync + 1);
-        __syncthreads();
     }
     if (threadIdx.x == 0) stop_sh = cycle_idle(P, p, i) ? 1 : 0;
     const int b0 = P.prob_b0[p], b1 = P.prob_b0[p + 1];
@@ -671,7 +684,7 @@ __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last,
             const int k = k0 + u * (int)blockDim.x;
             const bool ok = k < bi.len;
             const int r = bi.v0 + k;
-            wr[u] = ok ? (wsm ? wsm[k] : wrd(r)) : AT(0);
+            wr[u] = ok ? wrd(r) : AT(0);
 #pragma unroll
             for (int q = 0; q < NW; ++q) uq[u][q] = ok ? win(q, r) : AT(0);
         }
@@ -685,31 +698,235 @@ __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last,
 
 template <int NW, typename VT, typename AT>
 __global__ void __launch_bounds__(512, (NW <= 3) ? 3 : 2) k_inner_axpy(const Plan P, int i, int last) {
-    inner_axpy_block<NW, VT, AT, false>(P, i, last, nullptr, 0);
+    inner_axpy_block<NW, VT, AT>(P, i, last);
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// One inner step in one launch, for plans whose row blocks all fit on the GPU at once (one wave): the fused SpMV +
-// dots + sketch partials, then a grid-wide arrival (every CTA, also one with no step to take), then, once all of the
-// launch's partials are written, the truncated-Arnoldi update of the CTA's own rows.  Every CTA of the launch is
-// resident at the same time (the host launches it only when the occupancy allows all blocks at once, beside the
-// sketched-QR cluster), so the wait ends; it gives up after a bounded number of polls and raises the plan's sync
-// flag, which the outer step turns into an error.  The arithmetic and its order are those of the two kernels.
+// Named barrier among the first `threads` threads of the CTA (barrier 0 is __syncthreads).
+__device__ __forceinline__ void bar_sync_named(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Bounded wait of one lane for a shared-memory flag set by another warp of the CTA; false if it gave up.
+constexpr int kFlagPolls = 1 << 26;  // several seconds: well beyond the grid wait's own bound (the flag is set once that wait ends)
+__device__ __forceinline__ bool wait_flag(const int* flag) {
+    for (int it = 0; it < kFlagPolls; ++it) {
+        if (*(const volatile int*)flag) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+// Phase 2 of the fused step (after the CTA's grid-wide arrival), with the warps split by role so that the sketch
+// gathers (shared memory and integer adds) run beside the row update (HBM):
+//  * warps 0..NW: thread 0 waits for every CTA's phase-1 partials (grid counter 0); warp 0 sums the problem's
+//    ||u_i||^2 partials and warps 1..NW its window-dot partials; thread 0 forms sigma_i and the coefficients and
+//    publishes them through a shared-memory flag;
+//  * the other warps: the block's sketch partials (every sketch row), then one arrival per CTA on grid counter 2;
+//  * then every warp claims chunks of 32 UR rows of the block and updates them (the chunk's loads are issued before
+//    the first wait for the coefficients);
+//  * last, the warps that own a row of the sketched column S A b_i (rows spread over all blocks) wait for every CTA's
+//    sketch partials (grid counter 2) and sum them.
+// The arithmetic of every value and its order are those of the two-launch step.
+template <int NW, typename VT, typename AT>
+__device__ __forceinline__ void fused_phase2(const Plan& P, int i, int last, AT* __restrict__ wblk, int Eb,
+                                             const unsigned long long* target_ptr) {
+    constexpr int NSW = NW + 1;  // warps of the scalar role
+    constexpr bool WIDE = (sizeof(AT) == 8 && NW >= 3);
+    constexpr int UR = WIDE ? 2 : 4;  // rows per lane of an update chunk
+    __shared__ AT coef_sh[kMaxTrunc];
+    __shared__ AT part_sh[kMaxTrunc + 1];
+    __shared__ double sig_sh;
+    __shared__ int stop_sh, ready_sh, chunk_sh, skdone_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int b = blockIdx.x;
+    const BlockInfo bi = block_info(P, b);
+    const int p = bi.prob;
+    if (threadIdx.x == 0) {
+        stop_sh = 0;
+        ready_sh = 0;
+        chunk_sh = 0;
+        skdone_sh = 0;
+    }
+    sketch_prepare(P, bi.len, wblk, Eb);  // ends with a block barrier: the flags above and *target_ptr are visible
+    const unsigned long long target = *target_ptr;
+    const int N = P.N, s = P.s, m = P.m;
+    const int b0 = P.prob_b0[p], b1 = P.prob_b0[p + 1];
+    const int lo = i - NW + 1;
+    if (warp < NSW) {
+        if (threadIdx.x == 0) grid_wait(P.gsync, target, P.gsync + 1);
+        bar_sync_named(1, NSW * 32);
+        if (warp == 0 && i > 0) {
+            const AT a = block_partials_sum((const AT*)P.normpart, 1, b0, b1, lane);
+            if (lane == 0) part_sh[0] = a;
+        } else if (warp >= 1) {
+            const AT a = block_partials_sum((const AT*)P.hpart + (warp - 1), kMaxTrunc, b0, b1, lane);
+            if (lane == 0) part_sh[warp] = a;
+        }
+        bar_sync_named(1, NSW * 32);
+        if (threadIdx.x == 0) {
+            const bool lead = (b == b0);  // the problem's first block writes its scalars
+            double* sigma = P.sigma + (int64_t)p * (m + 1);
+            int stop = cycle_idle(P, p, i) ? 1 : 0;
+            double sig = 1.0;
+            if (!stop) {
+                // sigma_i = 1/||u_i||
+                bool bad = false;
+                int why = 4;
+                if (i == 0) {
+                    sig = sigma[0];
+                } else {
+                    const double a2 = (double)part_sh[0];
+                    bad = !(a2 > 0.0) || !isfinite(a2);
+                    why = (a2 == 0.0) ? 4 : 6;
+                    sig = 1.0 / sqrt(a2);
+                }
+                if (bad) {
+                    stop = 1;
+                    if (lead) {
+                        CycleState* cyc = P.cyc + p;
+                        cyc->brk_reason = why;
+                        atomicMin(&cyc->brk_step, i);
+                    }
+                } else {
+                    if (lead) sigma[i] = sig;
+                    // h_l = sigma_l sigma_i (u_l^T w'); the stored update uses sigma_l^2 (u_l^T w')
+#pragma unroll
+                    for (int q = 0; q < NW; ++q) {
+                        const int l = lo + q;
+                        const double a = (double)part_sh[1 + q];
+                        const double sl = (l == i) ? sig : sigma[l];
+                        coef_sh[q] = (AT)(sl * sl * a);
+                        if (lead) P.hco[((int64_t)p * m + i) * kMaxTrunc + q] = sl * sig * a;
+                    }
+                }
+            }
+            sig_sh = sig;
+            stop_sh = stop;
+            __threadfence_block();
+            *(volatile int*)&ready_sh = 1;
+        }
+    } else {
+        sketch_rows(P, b, bi.list, wblk, Eb, threadIdx.x - NSW * 32, (int)blockDim.x - NSW * 32);
+        __threadfence();  // this warp's partials are visible device-wide before the CTA's arrival on counter 2
+        __syncwarp();
+        if (lane == 0 && atomicAdd(&skdone_sh, 1) == nw - NSW - 1) {
+            __threadfence();
+            atomicAdd(P.gsync + 2, 1ull);
+        }
+    }
+    // the scalars, once per warp
+    bool stop = false;
+    double sig_i = 1.0;
+    AT cf[NW > 0 ? NW : 1];
+    auto get_scalars = [&]() {
+        bool ok = true;
+        if (lane == 0) {
+            ok = wait_flag(&ready_sh);
+            if (!ok) atomicOr(P.gsync + 1, 1ull);  // the solve reports the give-up; this warp writes nothing
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        __threadfence_block();
+        stop = !ok || stop_sh;
+        sig_i = sig_sh;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) cf[q] = coef_sh[q];
+    };
+    bool have = false;
+    if (!last) {
+        // u_{i+1} = 2^p2 (w' - sum_q coef_q u_{lo+q}), 2^p2 the power of two just below sigma_i
+        VT* Ub = (VT*)P.U;
+        const AT* W = (const AT*)P.W;
+        VT* un = Ub + (int64_t)(i + 1) * N;
+        const unsigned long long keep = l2_keep_policy();
+        // last reads of w' and of the oldest window vector (the next step's window starts one later): L2 may drop
+        // them (FP64 and FP32 bases; a BF16 basis keeps plain loads)
+        constexpr bool DROP = sizeof(VT) >= 4;
+        const unsigned long long drop = l2_drop_policy();
+        int p2 = 0;
+        AT sc2 = AT(1);
+        for (;;) {
+            int c = 0;
+            if (lane == 0) c = atomicAdd(&chunk_sh, 1);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            const int k0 = c * 32 * UR;
+            if (k0 >= bi.len) break;
+            AT wr[UR], uq[UR][NW > 0 ? NW : 1];
+#pragma unroll
+            for (int u = 0; u < UR; ++u) {
+                const int k = k0 + 32 * u + lane;
+                const bool ok = k < bi.len;
+                const int r = bi.v0 + k;
+                if constexpr (sizeof(AT) == 8) wr[u] = ok ? (DROP ? ld_keep(W + r, drop) : W[r]) : AT(0);
+                else wr[u] = ok ? wblk[k] : AT(0);  // FP32: w' is still the shared block
+#pragma unroll
+                for (int q = 0; q < NW; ++q) {
+                    const VT* ap = Ub + (int64_t)(lo + q) * N + r;
+                    uq[u][q] = ok ? ((DROP && q == 0 && NW > 1) ? ld_keep(ap, drop) : ld_plain(ap)) : AT(0);
+                }
+            }
+            if (!have) {
+                get_scalars();
+                have = true;
+                if (stop) break;
+                frexp(sig_i, &p2);  // sigma_i = f * 2^p2, f in [0.5, 1)
+                p2 -= 1;
+                sc2 = (AT)ldexp(1.0, p2);
+            }
+#pragma unroll
+            for (int u = 0; u < UR; ++u) {
+                const int k = k0 + 32 * u + lane;
+                if (k < bi.len) {
+                    AT v = wr[u];
+#pragma unroll
+                    for (int q = 0; q < NW; ++q) v -= cf[q] * uq[u][q];
+                    if constexpr (sizeof(AT) == 8) v = mul_pow2((double)v, p2);
+                    else v = v * sc2;
+                    st_keep(un + bi.v0 + k, v, keep);  // the next step gathers it and reads it as a window row
+                }
+            }
+        }
+    }
+    if (!have) get_scalars();
+    if (stop) return;
+    // sketched column S A b_i = sigma_i S w': sketch row rr to warp rr / nb of the problem's block rr % nb, once every
+    // CTA's sketch partials are in place
+    const double csc = P.sk_scale * sig_i;
+    const int nb = b1 - b0;
+    bool waited = false;
+    for (int rr = warp * nb + (b - b0); rr < s; rr += nw * nb) {
+        if (!waited) {
+            if (lane == 0) grid_wait(P.gsync + 2, target, P.gsync + 1);
+            __syncwarp();
+            waited = true;
+        }
+        const AT a = block_partials_sum((const AT*)P.cpart + rr, s, b0, b1, lane);
+        if (lane == 0) P.C[((int64_t)p * m + i) * s + rr] = csc * (double)a;
+    }
+}
+
+// One inner step in one launch, for plans whose row blocks all fit on the GPU at once (one wave): phase 1 (SpMV,
+// window dots, ||u_i||^2), a grid-wide arrival of every CTA (also one with no step to take) on grid counter 0, then
+// phase 2 (fused_phase2: the sketch partials beside the truncated-Arnoldi update, and the sketched column after a
+// second grid-wide arrival, on counter 2).  Every CTA of the launch is resident at the same time (the host launches
+// it only when the occupancy allows all blocks at once, beside the sketched-QR cluster), so the waits end; each
+// gives up after a bounded number of polls and raises the plan's sync flag, which the outer step turns into an error.
 template <int V, int U, int NW, typename MT, typename VT, typename AT>
 __global__ void __maxnreg__(56) k_inner_step(const Plan P, int i, const MT* __restrict__ val, int last) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AT* wblk = reinterpret_cast<AT*>(smem_raw);
     __shared__ unsigned long long target_sh;
-    const bool active = inner_spmv_block<V, U, NW, MT, VT, AT>(P, i, val, wblk);
+    int Eb = 1;
+    const bool active = inner_spmv_part<V, U, NW, MT, VT, AT>(P, i, val, wblk, Eb);
     __threadfence();  // this thread's partials are visible device-wide before the CTA arrives
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned long long old = atomicAdd(P.gsync, 1ull);
         target_sh = (old / gridDim.x + 1) * (unsigned long long)gridDim.x + (unsigned long long)P.gwait_extra;
+        if (!active) atomicAdd(P.gsync + 2, 1ull);  // no sketch partials from this CTA either
     }
     if (!active) return;
-    // FP64: the shared block now holds the fixed-point image of w', so w' is read back from W
-    inner_axpy_block<NW, VT, AT, true>(P, i, last, sizeof(AT) == 8 ? nullptr : wblk, target_sh);
+    fused_phase2<NW, VT, AT>(P, i, last, wblk, Eb, &target_sh);
 }
 
 template <int V, int U, int NW, typename MT, typename VT, typename AT>
