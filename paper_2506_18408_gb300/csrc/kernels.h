@@ -79,7 +79,8 @@ struct Plan {
     void* hpart = nullptr;     // AT[nblk * kMaxTrunc]
     void* cpart = nullptr;     // AT[nblk * s]
     double* C = nullptr;       // [P][m][s]  S A b_i
-    double* Q = nullptr;       // [P][m][s]
+    double* Q = nullptr;       // [P][m][s]  column-major: Q[l*s + r]
+    double* Qt = nullptr;      // [P][s][m]  the same, row-major: Qt[r*m + l]
     double* R = nullptr;       // [P][m][m]  column-major, R[i*m + l] = R_{l,i}
     double* d = nullptr;       // [P][m]
     double* e = nullptr;       // [P][s]     running sketched residual
@@ -89,7 +90,7 @@ struct Plan {
     double* coef = nullptr;    // [P][m]     y_l * sigma_l
     double* hco = nullptr;     // [P][m][kMaxTrunc] truncated-Arnoldi coefficients
     CycleState* cyc = nullptr; // [P]
-    int qr_cluster = 8;        // CTAs per problem in the sketched-QR kernel
+    int qr_cluster = 8;        // CTAs per problem in the sketched-QR kernel (1 for small s m)
 
     // outer FGMRES
     int jmax = 0;

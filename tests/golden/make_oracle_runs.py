@@ -24,6 +24,7 @@ OUT = os.path.join(HERE, "oracle_runs.json")
 
 # (workload config, inner precision of the sGMRES cycles)
 RUNS = {
+    "cd3d_128_fp64": ("cd3d_128", "fp64"),
     "cd3d_128_fp32": ("cd3d_128", "fp32"),
     "cd3d_128_bf16": ("cd3d_128", "bf16"),
     "zipf_2m_fp64": ("zipf_2m", "fp64"),
