@@ -285,6 +285,28 @@ SFGMRES_API int sfgmres_solve_restarted(sfgmres_t h, const double* b, const doub
                                         int32_t k, double tol, int32_t max_cycles, double* res_hist,
                                         int32_t* cycles_out);
 
+/* Multi-level FGMRES (the outlook of Section 5): FGMRES on A x = b whose preconditioner at step j is itself an FGMRES
+ * run on A z = v_j (zero initial guess) of at most level_steps[0] outer steps, preconditioned in turn by an FGMRES run
+ * of at most level_steps[1] steps, and so on for nlower levels; the lowest level is preconditioned by sGMRES cycles as
+ * in sfgmres_solve.  Each level keeps its basis small, so the orthogonalisation cost O(n J^2) of one long outer
+ * basis is spread over short ones, without restarting any level.  A lower level stops at its budget or once the
+ * bound of Eq. 5 predicts that its parent meets the parent's target: with rule C3 on (SFGMRES_OPT_C3) the
+ * preconditioner of step j is asked for the relative tolerance tol_parent / ||r~_{j-1}|| (the parent's target over its
+ * FFOM residual of Eq. 4, beta before the first step: the test rule C3 applies to an sGMRES cycle); with C3 off every
+ * lower level runs its whole budget.  A lower level always takes at least one step, stops on its Givens estimate and
+ * returns its last iterate.  The top level's budget is SFGMRES_OPT_MAX_OUTER and it stops as sfgmres_solve does.
+ *   b, x0, x, m, s, k, tol   as for sfgmres_solve (single-system handles)
+ *   nlower           number of FGMRES levels below the top, 1..4
+ *   level_steps      host int32[nlower]: outer-step budget of each lower level, top-most first, each in [1, 1024]
+ *   st               optional statistics of the top level; inner_k[j] is the number of steps the level below took
+ *                    for step j, inner_reason[j] 3 (it met its tolerance) or 1 (budget), inner_rho[j] its last
+ *                    estimate, inner_res[j] the true ||v_j - A z_j||; total_inner counts the sGMRES steps of all
+ *                    lowest-level cycles; the kernel timing fields stay 0
+ * Returns a status code as sfgmres_solve does. */
+SFGMRES_API int sfgmres_solve_multilevel(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m,
+                                         int32_t s, int32_t k, double tol, int32_t nlower,
+                                         const int32_t* level_steps, sfgmres_stats* st);
+
 /* c = S v for the handle's embedding with s rows (Eq. 1).  v: device float64[n], c: device float64[s].
  * Single-system handles only. */
 SFGMRES_API int sfgmres_sketch_apply(sfgmres_t h, int32_t s, const double* v, double* c);

@@ -20,7 +20,7 @@ lasts.  ``h_{j+1,j} = 0`` means the iterate is exact (happy breakdown).  The out
 from __future__ import annotations
 
 import dataclasses
-from typing import Callable, List, Optional
+from typing import Callable, List, Optional, Sequence
 
 import numpy as np
 from scipy.sparse.linalg import LinearOperator
@@ -63,7 +63,8 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
            cond_thr: float = 1e15, c3: bool = True, outer_orth: str = "mgs", variant: str = "fgmres",
            inner: str = "fp64", precond: Optional[Callable[[np.ndarray], np.ndarray]] = None,
            record: bool = False, track_true: bool = False,
-           right_precond: Optional[Callable[[np.ndarray], np.ndarray]] = None, trace: bool = False) -> FGMRESResult:
+           right_precond: Optional[Callable[[np.ndarray], np.ndarray]] = None, trace: bool = False,
+           level_steps: Sequence[int] = (), _child: bool = False) -> FGMRESResult:
     """Solve ``A x = b`` by FGMRES (or FFOM) preconditioned with sGMRES cycles (Algorithm 1 + Section 3).
 
     ``A``: scipy sparse (FP64).  ``m``: inner basis size (C1, the paper's ``k_max``); ``t``: Arnoldi truncation;
@@ -74,6 +75,15 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
     ``trace`` records, per outer step, the true inner residual ``||v_j - A z_j||`` and the sketched residual the
     cycle ended with (the two sides of the Eq. 5 bound and its estimate) without keeping the bases that ``record``
     keeps.
+
+    ``level_steps`` = (J_1, J_2, ...) makes this the top of a multi-level FGMRES (Section 5): the preconditioner of
+    step j is an FGMRES run of at most J_1 outer steps on ``A z = v_j`` (zero initial guess), whose own preconditioner
+    is an FGMRES run of at most J_2 steps, and so on; the lowest level uses the sGMRES cycle.  A lower level stops
+    early once the bound of Eq. 5 predicts that its parent meets the parent's target: with rule C3 on, the child of
+    step j solves to the relative tolerance tol ||b|| / ||r~_{j-1}|| (||r~_{-1}|| = beta), the same test C3 applies to
+    an sGMRES cycle; with C3 off it runs its full budget.  A lower level always takes at least one step, stops on its
+    Givens estimate and returns its last iterate.  For the parent, ``inner_k`` then counts the child's outer steps
+    and ``inner_reason`` is 3 (the child met its tolerance) or 1 (budget).
     """
     n = b.shape[0]
     b = np.asarray(b, dtype=np.float64)
@@ -83,7 +93,7 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
         return FGMRESResult(np.zeros(n), CONVERGED, 0, 0.0, [], [], [], [])
     r0 = b - A @ x0
     beta = float(np.linalg.norm(r0))
-    if beta <= tol * nb:
+    if beta <= tol * nb and not _child:
         return FGMRESResult(x0.copy(), CONVERGED, 0, beta / nb, [], [], [], [], beta=beta)
 
     S = None
@@ -115,7 +125,21 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
     j_done = 0
     for j in range(max_outer):
         v = V[:, j]
-        if precond is None:
+        if level_steps:
+            # preconditioner: an FGMRES run one level down (Section 5), to the tolerance the Eq. 5 bound asks for
+            tau = tol * nb / ffom_prev if (c3 and np.isfinite(ffom_prev) and ffom_prev > 0.0) else 0.0
+            child = fgmres(A, v, None, m=m, s=s, t=t, tol=tau, max_outer=level_steps[0], sketch_seed=sketch_seed,
+                           zeta=zeta, sketch_kind=sketch_kind, cond_thr=cond_thr, c3=c3, outer_orth=outer_orth,
+                           inner=inner, level_steps=level_steps[1:], _child=True)
+            z = child.x
+            ks.append(child.outer_iters)
+            reasons.append(3 if child.status == CONVERGED else 1)
+            if rho_hist is not None:
+                rho_hist.append(child.est_hist[-1] if child.est_hist else float("inf"))
+            if child.outer_iters == 0:  # the child's first cycle accepted no column: no correction
+                status = BREAKDOWN
+                break
+        elif precond is None:
             scale = ffom_prev if (c3 and np.isfinite(ffom_prev)) else None
             cyc = sgmres_cycle(A if right_precond is None else A_in, v, S, m, t, cond_thr, bound_scale=scale,
                                bound_tol=tol * nb, inner=inner, A_inner=A_in, S_inner=S_in, record=record)
@@ -175,6 +199,14 @@ def fgmres(A, b: np.ndarray, x0: Optional[np.ndarray] = None, *, m: int, s: int,
         est_hist.append(est / nb)
         ffom_hist.append(ffom / nb)
         j_done = j + 1
+        if _child:
+            # a lower level of a multi-level FGMRES: its estimate decides, and its last iterate is returned
+            x = x0 + Z[:, : j + 1] @ y
+            if est <= tol * nb or breakdown:
+                status = CONVERGED
+                break
+            ffom_prev = ffom
+            continue
         need_x = track_true or est <= tol * nb or breakdown or j + 1 == max_outer
         if need_x:
             x = x0 + Z[:, : j + 1] @ y

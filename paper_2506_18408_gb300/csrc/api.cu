@@ -132,6 +132,12 @@ struct sfgmres_ctx {
         k_hist, reason_hist,
         ost;
     DevBuf bst, xst, x0st;  // staging / internal copies
+    // outer workspaces of the lower levels of sfgmres_solve_multilevel (level 1, 2, ...)
+    struct LevelWs {
+        DevBuf Vb, Z, nu, Wo, opart, npart, npart2, h1, h2, H, cs, sn, g, yo, est_hist, ffom_hist, ires_hist,
+            rho_hist, k_hist, reason_hist, ost, pflag, rhs;
+    };
+    std::vector<LevelWs> lvl;
     DevBuf gsync;           // fused inner step: grid arrival counters [0], [2] and give-up flag [1] (u64)
 
     // pinned host mirrors of the per-problem device state
@@ -345,6 +351,23 @@ __global__ void k_axpy_scalar(int64_t n, double a, const double* __restrict__ z,
 }
 
 // x = 0 over the rows of the problems whose flag has bit 2 set (right-hand side zero).
+// b = scale[0] * v (the right-hand side of a lower level of the multi-level FGMRES: the parent's outer vector v_j,
+// stored unnormalised with its scale nu_j on the device)
+__global__ void k_scale_copy(int64_t n, const double* __restrict__ v, const double* __restrict__ scale,
+                             double* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = scale[0] * v[i];
+}
+
+// The cycle-state fields the outer Givens kernel records, set from a completed lower-level FGMRES run (the multi-level
+// FGMRES's preconditioner): its outer steps, why it stopped (3 met its tolerance, 1 budget), its last estimate.
+__global__ void k_set_cycle(CycleState* cyc, int k, int reason, double rho) {
+    cyc->k = k;
+    cyc->reason = reason;
+    cyc->rho = rho;
+    cyc->stopped = 1;
+}
+
 __global__ void k_zero_flagged(const Plan P, double* __restrict__ x) {
     const BlockInfo bi = block_info(P, blockIdx.x);
     if (!(P.pflag[bi.prob] & 4)) return;
@@ -1419,6 +1442,11 @@ int sfgmres_destroy(sfgmres_t h) {
                       &h->est_hist, &h->ffom_hist, &h->ires_hist, &h->rho_hist, &h->k_hist, &h->reason_hist, &h->ost, &h->bst, &h->xst,
                       &h->x0st, &h->gsync};
     for (DevBuf* b : bufs) release(*b);
+    for (auto& L : h->lvl)
+        for (DevBuf* b : {&L.Vb, &L.Z, &L.nu, &L.Wo, &L.opart, &L.npart, &L.npart2, &L.h1, &L.h2, &L.H, &L.cs, &L.sn,
+                          &L.g, &L.yo, &L.est_hist, &L.ffom_hist, &L.ires_hist, &L.rho_hist, &L.k_hist,
+                          &L.reason_hist, &L.ost, &L.pflag, &L.rhs})
+            release(*b);
     for (Geo& g : h->geos) {
         release(g.tab);
         release(g.grp);
@@ -1834,6 +1862,304 @@ int sfgmres_solve_restarted(sfgmres_t h, const double* b, const double* x0, doub
     CK(cudaGetLastError());
     if (cycles_out) *cycles_out = c;
     if (status == SFGMRES_ERR_NAN) return fail(h, SFGMRES_ERR_NAN, msg);
+    return status;
+}
+
+}  // extern "C"
+
+// ---- multi-level FGMRES (Section 5) ----
+namespace {
+constexpr int kMaxLowerLevels = 4;
+
+// Write one int of device memory on the handle's stream (a level's per-problem flag word).
+int set_flag(sfgmres_ctx* h, const int* flag, int v) {
+    CK(cudaMemcpyAsync((void*)flag, &v, sizeof(int), cudaMemcpyHostToDevice, h->st));
+    return 0;
+}
+
+// The plan of lower level L (1-based) for a basis of at most J steps: the top plan P0 with every outer FGMRES pointer
+// replaced by level L's own workspace and flag word.  The inner-cycle workspaces, sketch lists and row blocks are
+// shared: the levels run strictly nested, one at a time.
+int level_plan(sfgmres_ctx* h, const Plan& P0, int L, int J, Plan* out) {
+    if ((int)h->lvl.size() < L) h->lvl.resize(L);
+    auto& W = h->lvl[L - 1];
+    const size_t N = (size_t)P0.N, nb = (size_t)P0.nblk, Jz = (size_t)J;
+    int rc;
+    const std::pair<DevBuf*, size_t> need[] = {
+        {&W.Vb, (Jz + 1) * N * 8}, {&W.Z, Jz * N * 8},       {&W.nu, (Jz + 1) * 8},     {&W.Wo, N * 8},
+        {&W.opart, nb * (Jz + 1) * 8}, {&W.npart, nb * 8}, {&W.npart2, nb * 8},     {&W.h1, (Jz + 1) * 8},
+        {&W.h2, (Jz + 1) * 8},     {&W.H, (Jz + 1) * Jz * 8}, {&W.cs, Jz * 8},        {&W.sn, Jz * 8},
+        {&W.g, (Jz + 1) * 8},      {&W.yo, Jz * 8},           {&W.est_hist, Jz * 8},  {&W.ffom_hist, Jz * 8},
+        {&W.ires_hist, Jz * 8},    {&W.rho_hist, Jz * 8},     {&W.k_hist, Jz * 4},    {&W.reason_hist, Jz * 4},
+        {&W.ost, sizeof(OuterState)}, {&W.pflag, sizeof(int)}, {&W.rhs, N * 8}};
+    for (const auto& q : need)
+        if ((rc = ensure(h, *q.first, q.second))) return rc;
+    Plan P = P0;
+    P.jmax = J;
+    P.Vb = (double*)W.Vb.p;
+    P.Z = (double*)W.Z.p;
+    P.nu = (double*)W.nu.p;
+    P.Wo = (double*)W.Wo.p;
+    P.opart = (double*)W.opart.p;
+    P.npart = (double*)W.npart.p;
+    P.npart2 = (double*)W.npart2.p;
+    P.h1 = (double*)W.h1.p;
+    P.h2 = (double*)W.h2.p;
+    P.H = (double*)W.H.p;
+    P.cs = (double*)W.cs.p;
+    P.sn = (double*)W.sn.p;
+    P.g = (double*)W.g.p;
+    P.yo = (double*)W.yo.p;
+    P.est_hist = (double*)W.est_hist.p;
+    P.ffom_hist = (double*)W.ffom_hist.p;
+    P.ires_hist = (double*)W.ires_hist.p;
+    P.rho_hist = (double*)W.rho_hist.p;
+    P.k_hist = (int*)W.k_hist.p;
+    P.reason_hist = (int*)W.reason_hist.p;
+    P.ost = (OuterState*)W.ost.p;
+    P.pflag = (const int*)W.pflag.p;
+    if ((rc = set_flag(h, P.pflag, 0))) return rc;
+    *out = P;
+    return 0;
+}
+
+// Outcome of one run of a lower level.
+struct LevelRun {
+    int outer = 0;          // outer steps taken
+    int reason = 1;         // 3: met its tolerance, 1: used its budget
+    double est = INFINITY;  // last Givens estimate relative to the norm of its right-hand side
+    int64_t inner = 0;      // sGMRES steps of the lowest-level cycles under this run
+    int error = 0;          // SFGMRES_ERR_NAN or SFGMRES_ERR_CUDA
+};
+
+// Tolerance the Eq. 5 bound asks of the preconditioner of a level's next step: its target tol_abs over its FFOM
+// residual of the previous step (beta before the first), relative to the unit right-hand side v_j; 0 (the child's
+// whole budget) with rule C3 off or an undefined FFOM residual.
+double child_tolerance(const sfgmres_ctx* h, const OuterState& os, int j) {
+    const double fprev = (j == 0) ? os.beta : os.ffom;
+    return (h->c3 && std::isfinite(fprev) && fprev > 0.0) ? os.tol_abs / fprev : 0.0;
+}
+
+// Lower level L: FGMRES on A z = scale[0] v (zero initial guess) until its Givens estimate meets the relative
+// tolerance tau or it has taken its J steps (at least one step either way); its preconditioner is level L + 1, or an
+// sGMRES cycle at the lowest level.  The last iterate is written to out (zero if the first step had no correction).
+int run_level(sfgmres_ctx* h, const std::vector<Plan>& Ps, int L, const double* v, const double* scale, double tau,
+              double* out, LevelRun* res) {
+    const Plan& P = Ps[L];
+    const int N = P.N, J = P.jmax;
+    const bool lowest = (L + 1 == (int)Ps.size());
+    OuterState* host_ost = (OuterState*)h->h_ost.p;
+    double* rhs = (double*)h->lvl[L - 1].rhs.p;
+    k_scale_copy<<<grid_for(N), 256, 0, h->st>>>(N, v, scale, rhs);
+    ++g_launches;
+    launch_residual(P, rhs, nullptr, P.Vb, false);
+    launch_init_state(P, tau);
+    CK(cudaMemcpyAsync(host_ost, P.ost, sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    OuterState os = host_ost[0];
+    if (!std::isfinite(os.beta) || os.nan) {
+        res->error = SFGMRES_ERR_NAN;
+        return 0;
+    }
+    for (int j = 0; j < J; ++j) {
+        double* zj = P.Z + (int64_t)j * N;
+        if (lowest) {
+            int rc = run_cycle(h, P, j, P.Vb + (int64_t)j * N, P.nu + j, J + 1, h->c3, zj);
+            if (rc) return rc;
+        } else {
+            LevelRun cr;
+            int rc = run_level(h, Ps, L + 1, P.Vb + (int64_t)j * N, P.nu + j, child_tolerance(h, os, j), zj, &cr);
+            if (rc) return rc;
+            res->inner += cr.inner;
+            if (cr.error) {
+                res->error = cr.error;
+                return 0;
+            }
+            k_set_cycle<<<1, 1, 0, h->st>>>(P.cyc, cr.outer, cr.reason, cr.est);
+            ++g_launches;
+        }
+        launch_outer_step(P, j);
+        CK(cudaMemcpyAsync(host_ost, P.ost, sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        CK(cudaGetLastError());
+        os = host_ost[0];
+        if (os.nan) {
+            res->error = os.sync_fail ? SFGMRES_ERR_CUDA : SFGMRES_ERR_NAN;
+            return 0;
+        }
+        if (os.breakdown == 2) break;  // step j made no correction: the iterate of step j - 1 stands
+        res->outer = j + 1;
+        res->est = os.est / os.bnorm;
+        if (os.conv_est || os.breakdown == 1) {
+            res->reason = 3;
+            break;
+        }
+    }
+    if (lowest && res->outer > 0) {
+        std::vector<int> kh(res->outer);
+        CK(cudaMemcpy(kh.data(), P.k_hist, kh.size() * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int q : kh) res->inner += q;
+    }
+    if (res->outer == 0) {
+        k_fill<<<grid_for(N), 256, 0, h->st>>>(N, 0.0, out);
+        ++g_launches;
+        return 0;
+    }
+    int rc;
+    if ((rc = set_flag(h, P.pflag, 2))) return rc;  // finalise this level's only problem: out = Z y
+    launch_final_x(P, J, nullptr, out);
+    return set_flag(h, P.pflag, 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfgmres_solve_multilevel(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m, int32_t s,
+                             int32_t k, double tol, int32_t nlower, const int32_t* level_steps,
+                             sfgmres_stats* st) {
+    if (!h) return SFGMRES_ERR_INVALID_ARG;
+    if (h->nsys != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "sfgmres_solve_multilevel needs a single-system handle");
+    if (nlower < 1 || nlower > kMaxLowerLevels || !level_steps)
+        return fail(h, SFGMRES_ERR_INVALID_ARG, "need 1 <= nlower <= 4 lower levels and their step budgets");
+    for (int L = 0; L < nlower; ++L)
+        if (level_steps[L] < 1 || level_steps[L] > kMaxM)
+            return fail(h, SFGMRES_ERR_INVALID_ARG, "every lower level's budget must be in [1, 1024]");
+    int rc = check_solve_args(h, b, x, m, s, k, tol);
+    if (rc) return rc;
+    CK(cudaSetDevice(h->dev));
+    const int64_t launches0 = g_launches;
+    const int jmax = h->max_outer;
+    std::vector<Plan> Ps(nlower + 1);
+    if ((rc = prepare(h, 1, m, s, k, jmax, &Ps[0], nullptr))) return rc;
+    const Plan& P0 = Ps[0];
+    for (int L = 1; L <= nlower; ++L)
+        if ((rc = level_plan(h, P0, L, level_steps[L - 1], &Ps[L]))) return rc;
+    const int N = P0.N;
+    const size_t nbytes = (size_t)N * sizeof(double);
+    if ((rc = ensure(h, h->bst, nbytes))) return rc;
+    if ((rc = ensure(h, h->xst, nbytes))) return rc;
+    if ((rc = ensure(h, h->x0st, nbytes))) return rc;
+    double* db = (double*)h->bst.p;
+    double* dx = (double*)h->xst.p;
+    double* dx0 = (double*)h->x0st.p;
+    CK(cudaEventRecord(h->ev_t0, h->st));
+    CK(cudaMemcpyAsync(db, b, nbytes, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    if (x0) {
+        CK(cudaMemcpyAsync(dx0, x0, nbytes, is_device_ptr(x0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           h->st));
+        k_copy<<<grid_for(N), 256, 0, h->st>>>(N, dx0, dx);
+    } else {
+        k_fill<<<grid_for(N), 256, 0, h->st>>>(N, 0.0, dx);
+    }
+    ++g_launches;
+    const double* px0 = x0 ? dx0 : nullptr;
+    OuterState* host_ost = (OuterState*)h->h_ost.p;
+    launch_residual(P0, db, px0, P0.Vb, false);
+    launch_init_state(P0, tol);
+    CK(cudaMemcpyAsync(host_ost, P0.ost, sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    OuterState os = host_ost[0];
+    int status = SFGMRES_NOT_CONVERGED, outer = 0;
+    double rel_true = 0.0, rel_est = 0.0;
+    int64_t total_inner = 0;
+    std::string msg;
+    bool done = false;
+    if (!std::isfinite(os.beta) || !std::isfinite(os.bnorm) || os.nan) {
+        return fail(h, SFGMRES_ERR_NAN, "non-finite value in b or x0 (or in A x0)");
+    } else if (os.bnorm == 0.0) {  // x = 0
+        k_fill<<<grid_for(N), 256, 0, h->st>>>(N, 0.0, dx);
+        ++g_launches;
+        status = SFGMRES_OK;
+        done = true;
+    } else if (os.beta <= os.tol_abs) {  // x0 already meets the tolerance
+        status = SFGMRES_OK;
+        rel_true = rel_est = os.beta / os.bnorm;
+        done = true;
+    }
+    for (int j = 0; j < jmax && !done; ++j) {
+        LevelRun cr;
+        if ((rc = run_level(h, Ps, 1, P0.Vb + (int64_t)j * N, P0.nu + j, child_tolerance(h, os, j),
+                            P0.Z + (int64_t)j * N, &cr)))
+            return rc;
+        total_inner += cr.inner;
+        if (cr.error == SFGMRES_ERR_CUDA) return fail(h, SFGMRES_ERR_CUDA, "the fused inner step's grid-wide wait gave up");
+        if (cr.error) return fail(h, SFGMRES_ERR_NAN, "non-finite value during the iteration");
+        k_set_cycle<<<1, 1, 0, h->st>>>(P0.cyc, cr.outer, cr.reason, cr.est);
+        ++g_launches;
+        launch_outer_step(P0, j);
+        CK(cudaMemcpyAsync(host_ost, P0.ost, sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        CK(cudaGetLastError());
+        os = host_ost[0];
+        if (os.nan) {
+            if (os.sync_fail) return fail(h, SFGMRES_ERR_CUDA, "the fused inner step's grid-wide wait gave up");
+            return fail(h, SFGMRES_ERR_NAN, "non-finite value during the iteration");
+        }
+        const bool brk = (os.breakdown == 2);
+        const bool last = (j + 1 == jmax);
+        if (!brk) {
+            outer = j + 1;
+            rel_est = os.est / os.bnorm;
+        }
+        if (brk || os.conv_est || os.breakdown == 1 || last) {
+            // x = x0 + Z y over the steps taken, and its recomputed residual
+            if ((rc = set_flag(h, P0.pflag, 2))) return rc;
+            launch_final_x(P0, jmax, px0, dx);
+            launch_residual(P0, db, dx, nullptr, true);
+            launch_true_residual_reduce(P0);
+            CK(cudaMemcpyAsync(host_ost, P0.ost, sizeof(OuterState), cudaMemcpyDeviceToHost, h->st));
+            CK(cudaStreamSynchronize(h->st));
+            CK(cudaGetLastError());
+            if ((rc = set_flag(h, P0.pflag, 0))) return rc;
+            os = host_ost[0];
+            rel_true = std::sqrt(os.true_res2) / os.bnorm;
+            if (brk) status = SFGMRES_BREAKDOWN;
+            else if (rel_true <= tol || os.breakdown == 1) status = SFGMRES_OK;
+            else if (last) status = SFGMRES_NOT_CONVERGED;
+            else continue;
+            done = true;
+        }
+    }
+    CK(cudaMemcpyAsync(x, dx, nbytes, is_device_ptr(x) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    CK(cudaEventRecord(h->ev_t1, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    if (st) {
+        st->status = status;
+        st->outer_iters = outer;
+        st->total_inner = (int32_t)std::min<int64_t>(total_inner, INT32_MAX);
+        st->rel_res_true = rel_true;
+        st->rel_res_est = rel_est;
+        const int cnt = std::min(outer + (status == SFGMRES_BREAKDOWN ? 1 : 0), jmax);
+        const int cap = std::min(cnt, st->hist_cap);
+        if (cap > 0) {
+            std::vector<int> kh(cap), rh(cap);
+            std::vector<double> eh(cap), fh(cap), ih(cap), qh(cap);
+            CK(cudaMemcpy(kh.data(), P0.k_hist, cap * sizeof(int), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(rh.data(), P0.reason_hist, cap * sizeof(int), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(eh.data(), P0.est_hist, cap * sizeof(double), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(fh.data(), P0.ffom_hist, cap * sizeof(double), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(ih.data(), P0.ires_hist, cap * sizeof(double), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(qh.data(), P0.rho_hist, cap * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int q = 0; q < cap; ++q) {
+                if (st->inner_k) st->inner_k[q] = kh[q];
+                if (st->inner_reason) st->inner_reason[q] = rh[q];
+                if (st->res_est && q < outer) st->res_est[q] = eh[q];
+                if (st->ffom_res && q < outer) st->ffom_res[q] = fh[q];
+                if (st->inner_res && q < outer) st->inner_res[q] = ih[q];
+                if (st->inner_rho && q < outer) st->inner_rho[q] = qh[q];
+            }
+        }
+        st->kernel_launches = g_launches - launches0;
+        float tms = 0.f;
+        cudaEventElapsedTime(&tms, h->ev_t0, h->ev_t1);
+        st->t_total_ms = tms;
+        st->t_inner_spmv_ms = st->t_inner_axpy_ms = st->t_qr_ms = 0.0;
+        st->n_inner_spmv = st->n_inner_axpy = st->n_qr = 0;
+    }
     return status;
 }
 

@@ -30,7 +30,8 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SKETCH_KIND = {"sparse_sign": 0, "identity": 1}
 
 EXPORTED = ["sfgmres_create", "sfgmres_create_batch", "sfgmres_set_option", "sfgmres_get_option", "sfgmres_solve",
-            "sfgmres_solve_transpose", "sfgmres_solve_batch", "sfgmres_solve_restarted", "sfgmres_autotune", "sfgmres_update_values", "sfgmres_pattern_outer", "sfgmres_inner_cycle",
+            "sfgmres_solve_transpose", "sfgmres_solve_batch", "sfgmres_solve_restarted", "sfgmres_solve_multilevel",
+            "sfgmres_autotune", "sfgmres_update_values", "sfgmres_pattern_outer", "sfgmres_inner_cycle",
             "sfgmres_sketch_apply", "sfgmres_sketch_apply_noalloc", "sfgmres_sketch_pattern", "sfgmres_spmv",
             "sfgmres_destroy", "sfgmres_last_error", "sfgmres_version"]
 
@@ -74,6 +75,7 @@ def load():
     lib.sfgmres_solve_batch.argtypes = [vp, i32, vp, vp, vp, i32, i32, i32, f64, i32, C.POINTER(BatchStats)]
     lib.sfgmres_autotune.argtypes = [vp, i32, i32, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(f64)]
     lib.sfgmres_solve_restarted.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, i32, vp, C.POINTER(i32)]
+    lib.sfgmres_solve_multilevel.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, i32, vp, C.POINTER(Stats)]
     lib.sfgmres_update_values.argtypes = [vp, vp]
     lib.sfgmres_pattern_outer.argtypes = [vp, vp, vp, f64, vp]
     lib.sfgmres_inner_cycle.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, C.POINTER(i32), C.POINTER(i32)]
@@ -201,6 +203,14 @@ def sfgmres_solve_restarted(h: int, b, x0, x, m: int, s: int, k: int, tol: float
     return rc, cyc.value
 
 
+def sfgmres_solve_multilevel(h: int, b, x0, x, m: int, s: int, k: int, tol: float, level_steps,
+                             stats: Optional[Stats] = None) -> int:
+    """Multi-level FGMRES: ``level_steps`` lists the outer-step budgets of the FGMRES levels below the top."""
+    ls = np.ascontiguousarray(level_steps, dtype=np.int32)
+    return _check(h, load().sfgmres_solve_multilevel(h, _ptr(b), _ptr(x0), _ptr(x), m, s, k, tol, len(ls), _ptr(ls),
+                                                     C.byref(stats) if stats is not None else None))
+
+
 def sfgmres_inner_cycle(h: int, v, z, m: int, s: int, k: int, basis=None, y=None):
     kk, rr = C.c_int32(), C.c_int32()
     rc = _check(h, load().sfgmres_inner_cycle(h, _ptr(v), _ptr(z), m, s, k, _ptr(basis), _ptr(y), C.byref(kk),
@@ -290,9 +300,10 @@ class Solver:
         return sfgmres_get_option(self.h, self._KEYS[key])
 
     def solve(self, b, x0=None, *, m: int, s: int, k: int, tol: float = 1e-8, out=None, hist_cap: int = 1000,
-              transpose: bool = False):
+              transpose: bool = False, level_steps=None):
         """Solve ``A x = b`` (``A^T x = b`` with ``transpose``); ``b``/``x0``/``out`` are float64 CUDA tensors or NumPy
-        arrays.  Returns ``(x, info)``."""
+        arrays.  ``level_steps`` (a list of outer-step budgets) runs the multi-level FGMRES with that many levels
+        below the top (``sfgmres_solve_multilevel``).  Returns ``(x, info)``."""
         import torch
 
         if out is None:
@@ -311,7 +322,10 @@ class Solver:
         st.inner_reason = C.cast(rh, C.POINTER(C.c_int32))
         st.res_est = C.cast(eh, C.POINTER(C.c_double))
         st.ffom_res = C.cast(fh, C.POINTER(C.c_double))
-        rc = (sfgmres_solve_transpose if transpose else sfgmres_solve)(self.h, b, x0, out, m, s, k, tol, st)
+        if level_steps is None:
+            rc = (sfgmres_solve_transpose if transpose else sfgmres_solve)(self.h, b, x0, out, m, s, k, tol, st)
+        else:
+            rc = sfgmres_solve_multilevel(self.h, b, x0, out, m, s, k, tol, level_steps, st)
         J = st.outer_iters
         cnt = min(J + (1 if rc == BREAKDOWN else 0), hist_cap)
         info = {"status": rc, "outer_iters": J, "total_inner": st.total_inner, "rel_res_true": st.rel_res_true,
