@@ -111,6 +111,18 @@ extern "C" {
                                         (Galerkin condition), its residual given by Eq. 4; the convergence test and
                                         res_est use that residual, and a step whose square system is singular ends
                                         the solve with SFGMRES_BREAKDOWN keeping the previous iterate. */
+#define SFGMRES_OPT_PRECOND 16        /* 0 (default): none.  1: zero-fill incomplete LU (ILU(0)) right preconditioning
+                                        (the "-p" runs of Section 4): the rows are ordered colour by colour (a greedy
+                                        colouring of the pattern of A + A^T in the natural order: no two coupled rows
+                                        share a colour), L U is the ILU(0) factorisation of the permuted matrix
+                                        P A P^T and M = P^T L U P; every sGMRES cycle works on A M^{-1} and its
+                                        correction is z_j = M^{-1} B_k y_k, so the outer FGMRES still minimises the
+                                        residual of A x = b.  Each colour's rows are independent in both triangular
+                                        solves (one pass per colour).  Single-system handles, one right-hand side,
+                                        FP64 inner cycles, not the transposed solve (other uses return
+                                        SFGMRES_ERR_INVALID_ARG); A must store every diagonal entry and no repeated
+                                        entries.  The ordering is built at the first solve that uses it, the
+                                        factors again after sfgmres_update_values. */
 /* ---- sfgmres_solve_batch flags ---------------------------------------------------------------------------- */
 #define SFGMRES_SOLVE_TRANSPOSE 1    /* solve A_q^T x = b for every problem (see sfgmres_solve_transpose) */
 
@@ -306,6 +318,15 @@ SFGMRES_API int sfgmres_solve_restarted(sfgmres_t h, const double* b, const doub
 SFGMRES_API int sfgmres_solve_multilevel(sfgmres_t h, const double* b, const double* x0, double* x, int32_t m,
                                          int32_t s, int32_t k, double tol, int32_t nlower,
                                          const int32_t* level_steps, sfgmres_stats* st);
+
+/* The ILU(0) preconditioner of SFGMRES_OPT_PRECOND (built now if it is not already; the option itself need not be
+ * set): colour (host int32[n], may be NULL) receives every row's colour, ncolours (host int32, may be NULL) their
+ * number, lu (host float64[nnz], may be NULL) the factor values in the order of A's stored entries: for the entry
+ * (i, j) of A, the entry (p(i), p(j)) of L (below the diagonal; L's unit diagonal is not stored) or of U (on and above
+ * it), with p(i) the position of row i in the colour order (colour by colour, natural order within a colour).
+ * Single-system handles.  Returns SFGMRES_ERR_INVALID_ARG for a zero pivot, a missing diagonal entry or repeated
+ * entries. */
+SFGMRES_API int sfgmres_precond_info(sfgmres_t h, int32_t* colour, int32_t* ncolours, double* lu);
 
 /* c = S v for the handle's embedding with s rows (Eq. 1).  v: device float64[n], c: device float64[s].
  * Single-system handles only. */

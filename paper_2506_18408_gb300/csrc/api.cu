@@ -101,6 +101,7 @@ struct sfgmres_ctx {
     int rhs_group = 1;  // right-hand sides per grouped inner-SpMV CTA (1: not grouped)
     int fuse_step = 1;  // 1: one launch per inner step where the row blocks fit on the GPU at once
     int outer_variant = 0;  // 0: FGMRES; 1: FFOM
+    int precond = 0;        // 0: none; 1: ILU(0) in a multicolour order, right preconditioning
     int wait_extra = 0;  // fused step: arrivals waited for beyond the launch's blocks (test of the give-up path)
     bool step_fused = false;  // the last cycle ran the fused inner step
     double cond_thr = 1e15;
@@ -132,6 +133,14 @@ struct sfgmres_ctx {
         k_hist, reason_hist,
         ost;
     DevBuf bst, xst, x0st;  // staging / internal copies
+    // ILU(0) right preconditioner (built on first use; the factors follow sfgmres_update_values)
+    IluHost ilu;
+    std::vector<int> ilu_colour;  // colour of every row (original order)
+    std::vector<int> ilu_src;     // host copy of ilu.src
+    DevBuf ilu_rp, ilu_col, ilu_diag, ilu_perm, ilu_src_d, ilu_lu, ilu_y, ilu_zp, ilu_t, ilu_zt, ilu_bad;
+    int ilu_built = 0;            // structure built
+    int ilu_vals_ver = -1;        // values version the factors were computed for
+    int vals_ver = 0;             // bumped by sfgmres_update_values
     // outer workspaces of the lower levels of sfgmres_solve_multilevel (level 1, 2, ...)
     struct LevelWs {
         DevBuf Vb, Z, nu, Wo, opart, npart, npart2, h1, h2, H, cs, sn, g, yo, est_hist, ffom_hist, ires_hist,
@@ -692,9 +701,126 @@ int ensure_groups(sfgmres_ctx* h, Geo* g, int G) {
 
 // Allocates the workspaces of a solve with nrhs right-hand sides per system and fills a Plan (for A, or for A^T
 // when transpose is set).  Every problem's flag is reset to "active".
+// ---- ILU(0) right preconditioner (set-up; the kernels are in precond.cu) ----
+// Structure, once per handle: a greedy colouring of the pattern of A + A^T in the natural row order (each row takes the
+// smallest colour no earlier coupled row has), the rows ordered colour by colour (natural order within a colour), and
+// P A P^T in CSR with sorted columns, its diagonal positions and the source position of every entry.  This is graph
+// analysis of the sparsity pattern, done on the host from a copy of the CSR structure.  Values, at every change of A's
+// values: the ILU(0) factorisation on the device, one pass per colour.
+int ensure_ilu(sfgmres_ctx* h) {
+    if (h->nsys != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "ILU(0) preconditioning needs a single-system handle");
+    const int n = h->n;
+    const int64_t nnz = h->nnz;
+    int rc;
+    if (!h->ilu_built) {
+        std::vector<int> rp(n + 1), col(std::max<int64_t>(nnz, 1));
+        CK(cudaMemcpy(rp.data(), h->rp, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+        if (nnz) CK(cudaMemcpy(col.data(), h->col, nnz * sizeof(int), cudaMemcpyDeviceToHost));
+        // the columns' rows (the pattern of A^T) by a counting sort
+        std::vector<int> tp(n + 1, 0), trow(std::max<int64_t>(nnz, 1));
+        for (int64_t p = 0; p < nnz; ++p) ++tp[col[p] + 1];
+        for (int i = 0; i < n; ++i) tp[i + 1] += tp[i];
+        {
+            std::vector<int> fill(tp.begin(), tp.end() - 1);
+            for (int i = 0; i < n; ++i)
+                for (int p = rp[i]; p < rp[i + 1]; ++p) trow[fill[col[p]]++] = i;
+        }
+        // greedy colouring in the natural order
+        std::vector<int> colour(n, -1), seen;  // seen[c] == i: colour c is taken by a coupled earlier row of row i
+        int ncol = 0;
+        for (int i = 0; i < n; ++i) {
+            auto mark = [&](int j) {
+                if (j < i && colour[j] >= 0) {
+                    if ((int)seen.size() <= colour[j]) seen.resize(colour[j] + 1, -1);
+                    seen[colour[j]] = i;
+                }
+            };
+            for (int p = rp[i]; p < rp[i + 1]; ++p) mark(col[p]);
+            for (int p = tp[i]; p < tp[i + 1]; ++p) mark(trow[p]);
+            int c = 0;
+            while (c < (int)seen.size() && seen[c] == i) ++c;
+            colour[i] = c;
+            ncol = std::max(ncol, c + 1);
+        }
+        // rows colour by colour
+        std::vector<int> starts(ncol + 1, 0), perm(n), inv(n);
+        for (int i = 0; i < n; ++i) ++starts[colour[i] + 1];
+        for (int c = 0; c < ncol; ++c) starts[c + 1] += starts[c];
+        {
+            std::vector<int> fill(starts.begin(), starts.end() - 1);
+            for (int i = 0; i < n; ++i) perm[fill[colour[i]]++] = i;
+        }
+        for (int r = 0; r < n; ++r) inv[perm[r]] = r;
+        // P A P^T with sorted columns, diagonal positions, source positions
+        std::vector<int> prp(n + 1, 0), pcol(std::max<int64_t>(nnz, 1)), psrc(std::max<int64_t>(nnz, 1)), pdiag(n, -1);
+        std::vector<std::pair<int, int>> row;
+        for (int r = 0; r < n; ++r) {
+            const int i = perm[r];
+            row.clear();
+            for (int p = rp[i]; p < rp[i + 1]; ++p) row.push_back({inv[col[p]], p});
+            std::sort(row.begin(), row.end());
+            prp[r + 1] = prp[r] + (int)row.size();
+            for (size_t q = 0; q < row.size(); ++q) {
+                if (q > 0 && row[q].first == row[q - 1].first)
+                    return fail(h, SFGMRES_ERR_INVALID_ARG, "ILU(0) needs a CSR without repeated entries");
+                pcol[prp[r] + q] = row[q].first;
+                psrc[prp[r] + q] = row[q].second;
+                if (row[q].first == r) pdiag[r] = prp[r] + (int)q;
+            }
+            if (pdiag[r] < 0) return fail(h, SFGMRES_ERR_INVALID_ARG, "ILU(0) needs every diagonal entry of A stored");
+        }
+        const size_t N = (size_t)n, Z = (size_t)std::max<int64_t>(nnz, 1);
+        if ((rc = ensure(h, h->ilu_rp, (N + 1) * 4)) || (rc = ensure(h, h->ilu_col, Z * 4)) ||
+            (rc = ensure(h, h->ilu_diag, N * 4)) || (rc = ensure(h, h->ilu_perm, N * 4)) ||
+            (rc = ensure(h, h->ilu_src_d, Z * 4)) || (rc = ensure(h, h->ilu_lu, Z * 8)) ||
+            (rc = ensure(h, h->ilu_y, N * 8)) || (rc = ensure(h, h->ilu_zp, N * 8)) ||
+            (rc = ensure(h, h->ilu_t, N * 8)) || (rc = ensure(h, h->ilu_zt, N * 8)) ||
+            (rc = ensure(h, h->ilu_bad, sizeof(int))))
+            return rc;
+        CK(cudaMemcpy(h->ilu_rp.p, prp.data(), (N + 1) * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->ilu_col.p, pcol.data(), Z * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->ilu_diag.p, pdiag.data(), N * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->ilu_perm.p, perm.data(), N * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->ilu_src_d.p, psrc.data(), Z * 4, cudaMemcpyHostToDevice));
+        IluHost& H = h->ilu;
+        H.n = n;
+        H.ncol = ncol;
+        H.nnz = nnz;
+        H.starts = starts;
+        H.src = (const int*)h->ilu_src_d.p;
+        H.dev.rp = (const int*)h->ilu_rp.p;
+        H.dev.col = (const int*)h->ilu_col.p;
+        H.dev.diag = (const int*)h->ilu_diag.p;
+        H.dev.perm = (const int*)h->ilu_perm.p;
+        H.dev.lu = (double*)h->ilu_lu.p;
+        H.dev.y = (double*)h->ilu_y.p;
+        H.dev.zp = (double*)h->ilu_zp.p;
+        h->ilu_colour = colour;
+        h->ilu_src = psrc;
+        h->ilu_built = 1;
+        h->ilu_vals_ver = -1;
+    }
+    if (h->ilu_vals_ver != h->vals_ver) {
+        CK(cudaMemsetAsync(h->ilu_bad.p, 0, sizeof(int), h->st));
+        CK(launch_ilu_factor(h->ilu, h->val, (int*)h->ilu_bad.p, h->st));
+        int bad = 0;
+        CK(cudaMemcpyAsync(&bad, h->ilu_bad.p, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        if (bad) return fail(h, SFGMRES_ERR_INVALID_ARG, "ILU(0) met a zero pivot");
+        h->ilu_vals_ver = h->vals_ver;
+    }
+    return 0;
+}
+
 int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Geo** geo_out, bool transpose = false) {
     int rc;
     Geo* g = nullptr;
+    if (h->precond) {
+        if (h->nsys != 1 || nrhs != 1 || transpose || h->prec != kFP64)
+            return fail(h, SFGMRES_ERR_INVALID_ARG, "ILU(0) preconditioning needs a single system, one right-hand "
+                                                    "side, FP64 inner cycles and no transpose");
+        if ((rc = ensure_ilu(h))) return rc;
+    }
     if ((rc = get_geometry(h, nrhs, &g))) return rc;
     if ((rc = build_sketch(h, s))) return rc;
     if (transpose && (rc = ensure_transpose(h))) return rc;
@@ -836,6 +962,11 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     } else {
         P.gsync = nullptr;
     }
+    if (h->precond) {
+        P.ilu = h->ilu.dev;
+        P.ilu_host = &h->ilu;
+        P.xin = (const double*)h->ilu_t.p;
+    }
     if (geo_out) *geo_out = g;
     return 0;
 }
@@ -891,7 +1022,9 @@ double ev_sum(const std::vector<EventPair>& pool, size_t base, size_t count) {
 // Cluster size of the whole-cycle persistent kernel for this plan, or 0 where the per-step kernels run: small problems
 // (at most kPersistCluster row blocks each) with one thread per row and t <= 4, not profiled.
 int persistent_cluster(const sfgmres_ctx* h, const Plan& P) {
-    if (!h->persistent || h->profile || P.vec != 1 || P.t > 4 || P.maxbp < 1 || P.maxbp > kPersistCluster) return 0;
+    if (!h->persistent || h->profile || P.ilu_host || P.vec != 1 || P.t > 4 || P.maxbp < 1 ||
+        P.maxbp > kPersistCluster)
+        return 0;
     if (persistent_smem(P, P.maxbp) > 200 * 1024) return 0;
     return P.maxbp;
 }
@@ -908,6 +1041,8 @@ int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const doubl
     h->step_fused = false;
     for (int i = 0; i < P.m; ++i) {
         const bool last = (i == P.m - 1);
+        // right preconditioning: the step multiplies t_i = M^{-1} u_i (the passes return at once after a stop)
+        if (P.ilu_host) launch_ilu_apply(P, i, (const double*)P.U + (int64_t)i * P.N, const_cast<double*>(P.xin));
         if (prof) ev_rec(h->ev_spmv[ev + i].a, h->st, capturing);
         const bool fused = launch_inner_step(P, i, last);  // one launch, timed as the inner kernel
         if (!fused) launch_inner_spmv(P, i);
@@ -926,7 +1061,12 @@ int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const doubl
     }
     CK(cudaEventRecord(h->ev_q, h->qst));
     CK(cudaStreamWaitEvent(h->st, h->ev_q, 0));
-    launch_inner_finish(P, z);
+    if (P.ilu_host) {  // z = M^{-1} (B_k y)
+        launch_inner_finish(P, (double*)h->ilu_zt.p);
+        launch_ilu_apply(P, -1, (const double*)h->ilu_zt.p, z);
+    } else {
+        launch_inner_finish(P, z);
+    }
     return 0;
 }
 
@@ -947,7 +1087,8 @@ std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
                           (const void*)P.sn, (const void*)P.g, (const void*)P.yo, (const void*)P.est_hist,
                           (const void*)P.ffom_hist, (const void*)P.ires_hist, (const void*)P.rho_hist,
                           (const void*)P.k_hist, (const void*)P.reason_hist,
-                          (const void*)P.ost, (const void*)P.st, (const void*)h->qst, (const void*)P.gsync})
+                          (const void*)P.ost, (const void*)P.st, (const void*)h->qst, (const void*)P.gsync,
+                          (const void*)P.xin, (const void*)P.ilu.lu})
         u(p);
     for (int64_t v : std::initializer_list<int64_t>{(int64_t)P.G, (int64_t)P.ngrp, (int64_t)P.nnz, (int64_t)P.vec, (int64_t)P.N, (int64_t)P.P, (int64_t)P.nblk, (int64_t)P.Bn,
                       (int64_t)P.s, (int64_t)P.zeta, (int64_t)P.kind, (int64_t)P.sk_headroom, (int64_t)P.prec,
@@ -1442,6 +1583,9 @@ int sfgmres_destroy(sfgmres_t h) {
                       &h->est_hist, &h->ffom_hist, &h->ires_hist, &h->rho_hist, &h->k_hist, &h->reason_hist, &h->ost, &h->bst, &h->xst,
                       &h->x0st, &h->gsync};
     for (DevBuf* b : bufs) release(*b);
+    for (DevBuf* b : {&h->ilu_rp, &h->ilu_col, &h->ilu_diag, &h->ilu_perm, &h->ilu_src_d, &h->ilu_lu, &h->ilu_y,
+                      &h->ilu_zp, &h->ilu_t, &h->ilu_zt, &h->ilu_bad})
+        release(*b);
     for (auto& L : h->lvl)
         for (DevBuf* b : {&L.Vb, &L.Z, &L.nu, &L.Wo, &L.opart, &L.npart, &L.npart2, &L.h1, &L.h2, &L.H, &L.cs, &L.sn,
                           &L.g, &L.yo, &L.est_hist, &L.ffom_hist, &L.ires_hist, &L.rho_hist, &L.k_hist,
@@ -1537,6 +1681,10 @@ int sfgmres_set_option(sfgmres_t h, int32_t key, double v) {
             if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "outer variant must be 0 or 1");
             h->outer_variant = iv;
             return 0;
+        case SFGMRES_OPT_PRECOND:
+            if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "precond must be 0 or 1");
+            h->precond = iv;
+            return 0;
         case SFGMRES_OPT_GRAPH:
             if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "graph must be 0 or 1");
             h->use_graph = iv;
@@ -1572,6 +1720,7 @@ int sfgmres_get_option(sfgmres_t h, int32_t key, double* v) {
         case SFGMRES_OPT_FUSED_STEP: *v = h->fuse_step; return 0;
         case SFGMRES_OPT_STEP_WAIT_EXTRA: *v = h->wait_extra; return 0;
         case SFGMRES_OPT_OUTER_VARIANT: *v = h->outer_variant; return 0;
+        case SFGMRES_OPT_PRECOND: *v = h->precond; return 0;
         default: return fail(h, SFGMRES_ERR_INVALID_ARG, "unknown option key");
     }
 }
@@ -1725,6 +1874,7 @@ int sfgmres_update_values(sfgmres_t h, const double* vals) {
     if (h->nnz == 0) return SFGMRES_OK;
     CK(cudaMemcpyAsync(h->val, vals, h->nnz * sizeof(double),
                        is_device_ptr(vals) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    ++h->vals_ver;  // the ILU(0) factors (if any) are recomputed at their next use
     if (h->val32) k_to_f32<<<grid_for(h->nnz), 256, 0, h->st>>>(h->nnz, h->val, h->val32);
     if (h->rpT) {
         launch_gather_vals(h->nnz, h->srcT, h->val, h->valT, h->st);
@@ -2161,6 +2311,21 @@ int sfgmres_solve_multilevel(sfgmres_t h, const double* b, const double* x0, dou
         st->n_inner_spmv = st->n_inner_axpy = st->n_qr = 0;
     }
     return status;
+}
+
+int sfgmres_precond_info(sfgmres_t h, int32_t* colour, int32_t* ncolours, double* lu) {
+    if (!h) return SFGMRES_ERR_INVALID_ARG;
+    CK(cudaSetDevice(h->dev));
+    int rc = ensure_ilu(h);
+    if (rc) return rc;
+    if (colour) std::memcpy(colour, h->ilu_colour.data(), (size_t)h->n * sizeof(int32_t));
+    if (ncolours) *ncolours = h->ilu.ncol;
+    if (lu && h->nnz > 0) {
+        std::vector<double> v((size_t)h->nnz);
+        CK(cudaMemcpy(v.data(), h->ilu_lu.p, (size_t)h->nnz * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int64_t p = 0; p < h->nnz; ++p) lu[h->ilu_src[p]] = v[p];
+    }
+    return SFGMRES_OK;
 }
 
 int sfgmres_sketch_apply(sfgmres_t h, int32_t s, const double* v, double* c) {

@@ -51,13 +51,13 @@ __device__ __forceinline__ void sell_chunk(const int* __restrict__ cp, const MT*
 template <int NW, typename MT, typename VT, typename AT>
 __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ soff, const uint8_t* __restrict__ slen,
                                               const int* __restrict__ scol, const MT* __restrict__ sval, int sb,
-                                              const VT* __restrict__ Ub, int i, int lo, int v0, int len, int cs,
-                                              AT* __restrict__ wblk, AT* __restrict__ W, AT (&acc)[NW > 0 ? NW : 1],
-                                              AT& nrm) {
+                                              const VT* __restrict__ Ub, const VT* __restrict__ xg, int i, int lo,
+                                              int v0, int len, int cs, AT* __restrict__ wblk, AT* __restrict__ W,
+                                              AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
     const int lane = threadIdx.x & 31;
     const unsigned long long pol = l2_keep_policy();  // window rows and w' are read again by the update
     const VT* x = Ub + (int64_t)i * N;
-    const VT* xs = x + cs;  // gather base: vector index of matrix column c is c + cs
+    const VT* xs = xg + cs;  // gather base (u_i, or M^{-1} u_i with a preconditioner): column c at vector index c + cs
     int emax = 1;
     int kw = threadIdx.x & ~31;
     int o0 = 0, o1 = 0, rl = 0;
@@ -124,13 +124,14 @@ __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ sof
 // flight together.  Returns the thread's largest exponent of w'.
 template <int NW, typename MT, typename VT, typename AT>
 __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ rp, const int* __restrict__ col,
-                                                const MT* __restrict__ val, const VT* __restrict__ Ub, int i, int lo,
-                                                int v0, int len, int cs, AT* __restrict__ wblk, AT* __restrict__ W,
+                                                const MT* __restrict__ val, const VT* __restrict__ Ub,
+                                                const VT* __restrict__ xg, int i, int lo, int v0, int len, int cs,
+                                                AT* __restrict__ wblk, AT* __restrict__ W,
                                                 AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
     const int lane = threadIdx.x & 31;
     const unsigned long long pol = l2_keep_policy();  // window rows and w' are read again by the update
     const VT* x = Ub + (int64_t)i * N;
-    const VT* xs = x + cs;                // gather base: vector index of matrix column c is c + cs
+    const VT* xs = xg + cs;               // gather base (u_i, or M^{-1} u_i): column c at vector index c + cs
     const int* rpm = rp + (v0 - cs);      // row pointers of the block's matrix rows
     int emax = 1;
     int kw = threadIdx.x & ~31;
@@ -225,18 +226,19 @@ __device__ __forceinline__ bool inner_spmv_part(const Plan& P, int i, const MT* 
 #pragma unroll
     for (int q = 0; q < NW; ++q) acc[q] = AT(0);
     int emax;
-    AT nrm = AT(0);  // ||u_i||^2 over the block (the vector this step multiplies)
+    AT nrm = AT(0);  // ||u_i||^2 over the block (u_i, the basis vector this step extends the basis from)
+    // the vector the SpMV multiplies: u_i, or t_i = M^{-1} u_i with a right preconditioner (an FP64 plan only)
+    const VT* xg = P.xin ? reinterpret_cast<const VT*>(P.xin) : Ub + (int64_t)i * N;
     if constexpr (V == kVecSell) {
-        emax = spmv_dots_sell<NW>(N, P.sl_off, P.sl_len, P.sl_col, val, P.sl_base[bi.list], Ub, i, lo, bi.v0,
+        emax = spmv_dots_sell<NW>(N, P.sl_off, P.sl_len, P.sl_col, val, P.sl_base[bi.list], Ub, xg, i, lo, bi.v0,
                                   bi.len, bi.cs, wblk, W, acc, nrm);
     } else if constexpr (V == 1) {
-        emax = spmv_dots_scalar<NW>(N, P.rp, P.col, val, Ub, i, lo, bi.v0, bi.len, bi.cs, wblk, W, acc, nrm);
+        emax = spmv_dots_scalar<NW>(N, P.rp, P.col, val, Ub, xg, i, lo, bi.v0, bi.len, bi.cs, wblk, W, acc, nrm);
     } else {
         const int m0 = bi.v0 - bi.cs;
         int n0, n01;
         block_bins(P, bi, n0, n01);
-        spmv_rows_to_smem<V, U, MT, VT, AT>(P.rp, P.col, val, Ub + (int64_t)i * N + bi.cs, m0, m0 + bi.len, wblk,
-                                            P.perm, n0, n01);
+        spmv_rows_to_smem<V, U, MT, VT, AT>(P.rp, P.col, val, xg + bi.cs, m0, m0 + bi.len, wblk, P.perm, n0, n01);
         __syncthreads();
         emax = dots_pass<NW>(N, bi.v0, bi.len, Ub, lo, i, wblk, W, acc, nrm);
     }

@@ -14,11 +14,33 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace sfg {
 
 enum Precision { kFP64 = 0, kFP32 = 1, kBF16 = 2 };
+
+// ILU(0) right preconditioner in a multicolour order (precond.cu): the permuted matrix P A P^T in CSR with sorted
+// columns, its factors and work vectors (device pointers; a value member of the plan, so kernels read it directly).
+struct IluDev {
+    const int* rp = nullptr;    // [n+1]
+    const int* col = nullptr;   // [nnz] columns (permuted indices), sorted within each row
+    const int* diag = nullptr;  // [n] position of the diagonal entry in its row
+    const int* perm = nullptr;  // [n] original index of permuted row r
+    double* lu = nullptr;       // [nnz] L strictly below the diagonal (unit diagonal implied), U from the diagonal on
+    double* y = nullptr;        // [n] forward-pass vector (permuted order)
+    double* zp = nullptr;       // [n] backward-pass vector (permuted order)
+};
+// Host side of the preconditioner: the colour ranges the launchers loop over.
+struct IluHost {
+    int n = 0, ncol = 0;
+    int64_t nnz = 0;
+    std::vector<int> starts;   // [ncol + 1] first permuted row of each colour
+    const int* src = nullptr;  // device [nnz]: position in A's CSR of every entry of P A P^T
+    IluDev dev;
+};
 
 // Everything a kernel needs, as plain device pointers and sizes (owned by the solver handle).
 struct Plan {
@@ -117,6 +139,12 @@ struct Plan {
     int* reason_hist = nullptr;   // [P][jmax]
     OuterState* ost = nullptr;    // [P]
 
+    // right preconditioning (ILU(0), single FP64 system): the factors, and xin, the vector the inner SpMV multiplies
+    // in place of the basis vector u_i (t_i = M^{-1} u_i); null without a preconditioner
+    IluDev ilu;
+    const IluHost* ilu_host = nullptr;
+    const double* xin = nullptr;
+
     cudaStream_t st = nullptr;
 };
 
@@ -185,6 +213,13 @@ void launch_inner_axpy(const Plan& p, int i, bool last);
 cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st);  // cluster launch on stream st
 void launch_inner_finish(const Plan& p, double* z);  // y = R^{-1} d, z = sum_l y_l b_l (FP64)
 void launch_export_basis(const Plan& p, double* out, int count);  // out[l*N + r] = sigma_l * u_l[r] (FP64)
+
+// ---- ILU(0) right preconditioning (precond.cu) ----
+// lu = the values of P A P^T (gathered from A's values), then ILU(0) colour by colour; *bad |= 1 on a zero pivot
+cudaError_t launch_ilu_factor(const IluHost& H, const double* val, int* bad, cudaStream_t st);
+// out = M^{-1} u = P^T (L U)^{-1} P u in the original order (u and out n float64, distinct); i >= 0: step i of the
+// plan's cycle (the passes return at once once the cycle has stopped), i < 0: always
+void launch_ilu_apply(const Plan& P, int i, const double* u, double* out);
 
 // ---- persistent cycle (persistent.cu) ----
 // The whole inner cycle (all steps, least squares and z = B y) in one launch, one cluster of nq CTAs per problem

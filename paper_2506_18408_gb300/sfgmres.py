@@ -24,13 +24,13 @@ ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NAN = -1, -2, -3, -4
 CSR_HOST = 1
 OPT_PRECISION, OPT_ZETA, OPT_COND_THRESHOLD, OPT_C3, OPT_MAX_OUTER, OPT_SKETCH_KIND, OPT_PROFILE, \
     OPT_SPMV_VECTOR, OPT_BLOCK_ROWS, OPT_GRAPH, OPT_RHS_GROUP, OPT_PERSISTENT, OPT_FUSED_STEP, \
-    OPT_STEP_WAIT_EXTRA, OPT_OUTER_VARIANT = range(1, 16)
+    OPT_STEP_WAIT_EXTRA, OPT_OUTER_VARIANT, OPT_PRECOND = range(1, 17)
 SOLVE_TRANSPOSE = 1
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SKETCH_KIND = {"sparse_sign": 0, "identity": 1}
 
 EXPORTED = ["sfgmres_create", "sfgmres_create_batch", "sfgmres_set_option", "sfgmres_get_option", "sfgmres_solve",
-            "sfgmres_solve_transpose", "sfgmres_solve_batch", "sfgmres_solve_restarted", "sfgmres_solve_multilevel",
+            "sfgmres_solve_transpose", "sfgmres_solve_batch", "sfgmres_solve_restarted", "sfgmres_solve_multilevel", "sfgmres_precond_info",
             "sfgmres_autotune", "sfgmres_update_values", "sfgmres_pattern_outer", "sfgmres_inner_cycle",
             "sfgmres_sketch_apply", "sfgmres_sketch_apply_noalloc", "sfgmres_sketch_pattern", "sfgmres_spmv",
             "sfgmres_destroy", "sfgmres_last_error", "sfgmres_version"]
@@ -76,6 +76,7 @@ def load():
     lib.sfgmres_autotune.argtypes = [vp, i32, i32, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(f64)]
     lib.sfgmres_solve_restarted.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, i32, vp, C.POINTER(i32)]
     lib.sfgmres_solve_multilevel.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, i32, vp, C.POINTER(Stats)]
+    lib.sfgmres_precond_info.argtypes = [vp, vp, C.POINTER(i32), vp]
     lib.sfgmres_update_values.argtypes = [vp, vp]
     lib.sfgmres_pattern_outer.argtypes = [vp, vp, vp, f64, vp]
     lib.sfgmres_inner_cycle.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, C.POINTER(i32), C.POINTER(i32)]
@@ -211,6 +212,14 @@ def sfgmres_solve_multilevel(h: int, b, x0, x, m: int, s: int, k: int, tol: floa
                                                      C.byref(stats) if stats is not None else None))
 
 
+def sfgmres_precond_info(h: int, colour=None, lu=None) -> int:
+    """The ILU(0) preconditioner's colouring (int32[n]) and factor values in A's entry order (float64[nnz]), both
+    NumPy arrays filled in place (either may be None); returns the number of colours."""
+    nc = C.c_int32()
+    _check(h, load().sfgmres_precond_info(h, _ptr(colour), C.byref(nc), _ptr(lu)), allow_positive=False)
+    return nc.value
+
+
 def sfgmres_inner_cycle(h: int, v, z, m: int, s: int, k: int, basis=None, y=None):
     kk, rr = C.c_int32(), C.c_int32()
     rc = _check(h, load().sfgmres_inner_cycle(h, _ptr(v), _ptr(z), m, s, k, _ptr(basis), _ptr(y), C.byref(kk),
@@ -262,7 +271,7 @@ class Solver:
              "spmv_vector": OPT_SPMV_VECTOR, "block_rows": OPT_BLOCK_ROWS, "graph": OPT_GRAPH,
              "rhs_group": OPT_RHS_GROUP, "persistent": OPT_PERSISTENT,
              "fused_step": OPT_FUSED_STEP, "step_wait_extra": OPT_STEP_WAIT_EXTRA,
-             "outer_variant": OPT_OUTER_VARIANT}
+             "outer_variant": OPT_OUTER_VARIANT, "precond": OPT_PRECOND}
 
     def __init__(self, n, row_ptr, col, val, sketch_seed: int = 1, stream=None, **options):
         import torch
@@ -397,6 +406,13 @@ class Solver:
         y = torch.zeros(m, dtype=torch.float64, device=v.device)
         _, kk, rr = sfgmres_inner_cycle(self.h, v, z, m, s, k, B, y)
         return z, kk, rr, B, y[:kk]
+
+    def precond_info(self):
+        """``(colour int32[n], ncolours, lu float64[nnz])`` of the ILU(0) preconditioner (see sfgmres_precond_info)."""
+        colour = np.empty(self.n, dtype=np.int32)
+        lu = np.empty(self.nnz, dtype=np.float64)
+        nc = sfgmres_precond_info(self.h, colour, lu)
+        return colour, nc, lu
 
     def sketch(self, v, s: int):
         import torch
