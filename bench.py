@@ -113,6 +113,21 @@ def alg_bytes_inner_spmv(n, nnz, t, zeta, s, nblk, sv):
     return a + vec + sk
 
 
+def alg_bytes_solve(n, nnz, t, sv, sval, inner_steps, outer_steps):
+    """Compulsory bytes of a whole solve of one problem: its inner steps (alg_bytes_inner_step), each cycle's z = B y
+    ((k + 1) n S_v read, n FP64 written, summed over the cycles: (inner_steps + outer_steps) n S_v + 8 n per cycle), and
+    each outer step j (an FP64 SpMV with A and z_j read, w written, and CGS2 against v_0..v_j: (4 j + 3) n 8)."""
+    inner = inner_steps * alg_bytes_inner_step_prec(n, nnz, t, sv, sval)
+    gemv = (inner_steps + outer_steps) * n * sv + outer_steps * 8 * n
+    outer = sum(nnz * 12 + 4 * (n + 1) + 16 * n + (4 * j + 3) * n * 8 for j in range(outer_steps))
+    return inner + gemv + outer
+
+
+def alg_bytes_inner_step_prec(n, nnz, t, sv, sval):
+    """alg_bytes_inner_step with the matrix values in sval bytes (FP32 copy for FP32 inner cycles)."""
+    return nnz * (sval + 4) + 4 * (n + 1) + (2 * t + 3) * n * sv
+
+
 def alg_bytes_inner_step(n, nnz, t, sv):
     """Compulsory bytes of one whole inner step (fused SpMV + dots + sketch, Arnoldi update; the sketch hashed, so no
     bytes for S): A once, b_i read, w written and read back, t window vectors read for the update, t - 1 of them
@@ -481,6 +496,16 @@ def run_batch(args, dev, stream):
     sv.close()
     sec = statistics.mean(times)
     st = info["status_p"]
+    # algorithmic bytes of the whole batch (FP32 inner cycles: FP32 values and basis), problem by problem
+    rows_nnz = np.diff(A.row_ptr)
+    sys_off = np.concatenate([[0], np.cumsum(A.sys_n)])
+    sys_nnz = [int(rows_nnz[sys_off[q]:sys_off[q + 1]].sum()) for q in range(len(A.sys_n))]
+    abytes = 0
+    for p in range(P):
+        q = p // cfg.nrhs
+        abytes += alg_bytes_solve(int(A.sys_n[q]), sys_nnz[q], cfg.t, 4, 4, info["inner_steps_p"][p],
+                                  info["outer_iters_p"][p])
+    hbm, peak_src = _peaks()
     # the plain FP64 solver on the same inputs, problem by problem, on a seeded sample of problems
     rng = np.random.default_rng([0, workloads.STREAM_SAMPLE])
     sample = sorted(rng.choice(P, size=16, replace=False).tolist())
@@ -505,6 +530,10 @@ def run_batch(args, dev, stream):
             "max_outer": max(info["outer_iters_p"]), "total_inner": info["total_inner"],
             "max_rel_res_true": max(info["rel_res_true_p"]), "kernel_launches": info["kernel_launches"],
             "autotune": {"block_rows": tile[0], "spmv_vector": tile[1], "step_ms": tile[2], "tune_s": tune_s},
+            "roofline": {"bound": "hbm", "alg_bytes": abytes, "achieved": abytes / sec / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": abytes / sec / 1e9 / hbm, "peak_source": peak_src,
+                         "counted": "per problem: inner steps (A in FP32, basis FP32), z = B y per cycle, outer "
+                                    "steps (FP64 SpMV + CGS2)"},
             "plain_fp64_per_problem": {"sample_problems": sample, "sample_s": t_plain,
                                        "extrapolated_s": plain_est, "batched_speedup": plain_est / sec}}
 

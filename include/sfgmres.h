@@ -171,6 +171,7 @@ typedef struct {
     double* rel_res_est;     /* per-problem last Givens estimate */
     int64_t kernel_launches; /* kernels this call launched */
     double t_total_ms;       /* device time of the whole solve (first to last kernel) */
+    int32_t* inner_steps;    /* per-problem sum over its cycles of the inner basis size k (length problems, or NULL) */
 } sfgmres_batch_stats;
 
 typedef struct sfgmres_ctx* sfgmres_t;

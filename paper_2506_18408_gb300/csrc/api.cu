@@ -121,6 +121,14 @@ struct sfgmres_ctx {
     int bins_ver[2] = {-1, -1};
     int* lb = nullptr;  // lb_m0 [nl], lb_len [nl]
     int lb_ver = -1;
+    // the length-binned SpMV's FP64 copies of A [0] and A^T [1] with each row block's rows in its processing order
+    // (built for one geometry version; values follow sfgmres_update_values)
+    struct BCopy {
+        int* rp = nullptr;
+        int* col = nullptr;
+        double* val = nullptr;
+        int ver = -1;
+    } bc[2];
 
     // sketch gather lists (cached for one (s, zeta, kind, geometry version))
     int sk_s = -1, sk_zeta = -1, sk_kind = -1, sk_ver = -1, sk_headroom = 0;
@@ -572,6 +580,32 @@ int ensure_bins(sfgmres_ctx* h, bool transpose) {
     return 0;
 }
 
+// The length-binned SpMV's copy of A (or A^T): every row block's rows stored in the order the SpMV processes them
+// (the bins of the current geometry), FP64 values.
+int ensure_bcopy(sfgmres_ctx* h, bool transpose) {
+    const int t = transpose ? 1 : 0;
+    sfgmres_ctx::BCopy& B = h->bc[t];
+    if (B.ver == h->geo_ver && B.rp) return 0;
+    const int* rp = transpose ? h->rpT : h->rp;
+    const int* col = transpose ? h->colT : h->col;
+    const double* val = transpose ? h->valT : h->val;
+    const size_t n = (size_t)h->n, nnz = (size_t)std::max<int64_t>(h->nnz, 1);
+    if (!B.rp) {
+        CK(cudaMalloc(&B.rp, (n + 1) * sizeof(int)));
+        CK(cudaMalloc(&B.col, nnz * sizeof(int)));
+        CK(cudaMalloc(&B.val, nnz * sizeof(double)));
+    }
+    int* lens = nullptr;
+    CK(cudaMalloc(&lens, std::max<size_t>(n, 1) * sizeof(int)));
+    launch_bcopy_build(h->n, h->nl, rp, h->lb, h->lb + h->nl, h->perm[t], lens, B.rp, h->st);
+    launch_bcopy_fill(h->nl, rp, col, val, h->lb, h->lb + h->nl, h->perm[t], B.rp, B.col, B.val, h->st);
+    CK(cudaStreamSynchronize(h->st));
+    cudaFree(lens);
+    CK(cudaGetLastError());
+    B.ver = h->geo_ver;
+    return 0;
+}
+
 // SELL-32 copy of A (or A^T) for the one-thread-per-row FP64 inner SpMV (measured faster there; the FP32 inner
 // kernel keeps the CSR arrays, which measured as fast or faster); the list blocks' first slices follow the
 // row-block geometry.
@@ -641,6 +675,11 @@ void plan_geometry(sfgmres_ctx* h, const Geo* g, bool transpose, Plan& P) {
     P.vec = transpose ? (h->vec_opt ? h->vec_opt : h->vecT) : h->vec;
     P.perm = (P.vec == 0) ? h->perm[transpose ? 1 : 0] : nullptr;
     P.cls = (P.vec == 0) ? h->cls[transpose ? 1 : 0] : nullptr;
+    const sfgmres_ctx::BCopy& B = h->bc[transpose ? 1 : 0];
+    const bool bc = (P.vec == 0) && B.rp && B.ver == h->geo_ver && h->bins_ver[transpose ? 1 : 0] == h->geo_ver;
+    P.brp = bc ? B.rp : nullptr;
+    P.bcol = bc ? B.col : nullptr;
+    P.bval = bc ? B.val : nullptr;
     const sfgmres_ctx::Sell& S = h->sell[transpose ? 1 : 0];
     const bool sl = (P.vec == 1) && h->prec == kFP64 && S.off && h->sl_base_ver == h->geo_ver;
     P.sl_off = sl ? S.off : nullptr;
@@ -828,6 +867,7 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     {
         const int v = transpose ? (h->vec_opt ? h->vec_opt : h->vecT) : h->vec;
         if (v == 0 && (rc = ensure_bins(h, transpose))) return rc;
+        if (v == 0 && (rc = ensure_bcopy(h, transpose))) return rc;
         if (v == 1 && h->prec == kFP64 && (rc = ensure_sell(h, transpose))) return rc;
     }
     const size_t vt = (h->prec == kFP64) ? 8 : (h->prec == kFP32 ? 4 : 2);
@@ -1088,7 +1128,8 @@ std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
                           (const void*)P.ffom_hist, (const void*)P.ires_hist, (const void*)P.rho_hist,
                           (const void*)P.k_hist, (const void*)P.reason_hist,
                           (const void*)P.ost, (const void*)P.st, (const void*)h->qst, (const void*)P.gsync,
-                          (const void*)P.xin, (const void*)P.ilu.lu})
+                          (const void*)P.xin, (const void*)P.ilu.lu, (const void*)P.brp, (const void*)P.bcol,
+                          (const void*)P.bval})
         u(p);
     for (int64_t v : std::initializer_list<int64_t>{(int64_t)P.G, (int64_t)P.ngrp, (int64_t)P.nnz, (int64_t)P.vec, (int64_t)P.N, (int64_t)P.P, (int64_t)P.nblk, (int64_t)P.Bn,
                       (int64_t)P.s, (int64_t)P.zeta, (int64_t)P.kind, (int64_t)P.sk_headroom, (int64_t)P.prec,
@@ -1572,6 +1613,9 @@ int sfgmres_destroy(sfgmres_t h) {
         if (h->cls[t]) cudaFree(h->cls[t]);
     }
     if (h->lb) cudaFree(h->lb);
+    for (auto& B : h->bc)
+        for (void* q : {(void*)B.rp, (void*)B.col, (void*)B.val})
+            if (q) cudaFree(q);
     for (auto& S : h->sell)
         for (void* q : {(void*)S.off, (void*)S.len, (void*)S.col, (void*)S.val})
             if (q) cudaFree(q);
@@ -1768,7 +1812,10 @@ int sfgmres_solve_batch(sfgmres_t h, int32_t nrhs, const double* b, const double
             const ProbOut& o = so.pr[p];
             lock = std::max(lock, o.outer + (o.brk ? 1 : 0));
             const int cnt = std::min(o.outer + (o.brk ? 1 : 0), so.jmax);
-            for (int q = 0; q < cnt; ++q) ninner += kh[(size_t)p * so.jmax + q];
+            int64_t kp = 0;
+            for (int q = 0; q < cnt; ++q) kp += kh[(size_t)p * so.jmax + q];
+            ninner += kp;
+            if (st->inner_steps) st->inner_steps[p] = (int32_t)std::min<int64_t>(kp, INT32_MAX);
             if (st->status) st->status[p] = o.status;
             if (st->outer_iters) st->outer_iters[p] = o.outer;
             if (st->rel_res_true) st->rel_res_true[p] = o.rel_true;
@@ -1879,6 +1926,14 @@ int sfgmres_update_values(sfgmres_t h, const double* vals) {
     if (h->rpT) {
         launch_gather_vals(h->nnz, h->srcT, h->val, h->valT, h->st);
         if (h->val32T) k_to_f32<<<grid_for(h->nnz), 256, 0, h->st>>>(h->nnz, h->valT, h->val32T);
+    }
+    for (int t = 0; t < 2; ++t) {  // the length-binned copies' values
+        sfgmres_ctx::BCopy& B = h->bc[t];
+        if (B.rp && B.ver == h->geo_ver && h->perm[t])
+            launch_bcopy_fill(h->nl, t ? h->rpT : h->rp, nullptr, t ? h->valT : h->val, h->lb, h->lb + h->nl,
+                              h->perm[t], B.rp, nullptr, B.val, h->st);
+        else
+            B.ver = -1;  // rebuilt at the next use
     }
     for (int t = 0; t < 2; ++t) {  // the SELL-32 copies' values
         sfgmres_ctx::Sell& S = h->sell[t];

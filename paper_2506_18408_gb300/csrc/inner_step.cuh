@@ -238,7 +238,18 @@ __device__ __forceinline__ bool inner_spmv_part(const Plan& P, int i, const MT* 
         const int m0 = bi.v0 - bi.cs;
         int n0, n01;
         block_bins(P, bi, n0, n01);
-        spmv_rows_to_smem<V, U, MT, VT, AT>(P.rp, P.col, val, xg + bi.cs, m0, m0 + bi.len, wblk, P.perm, n0, n01);
+        if constexpr (V == 0 && sizeof(MT) == 8) {  // FP64: the copy that stores the block's rows in this order
+            if (P.brp) {
+                spmv_rows_to_smem<V, U, MT, VT, AT>(P.rp, P.bcol, reinterpret_cast<const MT*>(P.bval), xg + bi.cs,
+                                                    m0, m0 + bi.len, wblk, P.perm, n0, n01, P.brp);
+            } else {
+                spmv_rows_to_smem<V, U, MT, VT, AT>(P.rp, P.col, val, xg + bi.cs, m0, m0 + bi.len, wblk, P.perm, n0,
+                                                    n01);
+            }
+        } else {
+            spmv_rows_to_smem<V, U, MT, VT, AT>(P.rp, P.col, val, xg + bi.cs, m0, m0 + bi.len, wblk, P.perm, n0,
+                                                n01);
+        }
         __syncthreads();
         emax = dots_pass<NW>(N, bi.v0, bi.len, Ub, lo, i, wblk, W, acc, nrm);
     }

@@ -60,6 +60,11 @@ struct Plan {
     const double* sl_val = nullptr;
     const int* sl_base = nullptr;
     const uint16_t* perm = nullptr;  // length-binned SpMV: per matrix row block, its rows in length order
+    // the length-binned SpMV's FP64 copy of A with each block's rows stored in that order (null: read the CSR
+    // arrays through perm): row i of block L's order at brp[m0 + i] .. brp[m0 + i + 1] of bcol/bval
+    const int* brp = nullptr;
+    const int* bcol = nullptr;
+    const double* bval = nullptr;
     const int* cls = nullptr;        // [2 * list blocks]: rows with <= 16 entries, rows with <= 64 entries
 
     // problems and row blocks
@@ -251,6 +256,13 @@ void launch_pattern_outer(int n, const int* rp, const int* col, const double* u,
 // of rows with at most 16 and at most 64 entries.
 void launch_bin_rows(int nl, const int* rp, const int* lb_m0, const int* lb_len, uint16_t* perm, int* cls,
                      cudaStream_t st);
+// The length-binned SpMV's copy: lens [n] (scratch) and brp [n + 1] from the row order perm of every list block
+// (launch_bcopy_build), then columns (when bcol is not null) and values in that order (launch_bcopy_fill).
+void launch_bcopy_build(int n, int nl, const int* rp, const int* lb_m0, const int* lb_len, const uint16_t* perm,
+                        int* lens, int* brp, cudaStream_t st);
+void launch_bcopy_fill(int nl, const int* rp, const int* col, const double* val, const int* lb_m0,
+                       const int* lb_len, const uint16_t* perm, const int* brp, int* bcol, double* bval,
+                       cudaStream_t st);
 // SELL-32 copy of a matrix whose rows have at most 255 entries: ns slices of 32 rows, slice s covering rows
 // moff[q] + 32 (s - sl0[q]) .. of system q (sl0: first slice of each system, nsys + 1 entries).  launch_sell_build
 // writes the row lengths len[ns * 32], the slice widths wid[ns] and their prefix sums off[ns + 1] (in units of 32

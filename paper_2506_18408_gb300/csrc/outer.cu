@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(512, 2)
         const int m0 = bi.v0 - bi.cs;
         int n0, n01;
         block_bins(P, bi, n0, n01);
-        spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, x + bi.cs, m0, m0 + bi.len, axb, P.perm,
-                                                        n0, n01);
+        spmv_rows_to_smem<V, U, double, double, double>(P.rp, (V == 0 && P.brp) ? P.bcol : P.col, (V == 0 && P.brp) ? P.bval : P.val, x + bi.cs, m0, m0 + bi.len, axb, P.perm,
+                                                        n0, n01, V == 0 ? P.brp : nullptr);
         __syncthreads();
     }
     double a1 = 0.0, a2 = 0.0;
@@ -135,8 +135,8 @@ __global__ void __launch_bounds__(512, 2) k_outer_spmv(const Plan P, int j) {
     const int m0 = bi.v0 - bi.cs;
     int n0, n01;
     block_bins(P, bi, n0, n01);
-    spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, z + bi.cs, m0, m0 + bi.len, wb, P.perm, n0,
-                                                    n01);
+    spmv_rows_to_smem<V, U, double, double, double>(P.rp, (V == 0 && P.brp) ? P.bcol : P.col, (V == 0 && P.brp) ? P.bval : P.val, z + bi.cs, m0, m0 + bi.len, wb, P.perm, n0,
+                                                    n01, V == 0 ? P.brp : nullptr);
     __syncthreads();
     // the true residual of inner cycle j, r_hat_j = v_j - A z_j (v_j = nu_j Vb_j), for the bound of Eq. 5: its
     // block partial of ||r_hat_j||^2 goes to npart2 (free during outer steps)
@@ -357,8 +357,8 @@ __global__ void __launch_bounds__(512, 2)
     const int m0 = bi.v0 - bi.cs;
     int n0, n01;
     block_bins(P, bi, n0, n01);
-    spmv_rows_to_smem<V, U, double, double, double>(P.rp, P.col, P.val, x + bi.cs, m0, m0 + bi.len, yb, P.perm, n0,
-                                                    n01);
+    spmv_rows_to_smem<V, U, double, double, double>(P.rp, (V == 0 && P.brp) ? P.bcol : P.col, (V == 0 && P.brp) ? P.bval : P.val, x + bi.cs, m0, m0 + bi.len, yb, P.perm, n0,
+                                                    n01, V == 0 ? P.brp : nullptr);
     __syncthreads();
     for (int k = threadIdx.x; k < bi.len; k += blockDim.x) y[bi.v0 + k] = yb[k];
 }

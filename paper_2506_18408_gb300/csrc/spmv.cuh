@@ -126,7 +126,7 @@ template <int V, int U, int E, typename MT, typename XT, typename AT>
 __device__ __forceinline__ void spmv_sorted_vector(const int* __restrict__ rpm, const int* __restrict__ col,
                                                    const MT* __restrict__ val, const XT* __restrict__ x,
                                                    const uint16_t* __restrict__ pm, int lo, int hi,
-                                                   AT* __restrict__ out) {
+                                                   AT* __restrict__ out, const int* __restrict__ brpm) {
     constexpr int SUBS = 32 / V;
     constexpr int TILE = SUBS * U;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -142,8 +142,9 @@ __device__ __forceinline__ void spmv_sorted_vector(const int* __restrict__ rpm, 
             len[u] = 0;
             if (i < hi) {
                 kk[u] = pm[i];
-                beg[u] = __ldg(rpm + kk[u]);
-                len[u] = __ldg(rpm + kk[u] + 1) - beg[u];
+                const int* rq = brpm ? brpm + i : rpm + kk[u];  // the copy in processing order, or the CSR row
+                beg[u] = __ldg(rq);
+                len[u] = __ldg(rq + 1) - beg[u];
             }
             maxlen = max(maxlen, len[u]);
         }
@@ -185,21 +186,26 @@ __device__ __forceinline__ void spmv_sorted_vector(const int* __restrict__ rpm, 
 // one thread each: a warp's 32 rows have (nearly) the same length, so the compile-time chunk loop issues about as
 // many FMAs as there are entries and 32 rows' loads are in flight per warp.  Medium rows take 8 lanes, long rows a
 // whole warp.  Every row's sum still runs over its entries in a fixed order (per lane, then a fixed shuffle tree).
+// With brp (the copy of the matrix that stores each block's rows in this order: row i at brp[m0 + i], col and val
+// then being that copy's arrays) the rows processed together are neighbours in memory; without it the CSR rows are
+// read through pm.
 template <typename MT, typename XT, typename AT>
 __device__ __forceinline__ void spmv_rows_binned(const int* __restrict__ rp, const int* __restrict__ col,
                                                  const MT* __restrict__ val, const XT* __restrict__ x, int m0, int len,
                                                  const uint16_t* __restrict__ perm, int n0, int n01,
-                                                 AT* __restrict__ out) {
+                                                 AT* __restrict__ out, const int* __restrict__ brp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint16_t* pm = perm + m0;
     const int* rpm = rp + m0;
+    const int* brpm = brp ? brp + m0 : nullptr;
     for (int i0 = warp * 32; i0 < n0; i0 += nwarps * 32) {  // warp-uniform loop over the short rows
         const int i = i0 + lane;
         int k = -1, a = 0, rl = 0;
         if (i < n0) {
             k = pm[i];
-            a = __ldg(rpm + k);
-            rl = __ldg(rpm + k + 1) - a;
+            const int* rq = brpm ? brpm + i : rpm + k;
+            a = __ldg(rq);
+            rl = __ldg(rq + 1) - a;
         }
         const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)rl);
         AT sum = AT(0);
@@ -213,17 +219,18 @@ __device__ __forceinline__ void spmv_rows_binned(const int* __restrict__ rp, con
         }
         if (k >= 0) out[k] = sum;
     }
-    spmv_sorted_vector<8, 2, 2, MT, XT, AT>(rpm, col, val, x, pm, n0, n01, out);
-    spmv_sorted_vector<32, 2, 4, MT, XT, AT>(rpm, col, val, x, pm, n01, len, out);
+    spmv_sorted_vector<8, 2, 2, MT, XT, AT>(rpm, col, val, x, pm, n0, n01, out, brpm);
+    spmv_sorted_vector<32, 2, 4, MT, XT, AT>(rpm, col, val, x, pm, n01, len, out, brpm);
 }
 
-// V == 0: length-binned (perm, n0, n01 as for spmv_rows_binned); V == 1: one thread per row; else V lanes per row.
+// V == 0: length-binned (perm, n0, n01, brp as for spmv_rows_binned); V == 1: one thread per row; else V lanes per
+// row.
 template <int V, int U, typename MT, typename XT, typename AT>
 __device__ __forceinline__ void spmv_rows_to_smem(const int* __restrict__ rp, const int* __restrict__ col,
                                                   const MT* __restrict__ val, const XT* __restrict__ x, int r0,
                                                   int r1, AT* __restrict__ out, const uint16_t* perm = nullptr,
-                                                  int n0 = 0, int n01 = 0) {
-    if constexpr (V == 0) spmv_rows_binned<MT, XT, AT>(rp, col, val, x, r0, r1 - r0, perm, n0, n01, out);
+                                                  int n0 = 0, int n01 = 0, const int* brp = nullptr) {
+    if constexpr (V == 0) spmv_rows_binned<MT, XT, AT>(rp, col, val, x, r0, r1 - r0, perm, n0, n01, out, brp);
     else if constexpr (V == 1) spmv_rows_scalar<MT, XT, AT>(rp, col, val, x, r0, r1, out);
     else spmv_rows_vector<V, U, MT, XT, AT>(rp, col, val, x, r0, r1, out);
 }

@@ -167,6 +167,53 @@ void launch_bin_rows(int nl, const int* rp, const int* lb_m0, const int* lb_len,
     ++g_launches;
 }
 
+// ---- the length-binned SpMV's copy of a matrix: each row block's rows stored in their processing order ----
+// Row i of block L's length order (local row perm[m0 + i]) is stored at brp[m0 + i] .. brp[m0 + i + 1] of bcol/bval,
+// so the rows a warp processes together are neighbours in memory and every sector it loads is used while it is in L1
+// (in CSR order the short rows of a warp lie among rows processed at other times, which share their sectors).
+
+__global__ void k_bcopy_len(const int* __restrict__ rp, const int* __restrict__ lb_m0, const int* __restrict__ lb_len,
+                            const uint16_t* __restrict__ perm, int* __restrict__ lens) {
+    const int L = blockIdx.x;
+    const int m0 = lb_m0[L], len = lb_len[L];
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const int k = m0 + perm[m0 + i];
+        lens[m0 + i] = rp[k + 1] - rp[k];
+    }
+}
+
+// One warp per row: the row's entries copied in order (columns only when bcol is not null).
+__global__ void k_bcopy_fill(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+                             const int* __restrict__ lb_m0, const int* __restrict__ lb_len,
+                             const uint16_t* __restrict__ perm, const int* __restrict__ brp, int* __restrict__ bcol,
+                             double* __restrict__ bval) {
+    const int L = blockIdx.x;
+    const int m0 = lb_m0[L], len = lb_len[L];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < len; i += nw) {
+        const int k = m0 + perm[m0 + i];
+        const int a = rp[k], e = rp[k + 1], d = brp[m0 + i];
+        for (int p = a + lane; p < e; p += 32) {
+            if (bcol) bcol[d + (p - a)] = col[p];
+            bval[d + (p - a)] = val[p];
+        }
+    }
+}
+
+void launch_bcopy_build(int n, int nl, const int* rp, const int* lb_m0, const int* lb_len, const uint16_t* perm,
+                        int* lens, int* brp, cudaStream_t st) {
+    k_bcopy_len<<<nl, 256, 0, st>>>(rp, lb_m0, lb_len, perm, lens);
+    k_scan_plain<<<1, 1024, 0, st>>>(lens, brp, n);
+    g_launches += 2;
+}
+
+void launch_bcopy_fill(int nl, const int* rp, const int* col, const double* val, const int* lb_m0,
+                       const int* lb_len, const uint16_t* perm, const int* brp, int* bcol, double* bval,
+                       cudaStream_t st) {
+    k_bcopy_fill<<<nl, 256, 0, st>>>(rp, col, val, lb_m0, lb_len, perm, brp, bcol, bval);
+    ++g_launches;
+}
+
 // ---- SELL-32 copy of a matrix with short rows ----
 // Slice s holds rows moff[q] + 32 c .. of system q (c = s - sl0[q]); entry e of the slice's lane l sits at
 // (off[s] + e) * 32 + l, so the 32 lanes of a warp read entry e of their rows with one coalesced load.  A slice is

@@ -51,7 +51,7 @@ class BatchStats(C.Structure):
     _fields_ = [("problems", C.c_int32), ("lockstep_outer", C.c_int32), ("total_inner", C.c_int64),
                 ("status", C.POINTER(C.c_int32)), ("outer_iters", C.POINTER(C.c_int32)),
                 ("rel_res_true", C.POINTER(C.c_double)), ("rel_res_est", C.POINTER(C.c_double)),
-                ("kernel_launches", C.c_int64), ("t_total_ms", C.c_double)]
+                ("kernel_launches", C.c_int64), ("t_total_ms", C.c_double), ("inner_steps", C.POINTER(C.c_int32))]
 
 
 _lib = None
@@ -361,6 +361,8 @@ class Solver:
         oa = (C.c_int32 * P)()
         ra = (C.c_double * P)()
         ea = (C.c_double * P)()
+        ka = (C.c_int32 * P)()
+        st.inner_steps = C.cast(ka, C.POINTER(C.c_int32))
         st.status = C.cast(sa, C.POINTER(C.c_int32))
         st.outer_iters = C.cast(oa, C.POINTER(C.c_int32))
         st.rel_res_true = C.cast(ra, C.POINTER(C.c_double))
@@ -368,7 +370,8 @@ class Solver:
         rc = sfgmres_solve_batch(self.h, nrhs, b, x0, out, m, s, k, tol, SOLVE_TRANSPOSE if transpose else 0, st)
         info = {"status": rc, "problems": st.problems, "lockstep_outer": st.lockstep_outer,
                 "total_inner": st.total_inner, "status_p": list(sa), "outer_iters_p": list(oa),
-                "rel_res_true_p": list(ra), "rel_res_est_p": list(ea), "kernel_launches": st.kernel_launches,
+                "rel_res_true_p": list(ra), "rel_res_est_p": list(ea), "inner_steps_p": list(ka),
+                "kernel_launches": st.kernel_launches,
                 "t_total_ms": st.t_total_ms}
         return out, info
 

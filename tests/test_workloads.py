@@ -124,3 +124,17 @@ def test_roofline_byte_counts_match_the_per_step_figures():
     assert nblk == 288
     k1 = bench.alg_bytes_inner_spmv(n, nnz, cfg.t, cfg.zeta, cfg.s, nblk, 8)
     assert abs(k1 / 1e6 - 268.6) < 0.1
+
+
+def test_whole_solve_byte_count():
+    """bench.py's bytes of a whole solve of one problem (the batch roofline): its inner steps at the per-step count
+    (FP32 values and basis for FP32 inner cycles), z = B y once per cycle, and the outer steps; written out for a
+    problem of 2 outer steps and 10 inner steps."""
+    import bench
+
+    n, nnz, t = 1000, 4960, 2
+    step = nnz * (4 + 4) + 4 * (n + 1) + (2 * t + 3) * n * 4
+    gemv = (10 + 2) * n * 4 + 2 * 8 * n
+    outer = sum(nnz * 12 + 4 * (n + 1) + 16 * n + (4 * j + 3) * n * 8 for j in range(2))
+    assert bench.alg_bytes_solve(n, nnz, t, 4, 4, 10, 2) == 10 * step + gemv + outer
+    assert bench.alg_bytes_inner_step_prec(n, nnz, t, 8, 8) == bench.alg_bytes_inner_step(n, nnz, t, 8)
