@@ -6,7 +6,7 @@ nnz = 14,581,760; beta = (50, 30, 10); b ~ N(0,1) seed 0; inner m = 100, truncat
 nonzeros per column, seed 1; tol 1e-8), with b and A resident in HBM.  The headline is the plain FP64 solver; the
 FP32-inner and BF16-basis forms are reported beside it on the same inputs.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--profile-case [cd3d_128|zipf_2m]]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--profile-case [cd3d_128|zipf_2m|qr_cd3d]]
 
 ``--impl reference`` times the CPU oracle (plain FP64 NumPy/SciPy restatement of the method) on a bounded sample
 of the same workload.  ``--profile-case`` runs two short solves for ncu captures and prints nothing else.
@@ -187,6 +187,13 @@ def run_ours(args):
             zs.solve(zb, m=20, s=zc.s, k=zc.t, tol=zc.tol)
         torch.cuda.synchronize()
         zs.close()
+        return
+    if args.profile_case == "qr_cd3d":
+        # one full inner cycle (m = 100, C3 off: sketched-QR updates i = 0..99) of the same workload
+        solver.set("max_outer", 1)
+        solver.set("c3", 0)
+        solver.solve(bd, m=CFG.m, s=CFG.s, k=CFG.t, tol=CFG.tol, out=xd)
+        torch.cuda.synchronize()
         return
     if args.profile_case:
         # same matrix, sketch and kernels; a short basis (m = 20) and two outer steps keep the device footprint
@@ -604,7 +611,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile-case", nargs="?", const="cd3d_128", default=None,
-                    help="short solves for ncu captures: cd3d_128 (default) or zipf_2m")
+                    help="short solves for ncu captures: cd3d_128 (default), zipf_2m, or qr_cd3d (one inner cycle "
+                         "of m = 100)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve line")
     ap.add_argument("--no-others", action="store_true", help="skip the other workloads' lines")
