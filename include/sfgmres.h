@@ -77,21 +77,7 @@ extern "C" {
                                         are kept while the solve's parameters and workspaces stay the same.  0: the
                                         kernels are launched one by one.  Results are identical either way.
                                         With SFGMRES_OPT_PROFILE = 1 the timing events are part of the graphs. */
-#define SFGMRES_OPT_RHS_GROUP 11     /* sfgmres_solve_batch with nrhs > 1 on a matrix whose rows have at most 16
-                                        entries: right-hand sides of one system served by one CTA of the fused inner
-                                        SpMV, which then reads A and the sketch lists once for all of them; 1
-                                        (default, not grouped) .. 4 (3 runs as 4).  Only the order of the block
-                                        partial sums differs from 1.  On GB300 the latency-bound inner kernel runs
-                                        slower grouped (measured), hence the default. */
-#define SFGMRES_OPT_PERSISTENT 12    /* 1: for problems of at most 8 row blocks (one-thread-per-row matrices,
-                                        truncation k <= 4) each inner cycle runs as one persistent launch, a
-                                        cluster of up to 8 CTAs per problem doing every step, the least squares and
-                                        z = B y, with the reductions in distributed shared memory; a single system
-                                        of order n <= 65536 is then cut into 8 row blocks.  0 (default): one launch
-                                        per kernel and step (replayed from CUDA graphs), which measured faster on
-                                        GB300 for these sizes.  Both compute the method's sums; the order of the
-                                        cross-block sums differs.  SFGMRES_OPT_PROFILE = 1 uses the per-step
-                                        kernels. */
+/* (keys 11 and 12 are not used) */
 #define SFGMRES_OPT_FUSED_STEP 13    /* 1 (default): where all row blocks of a plan fit on the GPU at once (one system
                                         of up to about 2 x SMs blocks), the truncation window is at most 4 and the
                                         SpMV is not the FP64 length-binned one (measured slower fused), each

@@ -10,8 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libsfgmres.so")
-SOURCES = ["inner_f64.cu", "inner_f32.cu", "inner_bf16.cu", "api.cu", "inner.cu", "outer.cu", "sketch.cu", "noalloc.cu", "precond.cu", "transpose.cu",
-           "persistent.cu"]
+SOURCES = ["inner_f64.cu", "inner_f32.cu", "inner_bf16.cu", "api.cu", "inner.cu", "outer.cu", "sketch.cu", "noalloc.cu", "precond.cu", "transpose.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

@@ -43,8 +43,6 @@ struct Geo {
     DevBuf tab;  // int: blk_v0, blk_len, blk_cs, blk_list, blk_prob [nblk each], prob_b0 [P+1], pflag [P]
     uint64_t used = 0;
     int maxbp = 0;           // largest number of blocks of one problem
-    int grpG = 0, ngrp = 0;  // groups of G right-hand sides' blocks (grouped inner SpMV)
-    DevBuf grp;              // int: grp_b, grp_n, grp_st [ngrp each]
 };
 
 constexpr int kGeoCache = 4;
@@ -97,8 +95,6 @@ struct sfgmres_ctx {
     // options
     int prec = kFP64, zeta = 8, c3 = 1, max_outer = 50, kind = 0, profile = 0, vec_opt = 0, block_rows = 0;
     int use_graph = 1;
-    int persistent = 0;  // 1: whole-cycle persistent kernel where the plan allows it
-    int rhs_group = 1;  // right-hand sides per grouped inner-SpMV CTA (1: not grouped)
     int fuse_step = 1;  // 1: one launch per inner step where the row blocks fit on the GPU at once
     int outer_variant = 0;  // 0: FGMRES; 1: FFOM
     int precond = 0;        // 0: none; 1: ILU(0) in a multicolour order, right preconditioning
@@ -276,8 +272,6 @@ void set_list_geometry(sfgmres_ctx* h) {
     h->sys_l0.assign(h->nsys + 1, 0);
     int Bq;
     if (h->block_rows) Bq = h->block_rows;
-    else if (h->nsys == 1 && h->persistent && h->n <= kPersistCluster * kBlockRowsMax)
-        Bq = std::max(32, ((h->n + kPersistCluster - 1) / kPersistCluster + 31) / 32 * 32);  // one cluster's blocks
     else if (h->nsys == 1) Bq = single_block_rows(h->n, h->sms, h->prec);
     else Bq = kBatchBlockRows;
     int Bn = 32, nl = 0;
@@ -497,7 +491,6 @@ int get_geometry(sfgmres_ctx* h, int nrhs, Geo** out) {
         tab.insert(tab.end(), pb0.begin(), pb0.end());
         tab.resize(tab.size() + P, 0);  // pflag
         g->nrhs = -1;
-        g->grpG = 0;
         int rc = ensure(h, g->tab, tab.size() * sizeof(int));
         if (rc) return rc;
         CK(cudaMemcpyAsync(g->tab.p, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
@@ -706,38 +699,6 @@ void plan_geometry(sfgmres_ctx* h, const Geo* g, bool transpose, Plan& P) {
 
 int* pflag_of(const Geo* g) { return (int*)g->tab.p + 5 * (int64_t)g->nblk + g->P + 1; }
 
-// Groups of row blocks for the grouped inner SpMV: for every system and every matrix row block, the blocks of
-// right-hand sides r0 .. r0+G-1 (block index stride = the system's blocks per right-hand side).
-int ensure_groups(sfgmres_ctx* h, Geo* g, int G) {
-    if (g->grpG == G) return 0;
-    const int R = g->nrhs;
-    std::vector<int> gbv, gnv, gsv;
-    for (int q = 0; q < h->nsys; ++q) {
-        const int nlq = (h->sys_n[q] + h->sys_Bq[q] - 1) / h->sys_Bq[q];
-        // blocks of problem (q, r) start at prob_b0[q*R + r] = base_q + r * nlq
-        int base = 0;
-        for (int q2 = 0; q2 < q; ++q2) base += R * ((h->sys_n[q2] + h->sys_Bq[q2] - 1) / h->sys_Bq[q2]);
-        for (int r0 = 0; r0 < R; r0 += G)
-            for (int k = 0; k < nlq; ++k) {
-                gbv.push_back(base + r0 * nlq + k);
-                gnv.push_back(std::min(G, R - r0));
-                gsv.push_back(nlq);
-            }
-    }
-    std::vector<int> tab;
-    tab.insert(tab.end(), gbv.begin(), gbv.end());
-    tab.insert(tab.end(), gnv.begin(), gnv.end());
-    tab.insert(tab.end(), gsv.begin(), gsv.end());
-    g->grpG = 0;
-    int rc = ensure(h, g->grp, tab.size() * sizeof(int));
-    if (rc) return rc;
-    CK(cudaMemcpyAsync(g->grp.p, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    g->grpG = G;
-    g->ngrp = (int)gbv.size();
-    return 0;
-}
-
 // Allocates the workspaces of a solve with nrhs right-hand sides per system and fills a Plan (for A, or for A^T
 // when transpose is set).  Every problem's flag is reset to "active".
 // ---- ILU(0) right preconditioner (set-up; the kernels are in precond.cu) ----
@@ -926,22 +887,6 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
 
     Plan& P = *p;
     plan_geometry(h, g, transpose, P);
-    // grouped inner SpMV for several right-hand sides of one-thread-per-row matrices
-    int G = 1;
-    if (nrhs > 1 && P.vec == 1 && h->rhs_group > 1) {
-        G = h->rhs_group;
-        G = std::min(G, nrhs);
-        if (G > 2) G = 4;  // kernels exist for groups of 2 and 4 (a group may hold fewer members)
-    }
-    if (G > 1) {
-        if ((rc = ensure_groups(h, g, G))) return rc;
-        const int* gt = (const int*)g->grp.p;
-        P.G = G;
-        P.ngrp = g->ngrp;
-        P.grp_b = gt;
-        P.grp_n = gt + g->ngrp;
-        P.grp_st = gt + 2 * (int64_t)g->ngrp;
-    }
     P.s = s;
     P.zeta = h->sk_zeta;
     P.kind = h->kind;
@@ -1059,24 +1004,10 @@ double ev_sum(const std::vector<EventPair>& pool, size_t base, size_t count) {
 // configured), j < 0 standalone.  The sketched-QR update of step i runs on the side stream after step i's sketch
 // column is ready, overlapping the next step's SpMV; the main stream waits for the last QR update before the
 // least-squares solve.
-// Cluster size of the whole-cycle persistent kernel for this plan, or 0 where the per-step kernels run: small problems
-// (at most kPersistCluster row blocks each) with one thread per row and t <= 4, not profiled.
-int persistent_cluster(const sfgmres_ctx* h, const Plan& P) {
-    if (!h->persistent || h->profile || P.ilu_host || P.vec != 1 || P.t > 4 || P.maxbp < 1 ||
-        P.maxbp > kPersistCluster)
-        return 0;
-    if (persistent_smem(P, P.maxbp) > 200 * 1024) return 0;
-    return P.maxbp;
-}
-
 // ev: base event pair of this cycle's launches (profiling), or SIZE_MAX; capturing: inside a stream capture.
 int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const double* vscale, int vstride, int c3,
               double* z, size_t ev = SIZE_MAX, bool capturing = false) {
     launch_cycle_start(P, j, v, vscale, vstride, c3, h->cond_thr);
-    if (const int nq = persistent_cluster(h, P)) {
-        CK(launch_cycle_persistent(P, nq, z));
-        return 0;
-    }
     const bool prof = (ev != SIZE_MAX);
     h->step_fused = false;
     for (int i = 0; i < P.m; ++i) {
@@ -1114,7 +1045,7 @@ int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const doubl
 std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
     std::vector<uint64_t> k;
     auto u = [&](const void* p) { k.push_back((uint64_t)(uintptr_t)p); };
-    for (const void* p : std::initializer_list<const void*>{(const void*)P.grp_b, (const void*)P.perm, (const void*)P.cls,
+    for (const void* p : std::initializer_list<const void*>{(const void*)P.perm, (const void*)P.cls,
                                                             (const void*)P.rp, (const void*)P.col, (const void*)P.val, (const void*)P.val32,
                           (const void*)P.blk_v0, (const void*)P.seg, (const void*)P.sl_off, (const void*)P.sl_col,
                           (const void*)P.sl_val, (const void*)P.sl_base, (const void*)P.sl_len, (const void*)P.ent, P.U, P.W,
@@ -1131,7 +1062,7 @@ std::vector<uint64_t> plan_key(const sfgmres_ctx* h, const Plan& P) {
                           (const void*)P.xin, (const void*)P.ilu.lu, (const void*)P.brp, (const void*)P.bcol,
                           (const void*)P.bval})
         u(p);
-    for (int64_t v : std::initializer_list<int64_t>{(int64_t)P.G, (int64_t)P.ngrp, (int64_t)P.nnz, (int64_t)P.vec, (int64_t)P.N, (int64_t)P.P, (int64_t)P.nblk, (int64_t)P.Bn,
+    for (int64_t v : std::initializer_list<int64_t>{(int64_t)P.nnz, (int64_t)P.vec, (int64_t)P.N, (int64_t)P.P, (int64_t)P.nblk, (int64_t)P.Bn,
                       (int64_t)P.s, (int64_t)P.zeta, (int64_t)P.kind, (int64_t)P.sk_headroom, (int64_t)P.prec,
                       (int64_t)P.m, (int64_t)P.t, (int64_t)P.qr_cluster, (int64_t)P.jmax, (int64_t)h->c3,
                       (int64_t)h->profile, (int64_t)P.gwait_extra, (int64_t)P.outer_variant})
@@ -1165,7 +1096,7 @@ int outer_step(sfgmres_ctx* h, const Plan& P, int j) {
         launch_outer_step(P, j);
         return 0;
     };
-    const bool prof = h->profile && !persistent_cluster(h, P);
+    const bool prof = h->profile != 0;
     auto take_events = [&](size_t& ev) -> int {
         ev = SIZE_MAX;
         if (!prof) return 0;
@@ -1637,7 +1568,6 @@ int sfgmres_destroy(sfgmres_t h) {
             release(*b);
     for (Geo& g : h->geos) {
         release(g.tab);
-        release(g.grp);
     }
     drop_graphs(h);
     release_host(h->h_ost);
@@ -1702,17 +1632,6 @@ int sfgmres_set_option(sfgmres_t h, int32_t key, double v) {
             h->vec_opt = iv;
             h->vec = iv ? iv : choose_vec(h->nnz, h->n, h->maxlen);
             return 0;
-        case SFGMRES_OPT_RHS_GROUP:
-            if (iv != v || iv < 1 || iv > 4) return fail(h, SFGMRES_ERR_INVALID_ARG, "rhs group must be 1..4");
-            h->rhs_group = iv;
-            return 0;
-        case SFGMRES_OPT_PERSISTENT:
-            if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "persistent must be 0 or 1");
-            if (iv != h->persistent) {
-                h->persistent = iv;
-                set_list_geometry(h);
-            }
-            return 0;
         case SFGMRES_OPT_FUSED_STEP:
             if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "fused step must be 0 or 1");
             h->fuse_step = iv;
@@ -1759,8 +1678,6 @@ int sfgmres_get_option(sfgmres_t h, int32_t key, double* v) {
         case SFGMRES_OPT_SPMV_VECTOR: *v = h->vec; return 0;
         case SFGMRES_OPT_BLOCK_ROWS: *v = h->sys_Bq.empty() ? 0 : h->sys_Bq[0]; return 0;
         case SFGMRES_OPT_GRAPH: *v = h->use_graph; return 0;
-        case SFGMRES_OPT_RHS_GROUP: *v = h->rhs_group; return 0;
-        case SFGMRES_OPT_PERSISTENT: *v = h->persistent; return 0;
         case SFGMRES_OPT_FUSED_STEP: *v = h->fuse_step; return 0;
         case SFGMRES_OPT_STEP_WAIT_EXTRA: *v = h->wait_extra; return 0;
         case SFGMRES_OPT_OUTER_VARIANT: *v = h->outer_variant; return 0;

@@ -245,38 +245,6 @@ __device__ __forceinline__ T sum_list(const uint16_t* __restrict__ ent, int a, i
     return acc;
 }
 
-// Grouped form for G vectors held in shared memory at x + j * stride (members with bit j of act): the list is read
-// once and every member's sum is formed exactly as sum_list forms it (eight-entry partial sums added in list order).
-template <int G, typename T>
-__device__ __forceinline__ void sum_list_g(const uint16_t* __restrict__ ent, int a, int e, const T* __restrict__ x,
-                                           int stride, unsigned act, T (&acc)[G]) {
-    const uint4* p = reinterpret_cast<const uint4*>(ent + a);
-    const int ng = (e - a) >> 3;
-#pragma unroll
-    for (int j = 0; j < G; ++j) acc[j] = T(0);
-    for (int g = 0; g < ng; ++g) {
-        const uint4 d = __ldg(p + g);
-        const unsigned w[4] = {d.x, d.y, d.z, d.w};
-        T part[G];
-#pragma unroll
-        for (int j = 0; j < G; ++j) part[j] = T(0);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const unsigned en = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-            const int off = (int)(en & 0x7fffu);
-#pragma unroll
-            for (int j = 0; j < G; ++j) {
-                if (act & (1u << j)) {
-                    const T v = x[j * stride + off];
-                    part[j] += (en & 0x8000u) ? -v : v;
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < G; ++j) acc[j] += part[j];
-    }
-}
-
 // ------------------------------------------------------------------------------------------------------------
 // Device-resident solver state (one instance per handle).
 struct CycleState {

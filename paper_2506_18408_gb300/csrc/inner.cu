@@ -389,7 +389,7 @@ void launch_inner_spmv(const Plan& p, int i) {
 }
 
 bool launch_inner_step(const Plan& p, int i, bool last) {
-    if (p.G > 1 || !p.gsync) return false;
+    if (!p.gsync) return false;
     bool ok;
     if (p.prec == kFP64) ok = inner_step_f64(p, i, last);
     else if (p.prec == kFP32) ok = inner_step_f32(p, i, last);

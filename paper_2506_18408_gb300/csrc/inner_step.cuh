@@ -330,203 +330,6 @@ __global__ void __maxnreg__(56) k_inner_spmv(const Plan P, int i, const MT* __re
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// Grouped form of k_inner_spmv for matrices with short rows (one thread per row): one CTA serves the same row block
-// of up to G problems that are right-hand sides of one system (the group's member blocks), so the CSR entries, the
-// row pointers and the sketch gather lists are read once for all members.  Each member gets what k_inner_spmv
-// computes for its block: w' stored, window dots and ||u_i||^2 partials (block sums formed warp by warp), and the
-// per-block sketch partials.  Members whose cycle has stopped are skipped.
-template <int CNT, int G, typename MT, typename XT, typename AT>
-__device__ __forceinline__ void row_chunk_g(const int* __restrict__ col, const MT* __restrict__ val,
-                                            const XT* __restrict__ x, int dn, unsigned act, int a, int len, int pk,
-                                            AT (&sum)[G]) {
-    int c[CNT];
-    AT v[CNT];
-#pragma unroll
-    for (int q = 0; q < CNT; ++q) {
-        if (pk + q < len) {
-            c[q] = __ldg(col + a + pk + q);
-            v[q] = (AT)__ldg(val + a + pk + q);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < G; ++j) {
-        if (act & (1u << j)) {
-#pragma unroll
-            for (int q = 0; q < CNT; ++q)
-                if (pk + q < len) sum[j] += v[q] * load_as(x + j * dn + c[q], AT());
-        }
-    }
-}
-
-template <int G, int NW, typename MT, typename VT, typename AT>
-__global__ void __maxnreg__(sizeof(AT) == 8 ? 64 : 56) k_inner_spmv_grp(const Plan P, int i, const MT* __restrict__ val) {
-    constexpr int NV = NW + 1;  // reduced values per member: ||u_i||^2 and the window dots
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ AT red[G * NV][16];
-    __shared__ int emax_sh[G][16];
-    __shared__ int mb_sh[G], mv0_sh[G], mcs_sh[G];
-    __shared__ unsigned act_sh;
-    const int gi = blockIdx.x;
-    const int gb = P.grp_b[gi], gn = P.grp_n[gi], gst = P.grp_st[gi];
-    if (threadIdx.x < G) {
-        const int j = threadIdx.x;
-        const int b = gb + min(j, gn - 1) * gst;
-        mb_sh[j] = b;
-        mv0_sh[j] = P.blk_v0[b];
-        mcs_sh[j] = P.blk_cs[b];
-    }
-    if (threadIdx.x == 0) {
-        unsigned a = 0;
-        for (int j = 0; j < gn; ++j)
-            if (!cycle_idle(P, P.blk_prob[gb + j * gst], i)) a |= 1u << j;
-        act_sh = a;
-    }
-    __syncthreads();
-    const unsigned act = act_sh;
-    if (!act) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int s = P.s, Bn = P.Bn, N = P.N, SB = Bn + 1;
-    const int len = P.blk_len[gb], list = P.blk_list[gb];
-    const int m0 = mv0_sh[0] - mcs_sh[0];
-    const VT* Ub = (const VT*)P.U;
-    AT* W = (AT*)P.W;
-    AT* wb = reinterpret_cast<AT*>(smem_raw);  // member j: wb[j * SB .. j * SB + Bn]
-    const int lo = i - NW + 1;
-    // members are consecutive right-hand sides of one system: their vector rows are dn apart
-    const int dn = (gn > 1) ? mv0_sh[1] - mv0_sh[0] : 0;
-    const int v00 = mv0_sh[0];
-    const VT* xs = Ub + (int64_t)i * N + mcs_sh[0];
-    AT acc[G][NW > 0 ? NW : 1], nrm[G];
-    int emax[G];
-#pragma unroll
-    for (int j = 0; j < G; ++j) {
-        nrm[j] = AT(0);
-        emax[j] = 1;
-#pragma unroll
-        for (int q = 0; q < NW; ++q) acc[j][q] = AT(0);
-    }
-    const int* rpm = P.rp + m0;
-    int kw = threadIdx.x & ~31;
-    int a = 0, rl = 0;
-    if (kw + lane < len) {
-        a = __ldg(rpm + kw + lane);
-        rl = __ldg(rpm + kw + lane + 1) - a;
-    }
-    for (; kw < len; kw += blockDim.x) {  // warp-uniform loop over the block's rows
-        const int k = kw + lane;
-        const bool ok = k < len;
-        const int kn = k + (int)blockDim.x;
-        int an = 0, rln = 0;
-        if (kn < len) {
-            an = __ldg(rpm + kn);
-            rln = __ldg(rpm + kn + 1) - an;
-        }
-        const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)rl);
-        AT sum[G];
-#pragma unroll
-        for (int j = 0; j < G; ++j) sum[j] = AT(0);
-        for (int pk = 0; pk < maxlen; pk += 4) {
-            switch (min(maxlen - pk, 4)) {
-                case 1: row_chunk_g<1, G>(P.col, val, xs, dn, act, a, rl, pk, sum); break;
-                case 2: row_chunk_g<2, G>(P.col, val, xs, dn, act, a, rl, pk, sum); break;
-                case 3: row_chunk_g<3, G>(P.col, val, xs, dn, act, a, rl, pk, sum); break;
-                default: row_chunk_g<4, G>(P.col, val, xs, dn, act, a, rl, pk, sum); break;
-            }
-        }
-        // window values after the SpMV (fewer live registers than prefetching them for every member)
-#pragma unroll
-        for (int j = 0; j < G; ++j) {
-            if (act & (1u << j)) {
-                const int r = v00 + j * dn + k;
-                if (ok) {
-                    W[r] = sum[j];
-                    wb[j * SB + k] = sum[j];
-                }
-                AT ui = AT(0);
-#pragma unroll
-                for (int q = 0; q < NW; ++q) {
-                    const AT u = ok ? ld_plain(Ub + (int64_t)(lo + q) * N + r) : AT(0);
-                    acc[j][q] += u * sum[j];
-                    ui = u;
-                }
-                if constexpr (NW == 0) ui = ok ? ld_plain(Ub + (int64_t)i * N + r) : AT(0);
-                nrm[j] += ui * ui;
-                emax[j] = max(emax[j], exp_of(sum[j]));
-            }
-        }
-        a = an;
-        rl = rln;
-    }
-    // block sums (warp by warp, then the warps' partials in order) of ||u_i||^2 and the window dots
-#pragma unroll
-    for (int j = 0; j < G; ++j) {
-        if (act & (1u << j)) {
-            const AT v = warp_sum(nrm[j]);
-            if (lane == 0) red[j * NV][warp] = v;
-#pragma unroll
-            for (int q = 0; q < NW; ++q) {
-                const AT d = warp_sum(acc[j][q]);
-                if (lane == 0) red[j * NV + 1 + q][warp] = d;
-            }
-            if constexpr (sizeof(AT) == 8) {
-                const int e = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax[j]);
-                if (lane == 0) emax_sh[j][warp] = e;
-            }
-            if (threadIdx.x == 0) wb[j * SB + Bn] = AT(0);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < G * NV) {
-        const int j = threadIdx.x / NV, v = threadIdx.x % NV;
-        if (act & (1u << j)) {
-            AT t = AT(0);
-            for (int w = 0; w < nw; ++w) t += red[threadIdx.x][w];
-            const int b = mb_sh[j];
-            if (v == 0) ((AT*)P.normpart)[b] = t;
-            else ((AT*)P.hpart)[(int64_t)b * kMaxTrunc + v - 1] = t;
-        }
-    }
-    const int* sg = P.seg + (int64_t)list * s;
-    AT* cpart = (AT*)P.cpart;
-    if constexpr (sizeof(AT) == 8) {
-        // exact fixed-point sketch sums per member (relative to the member's block maximum)
-        long long* qb = reinterpret_cast<long long*>(wb);
-        const int H = P.sk_headroom;
-        int Eb[G];
-#pragma unroll
-        for (int j = 0; j < G; ++j) {
-            Eb[j] = 1;
-            if (act & (1u << j))
-                for (int q = 0; q < nw; ++q) Eb[j] = max(Eb[j], emax_sh[j][q]);
-        }
-#pragma unroll
-        for (int j = 0; j < G; ++j)
-            if (act & (1u << j))
-                for (int r = threadIdx.x; r <= Bn; r += blockDim.x)
-                    qb[j * SB + r] = (r < len) ? to_fixed((double)wb[j * SB + r], Eb[j], H) : 0;
-        __syncthreads();
-        for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
-            long long sums[G];
-            sum_list_g<G>(P.ent, sg[rr], sg[rr + 1], qb, SB, act, sums);
-#pragma unroll
-            for (int j = 0; j < G; ++j)
-                if (act & (1u << j))
-                    cpart[(int64_t)mb_sh[j] * s + rr] =
-                        exp_nonfinite(0.0, Eb[j]) ? (AT)NAN : (AT)((double)sums[j] * fixed_unit(0.0, Eb[j], H));
-        }
-    } else {
-        __syncthreads();
-        for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
-            AT sums[G];
-            sum_list_g<G>(P.ent, sg[rr], sg[rr + 1], wb, SB, act, sums);
-#pragma unroll
-            for (int j = 0; j < G; ++j)
-                if (act & (1u << j)) cpart[(int64_t)mb_sh[j] * s + rr] = sums[j];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------------------------------------------
 // Waits until the grid counter reaches target (acquire), polling with a growing sleep; after kGridWaitPolls polls it
 // gives up and sets *fail.  Once a wait of the cycle has given up, later ones return at once.
 constexpr int kGridWaitPolls = 1 << 20;  // about a second of polls (256 ns sleeps plus an L2 round trip each)
@@ -964,32 +767,9 @@ static void inner_spmv_nw(const Plan& p, int i, const MT* val) {
     else inner_spmv_v<32, 2, NW, MT, VT, AT>(p, i, val);
 }
 
-template <int G, int NW, typename MT, typename VT, typename AT>
-static void inner_spmv_g(const Plan& p, int i, const MT* val) {
-    const size_t sm = (size_t)G * (p.Bn + 1) * sizeof(AT);
-    set_smem((const void*)k_inner_spmv_grp<G, NW, MT, VT, AT>, sm);
-    k_inner_spmv_grp<G, NW, MT, VT, AT><<<p.ngrp, 512, sm, p.st>>>(p, i, val);
-}
-
-template <int NW, typename MT, typename VT, typename AT>
-static void inner_spmv_gsel(const Plan& p, int i, const MT* val) {
-    if (p.G == 2) inner_spmv_g<2, NW, MT, VT, AT>(p, i, val);
-    else inner_spmv_g<4, NW, MT, VT, AT>(p, i, val);
-}
-
 template <typename MT, typename VT, typename AT>
 static void inner_spmv_t(const Plan& p, int i, const MT* val) {
     const int nwin = (p.t > 0) ? std::min(p.t, i + 1) : 0;
-    if (p.G > 1) {  // grouped right-hand sides (one thread per row); windows above 4 are not grouped
-        switch (nwin) {
-            case 0: inner_spmv_gsel<0, MT, VT, AT>(p, i, val); return;
-            case 1: inner_spmv_gsel<1, MT, VT, AT>(p, i, val); return;
-            case 2: inner_spmv_gsel<2, MT, VT, AT>(p, i, val); return;
-            case 3: inner_spmv_gsel<3, MT, VT, AT>(p, i, val); return;
-            case 4: inner_spmv_gsel<4, MT, VT, AT>(p, i, val); return;
-            default: break;
-        }
-    }
     switch (nwin) {
         case 0: inner_spmv_nw<0, MT, VT, AT>(p, i, val); break;
         case 1: inner_spmv_nw<1, MT, VT, AT>(p, i, val); break;

@@ -80,15 +80,9 @@ struct Plan {
     const int* prob_b0 = nullptr;  // [P+1] blocks of problem p: prob_b0[p] .. prob_b0[p+1]
     int maxbp = 0;                 // largest number of blocks of one problem
     const int* pflag = nullptr;    // [P] bit 0: done (skip), bit 1: finalise now
-    // groups of row blocks that are the same matrix rows of G right-hand sides of one system (the grouped inner
-    // SpMV reads A and the gather lists once per group): members grp_b[g] + j * grp_st[g], j < grp_n[g]
-    int G = 1, ngrp = 0;
     int sms = 0;                   // SMs of the device (one-wave test of the fused step)
     unsigned long long* gsync = nullptr;  // fused step: [0], [2] grid arrival counters (reset per cycle), [1] a wait gave up
     int gwait_extra = 0;           // fused step: arrivals waited for beyond the launch's blocks (0; > 0 tests give-up)
-    const int* grp_b = nullptr;
-    const int* grp_n = nullptr;
-    const int* grp_st = nullptr;
 
     // sketch: for list block L and sketch row r the list ent[seg[L*s + r] .. seg[L*s + r + 1])
     int s = 0, zeta = 0, kind = 0;
@@ -225,14 +219,6 @@ cudaError_t launch_ilu_factor(const IluHost& H, const double* val, int* bad, cud
 // out = M^{-1} u = P^T (L U)^{-1} P u in the original order (u and out n float64, distinct); i >= 0: step i of the
 // plan's cycle (the passes return at once once the cycle has stopped), i < 0: always
 void launch_ilu_apply(const Plan& P, int i, const double* u, double* out);
-
-// ---- persistent cycle (persistent.cu) ----
-// The whole inner cycle (all steps, least squares and z = B y) in one launch, one cluster of nq CTAs per problem
-// (nq = the largest number of row blocks of a problem, at most kPersistCluster); for plans with one thread per row
-// and t <= 4.
-constexpr int kPersistCluster = 8;
-size_t persistent_smem(const Plan& p, int nq);
-cudaError_t launch_cycle_persistent(const Plan& p, int nq, double* z);
 
 // ---- outer FGMRES and helpers (outer.cu) ----
 // rb = b - A x (x may be NULL = 0), npart/npart2 partials of ||rb||^2 and ||b||^2; rb may be NULL.

@@ -23,8 +23,8 @@ OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NAN = -1, -2, -3, -4
 CSR_HOST = 1
 OPT_PRECISION, OPT_ZETA, OPT_COND_THRESHOLD, OPT_C3, OPT_MAX_OUTER, OPT_SKETCH_KIND, OPT_PROFILE, \
-    OPT_SPMV_VECTOR, OPT_BLOCK_ROWS, OPT_GRAPH, OPT_RHS_GROUP, OPT_PERSISTENT, OPT_FUSED_STEP, \
-    OPT_STEP_WAIT_EXTRA, OPT_OUTER_VARIANT, OPT_PRECOND = range(1, 17)
+    OPT_SPMV_VECTOR, OPT_BLOCK_ROWS, OPT_GRAPH = range(1, 11)
+OPT_FUSED_STEP, OPT_STEP_WAIT_EXTRA, OPT_OUTER_VARIANT, OPT_PRECOND = range(13, 17)
 SOLVE_TRANSPOSE = 1
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 SKETCH_KIND = {"sparse_sign": 0, "identity": 1}
@@ -269,7 +269,6 @@ class Solver:
     _KEYS = {"precision": OPT_PRECISION, "zeta": OPT_ZETA, "cond_threshold": OPT_COND_THRESHOLD, "c3": OPT_C3,
              "max_outer": OPT_MAX_OUTER, "sketch_kind": OPT_SKETCH_KIND, "profile": OPT_PROFILE,
              "spmv_vector": OPT_SPMV_VECTOR, "block_rows": OPT_BLOCK_ROWS, "graph": OPT_GRAPH,
-             "rhs_group": OPT_RHS_GROUP, "persistent": OPT_PERSISTENT,
              "fused_step": OPT_FUSED_STEP, "step_wait_extra": OPT_STEP_WAIT_EXTRA,
              "outer_variant": OPT_OUTER_VARIANT, "precond": OPT_PRECOND}
 

@@ -224,52 +224,6 @@ def test_autotune_picks_a_valid_shape_and_solves_stay_correct(small):
     assert iz["status"] == 0 and _rel_res(Z, bz, xz.cpu().numpy()) <= 1e-8
 
 
-@pytest.mark.parametrize("group,prec", [(2, "fp64"), (4, "fp32")])
-def test_rhs_grouped_inner_spmv_matches_ungrouped(small, group, prec):
-    """The grouped inner SpMV (several right-hand sides of a system per CTA) changes only the order of block partial
-    sums: the same outer counts and solutions agreeing far below the solve tolerance."""
-    cfg, A, b = small
-    sv = _solver(A, max_outer=cfg.max_outer, precision=prec)
-    x1, i1 = sv.solve_batch(dev_vec(b), nrhs=cfg.nrhs, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
-    sv.set("rhs_group", group)
-    x2, i2 = sv.solve_batch(dev_vec(b), nrhs=cfg.nrhs, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
-    assert i2["status"] == 0
-    assert all(abs(a - c) <= 1 for a, c in zip(i1["outer_iters_p"], i2["outer_iters_p"]))
-    x1, x2 = x1.cpu().numpy(), x2.cpu().numpy()
-    assert np.linalg.norm(x1 - x2) <= 1e-6 * np.linalg.norm(x1)
-    for Aq, bp, xp in _per_problem(A, cfg.nrhs, b, x2):
-        assert _rel_res(Aq, bp, xp) <= cfg.tol
-
-
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_persistent_cycle_matches_per_step_kernels(small, prec):
-    """The whole-cycle persistent kernel (one launch per inner cycle, a cluster per problem) computes the method's
-    steps with the per-step kernels' arithmetic (only the order of cross-block sums differs): the same outer counts
-    within one step, the same inner lengths on the single system, and solutions far inside the tolerance."""
-    from paper_2506_18408_gb300 import Solver
-
-    A2 = workloads.convdiff(64, (20.0, 10.0))
-    b2 = workloads.rhs(A2.n, seed=0)
-    out = {}
-    for pers in (1, 0):
-        sv = Solver(A2.n, A2.row_ptr, A2.col, A2.val, sketch_seed=1, max_outer=20, precision=prec, persistent=pers)
-        x, info = sv.solve(dev_vec(b2), m=30, s=120, k=2, tol=1e-8)
-        assert info["status"] == 0 and _rel_res(A2, b2, x.cpu().numpy()) <= 1e-8
-        out[pers] = (x.cpu().numpy(), info)
-    assert abs(out[1][1]["outer_iters"] - out[0][1]["outer_iters"]) <= 1
-    assert np.linalg.norm(out[1][0] - out[0][0]) <= 1e-6 * np.linalg.norm(out[0][0])
-    cfg, A, b = small
-    res = {}
-    for pers in (1, 0):
-        sv = _solver(A, max_outer=cfg.max_outer, precision=prec, persistent=pers)
-        x, info = sv.solve_batch(dev_vec(b), nrhs=cfg.nrhs, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol)
-        assert info["status"] == 0
-        res[pers] = (x.cpu().numpy(), info)
-        for Aq, bp, xp in _per_problem(A, cfg.nrhs, b, res[pers][0]):
-            assert _rel_res(Aq, bp, xp) <= cfg.tol
-    assert all(abs(a - c) <= 1 for a, c in zip(res[1][1]["outer_iters_p"], res[0][1]["outer_iters_p"]))
-
-
 def test_profiled_solves_time_the_working_launches_with_and_without_graphs():
     """Profiling puts the kernel timing events into the captured graphs: a profiled solve gives the same result as an
     unprofiled one, with graphs (captured, then replayed) and without, and counts exactly the inner steps that built
