@@ -127,7 +127,7 @@ struct sfgmres_ctx {
     } bc[2];
 
     // sketch gather lists (cached for one (s, zeta, kind, geometry version))
-    int sk_s = -1, sk_zeta = -1, sk_kind = -1, sk_ver = -1, sk_headroom = 0;
+    int sk_s = -1, sk_zeta = -1, sk_kind = -1, sk_ver = -1, sk_headroom = 0, sk_word = 0;
     int* seg = nullptr;
     uint16_t* ent = nullptr;
 
@@ -395,7 +395,10 @@ int grid_for(int64_t n, int th = 256) { return (int)std::max<int64_t>(1, std::mi
 // Gather lists of every system's sketch for s rows (one pattern per system, all drawn from the handle's seed).
 int build_sketch(sfgmres_ctx* h, int s) {
     const int zeta = (h->kind == 1) ? 1 : h->zeta;
-    if (h->seg && h->sk_s == s && h->sk_zeta == zeta && h->sk_kind == h->kind && h->sk_ver == h->geo_ver) return 0;
+    const int word = (h->prec == kFP64) ? 8 : 4;  // the summed words: FP64 fixed-point image, or FP32 data
+    if (h->seg && h->sk_s == s && h->sk_zeta == zeta && h->sk_kind == h->kind && h->sk_ver == h->geo_ver &&
+        h->sk_word == word)
+        return 0;
     if (h->seg) cudaFree(h->seg);
     if (h->ent) cudaFree(h->ent);
     h->seg = nullptr;
@@ -433,6 +436,14 @@ int build_sketch(sfgmres_ctx* h, int s) {
         launch_sketch_fill(h->sys_n[q], s, zeta, h->sys_Bq[q], rows, neg, h->seg + (int64_t)h->sys_l0[q] * s,
                            h->ent, h->st);
     }
+    {
+        const int G = 128 / word;
+        int max_group = 0;
+        for (int64_t k = 0; k < h->nl; ++k)
+            for (int r0 = 0; r0 < s; r0 += G)
+                max_group = std::max(max_group, hs[k * s + std::min(s, r0 + G)] - hs[k * s + r0]);
+        launch_sketch_schedule(h->nl, s, word, max_group, h->seg, h->ent, h->st);
+    }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->st));
     cudaFree(rows);
@@ -450,6 +461,7 @@ int build_sketch(sfgmres_ctx* h, int s) {
     h->sk_s = s;
     h->sk_zeta = zeta;
     h->sk_kind = h->kind;
+    h->sk_word = word;
     h->sk_ver = h->geo_ver;
     return 0;
 }

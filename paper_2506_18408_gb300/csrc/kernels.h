@@ -182,6 +182,11 @@ void launch_list_scan(const int* counts, int* seg, int len, cudaStream_t st);
 void launch_sketch_fill(int n, int s, int zeta, int Bq, const int* rows, const int8_t* neg, const int* seg,
                         uint16_t* ent, cudaStream_t st);
 void launch_fill_u16(int64_t cnt, uint16_t v, uint16_t* out, cudaStream_t st);
+// Reorders the entries within every list of the nl list blocks for the shared-memory banks of the kernels that sum
+// them (word = 8: the FP64 fixed-point image, 4: FP32 data); max_group = the largest number of entries of G = 128 /
+// word consecutive lists (G aligned) of one block (above 80K entries the lists keep their fill order).  After the
+// fill, before any use of the lists.
+void launch_sketch_schedule(int nl, int s, int word, int max_group, const int* seg, uint16_t* ent, cudaStream_t st);
 // part[b*s + r] = per-block sketch sums of (scale_p * x) with scale_p = xscale[p * xstride] (1 if xscale is NULL);
 // optionally stores (VT)(scale_p * x) into dst.  Skips done problems.
 void launch_sketch_partials(const Plan& p, const double* x, const double* xscale, int xstride, void* dst,

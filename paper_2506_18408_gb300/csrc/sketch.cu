@@ -8,6 +8,7 @@
 #include "kernels.h"
 
 #include <algorithm>
+#include <climits>
 #include <mutex>
 #include <unordered_map>
 
@@ -114,6 +115,87 @@ __global__ void k_seg_fill(int n, int s, int zeta, int Bq, const int* __restrict
             __syncwarp();
         }
     }
+}
+
+// Reorders the entries within each gather list for the shared-memory banks.  The lists of G consecutive sketch rows
+// (G aligned) are summed in lockstep by G lanes that share one shared-memory wavefront -- entry e of every list at
+// step e -- and two lanes whose entries at a step lie in the same bank (offset mod G, for words of 128/G bytes: G = 16
+// for the FP64 fixed-point image, read in half-warps, 32 for FP32 data) serialise.  Each CTA takes one such group of
+// one row block: its lists are bucketed by residue (stably, in shared memory), then step by step the lanes, in an
+// order rotating with the step, each take the next entry of the residue that is least used at this step so far
+// (ties: the lane's fullest bucket, then the lowest residue).  Only the order within a list changes, and it is a
+// fixed function of the list contents, so the sums stay reproducible (the FP64 ones are exact in any order).
+template <int G>
+__global__ void k_seg_schedule(int nl, int s, const int* __restrict__ seg, uint16_t* __restrict__ ent) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int cnt[G * G], pos[G * G], cur[G * G], rem[G], outp[G];
+    uint16_t* buf = reinterpret_cast<uint16_t*>(smem_raw);
+    const int l = threadIdx.x;
+    const int r0 = blockIdx.x * G, r1 = min(s, r0 + G);
+    const int nr = r1 - r0;
+    for (int k = blockIdx.y; k < nl; k += gridDim.y) {
+        const int* sg = seg + (int64_t)k * s;
+        const int base = sg[r0];
+        for (int i = l; i < G * G; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        if (l < nr) {
+            const int a = sg[r0 + l] - base, e = sg[r0 + l + 1] - base;
+            rem[l] = e - a;
+            outp[l] = a;
+            for (int p = a; p < e; ++p) ++cnt[l * G + (ent[base + p] & 0x7fff) % G];
+            int run = a;
+            for (int r = 0; r < G; ++r) {
+                pos[l * G + r] = run;
+                cur[l * G + r] = run;
+                run += cnt[l * G + r];
+            }
+            for (int p = a; p < e; ++p) {
+                const uint16_t v = ent[base + p];
+                buf[cur[l * G + (v & 0x7fff) % G]++] = v;
+            }
+        }
+        __syncthreads();
+        if (l == 0) {
+            for (int step = 0;; ++step) {
+                int used[G];
+                for (int r = 0; r < G; ++r) used[r] = 0;
+                bool any = false;
+                for (int q = 0; q < nr; ++q) {
+                    const int li = (step + q) % nr;
+                    if (rem[li] == 0) continue;
+                    any = true;
+                    int pick = 0, pu = INT_MAX, pc = 0;
+                    for (int r = 0; r < G; ++r) {
+                        const int c = cnt[li * G + r];
+                        if (c > 0 && (used[r] < pu || (used[r] == pu && c > pc))) {
+                            pick = r;
+                            pu = used[r];
+                            pc = c;
+                        }
+                    }
+                    ++used[pick];
+                    --cnt[li * G + pick];
+                    --rem[li];
+                    ent[base + outp[li]++] = buf[pos[li * G + pick]++];
+                }
+                if (!any) break;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+void launch_sketch_schedule(int nl, int s, int word, int max_group, const int* seg, uint16_t* ent, cudaStream_t st) {
+    const size_t sm = ((size_t)max_group * sizeof(uint16_t) + 15) & ~(size_t)15;
+    if (sm > 160 * 1024) return;  // very few sketch rows per block: the lists keep their fill order
+    if (word == 8) {
+        set_smem((const void*)k_seg_schedule<16>, sm);
+        k_seg_schedule<16><<<dim3((s + 15) / 16, std::min(nl, 65535)), 32, sm, st>>>(nl, s, seg, ent);
+    } else {
+        set_smem((const void*)k_seg_schedule<32>, sm);
+        k_seg_schedule<32><<<dim3((s + 31) / 32, std::min(nl, 65535)), 32, sm, st>>>(nl, s, seg, ent);
+    }
+    ++g_launches;
 }
 
 void launch_sketch_count(int n, int s, int zeta, int Bq, const int* rows, int* counts, cudaStream_t st) {
