@@ -74,6 +74,9 @@ __device__ __forceinline__ void st_keep(__nv_bfloat16* p, float v, unsigned long
 }
 
 // Value as it will read back after store_as (identity except for BF16 rounding).
+__device__ __forceinline__ double fma_as(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_as(float a, float b, float c) { return fmaf(a, b, c); }
+
 __device__ __forceinline__ double stored_value(double v, const double*) { return v; }
 __device__ __forceinline__ float stored_value(float v, const float*) { return v; }
 __device__ __forceinline__ float stored_value(float v, const __nv_bfloat16*) {

@@ -44,19 +44,18 @@ __device__ __forceinline__ void sell_chunk(const int* __restrict__ cp, const MT*
 
 // Phase 1, one thread per row, from the SELL-32 copy of A: w' = A u_i over the block (vector rows v0 .. v0+len,
 // whose matrix rows start the list block's first slice sb; warp rows kw .. kw+31 are slice sb + kw/32), fused with
-// storing w' (global W and the shared block copy), the window dot products acc_q += u_{lo+q}[r] * w'[r] and
-// ||u_i||^2.  Each row is summed in entry order, the warp issuing as many FMAs as its slice is wide.  The window
-// values and the next slice's extent are loaded before the row's SpMV, so they are in flight together.  Returns
-// the thread's largest exponent of w'.
+// storing w' (global W and the shared block copy) and the window dot products acc_q += u_{lo+q}[r] * w'[r].  Each
+// row is summed in entry order, the warp issuing as many FMAs as its slice is wide.  The window values and the next
+// slice's extent are loaded before the row's SpMV, so they are in flight together.  Returns the thread's largest
+// exponent of w'.
 template <int NW, typename MT, typename VT, typename AT>
 __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ soff, const uint8_t* __restrict__ slen,
                                               const int* __restrict__ scol, const MT* __restrict__ sval, int sb,
                                               const VT* __restrict__ Ub, const VT* __restrict__ xg, int i, int lo,
                                               int v0, int len, int cs, AT* __restrict__ wblk, AT* __restrict__ W,
-                                              AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
+                                              AT (&acc)[NW > 0 ? NW : 1]) {
     const int lane = threadIdx.x & 31;
     const unsigned long long pol = l2_keep_policy();  // window rows and w' are read again by the update
-    const VT* x = Ub + (int64_t)i * N;
     const VT* xs = xg + cs;  // gather base (u_i, or M^{-1} u_i with a preconditioner): column c at vector index c + cs
     int emax = 1;
     int kw = threadIdx.x & ~31;
@@ -74,9 +73,6 @@ __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ sof
         AT uw[NW > 0 ? NW : 1];
 #pragma unroll
         for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_keep(Ub + (int64_t)(lo + q) * N + r, pol) : AT(0);
-        AT ui;  // u_i[r] (the last window vector when there is a window) for ||u_i||^2
-        if constexpr (NW > 0) ui = uw[NW - 1];
-        else ui = ok ? ld_plain(x + r) : AT(0);
         const int kn = kw + (int)blockDim.x;
         int o0n = 0, o1n = 0, rln = 0;
         if (kn < len) {
@@ -108,7 +104,6 @@ __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ sof
         }
 #pragma unroll
         for (int q = 0; q < NW; ++q) acc[q] += uw[q] * sum;
-        nrm += ui * ui;
         emax = max(emax, exp_of(sum));
         o0 = o0n;
         o1 = o1n;
@@ -119,18 +114,17 @@ __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ sof
 
 // ---------------------------------------------------------------------------------------------------------------
 // Phase 1, one thread per row: w' = A u_i over the block (vector rows v0 .. v0+len = matrix rows v0-cs ..) fused
-// with storing w' (global W and the shared block copy), the window dot products acc_q += u_{lo+q}[r] * w'[r] and
-// ||u_i||^2.  The window values and the next row group's extents are loaded before the row's SpMV, so they are in
-// flight together.  Returns the thread's largest exponent of w'.
+// with storing w' (global W and the shared block copy) and the window dot products acc_q += u_{lo+q}[r] * w'[r].
+// The window values and the next row group's extents are loaded before the row's SpMV, so they are in flight
+// together.  Returns the thread's largest exponent of w'.
 template <int NW, typename MT, typename VT, typename AT>
 __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ rp, const int* __restrict__ col,
                                                 const MT* __restrict__ val, const VT* __restrict__ Ub,
                                                 const VT* __restrict__ xg, int i, int lo, int v0, int len, int cs,
                                                 AT* __restrict__ wblk, AT* __restrict__ W,
-                                                AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
+                                                AT (&acc)[NW > 0 ? NW : 1]) {
     const int lane = threadIdx.x & 31;
     const unsigned long long pol = l2_keep_policy();  // window rows and w' are read again by the update
-    const VT* x = Ub + (int64_t)i * N;
     const VT* xs = xg + cs;               // gather base (u_i, or M^{-1} u_i): column c at vector index c + cs
     const int* rpm = rp + (v0 - cs);      // row pointers of the block's matrix rows
     int emax = 1;
@@ -147,9 +141,6 @@ __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ r
         AT uw[NW > 0 ? NW : 1];
 #pragma unroll
         for (int q = 0; q < NW; ++q) uw[q] = ok ? ld_keep(Ub + (int64_t)(lo + q) * N + r, pol) : AT(0);
-        AT ui;  // u_i[r] (the last window vector when there is a window) for ||u_i||^2
-        if constexpr (NW > 0) ui = uw[NW - 1];
-        else ui = ok ? ld_plain(x + r) : AT(0);
         const int kn = k + (int)blockDim.x;
         int an = 0, rln = 0;
         if (kn < len) {
@@ -172,7 +163,6 @@ __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ r
         }
 #pragma unroll
         for (int q = 0; q < NW; ++q) acc[q] += uw[q] * sum;
-        nrm += ui * ui;
         emax = max(emax, exp_of(sum));
         a = an;
         rl = rln;
@@ -180,12 +170,11 @@ __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ r
     return emax;
 }
 
-// Phase 1 tail for the sub-warp path (w' already in shared memory): store w', accumulate the window dots and
-// ||u_i||^2.
+// Phase 1 tail for the sub-warp path (w' already in shared memory): store w' and accumulate the window dots.
 template <int NW, typename VT, typename AT>
-__device__ __forceinline__ int dots_pass(int N, int v0, int len, const VT* __restrict__ Ub, int lo, int i,
+__device__ __forceinline__ int dots_pass(int N, int v0, int len, const VT* __restrict__ Ub, int lo,
                                          const AT* __restrict__ wblk, AT* __restrict__ W,
-                                         AT (&acc)[NW > 0 ? NW : 1], AT& nrm) {
+                                         AT (&acc)[NW > 0 ? NW : 1]) {
     const unsigned long long pol = l2_keep_policy();  // window rows and w' are read again by the update
     int emax = 1;
 #pragma unroll 2
@@ -194,8 +183,6 @@ __device__ __forceinline__ int dots_pass(int N, int v0, int len, const VT* __res
         const AT w = wblk[k];
         st_keep(W + r, w, pol);
         emax = max(emax, exp_of(w));
-        const AT ui = ld_keep(Ub + (int64_t)i * N + r, pol);
-        nrm += ui * ui;
 #pragma unroll
         for (int q = 0; q < NW; ++q) acc[q] += ld_keep(Ub + (int64_t)(lo + q) * N + r, pol) * w;
     }
@@ -204,8 +191,8 @@ __device__ __forceinline__ int dots_pass(int N, int v0, int len, const VT* __res
 
 // ---------------------------------------------------------------------------------------------------------------
 // Phase 1 of an inner step for the CTA's row block: w' = A u_i (stored to W and kept in the shared block), the
-// block partials of ||u_i||^2 and of the window dots (normpart, hpart), and Eb, the block's largest exponent of w'
-// (the reference exponent of the FP64 fixed-point sketch sums).  Returns false (every thread of the CTA alike) when
+// block partials of the window dots (hpart), and Eb, the block's largest exponent of w' (the reference exponent of
+// the FP64 fixed-point sketch sums).  (The block partials of ||u_i||^2 come from the update that wrote u_i.)  Returns false (every thread of the CTA alike) when
 // the block's problem has no step i to take.
 template <int V, int U, int NW, typename MT, typename VT, typename AT>
 __device__ __forceinline__ bool inner_spmv_part(const Plan& P, int i, const MT* __restrict__ val,
@@ -226,14 +213,13 @@ __device__ __forceinline__ bool inner_spmv_part(const Plan& P, int i, const MT* 
 #pragma unroll
     for (int q = 0; q < NW; ++q) acc[q] = AT(0);
     int emax;
-    AT nrm = AT(0);  // ||u_i||^2 over the block (u_i, the basis vector this step extends the basis from)
     // the vector the SpMV multiplies: u_i, or t_i = M^{-1} u_i with a right preconditioner (an FP64 plan only)
     const VT* xg = P.xin ? reinterpret_cast<const VT*>(P.xin) : Ub + (int64_t)i * N;
     if constexpr (V == kVecSell) {
         emax = spmv_dots_sell<NW>(N, P.sl_off, P.sl_len, P.sl_col, val, P.sl_base[bi.list], Ub, xg, i, lo, bi.v0,
-                                  bi.len, bi.cs, wblk, W, acc, nrm);
+                                  bi.len, bi.cs, wblk, W, acc);
     } else if constexpr (V == 1) {
-        emax = spmv_dots_scalar<NW>(N, P.rp, P.col, val, Ub, xg, i, lo, bi.v0, bi.len, bi.cs, wblk, W, acc, nrm);
+        emax = spmv_dots_scalar<NW>(N, P.rp, P.col, val, Ub, xg, i, lo, bi.v0, bi.len, bi.cs, wblk, W, acc);
     } else {
         const int m0 = bi.v0 - bi.cs;
         int n0, n01;
@@ -251,28 +237,25 @@ __device__ __forceinline__ bool inner_spmv_part(const Plan& P, int i, const MT* 
                                                 n01);
         }
         __syncthreads();
-        emax = dots_pass<NW>(N, bi.v0, bi.len, Ub, lo, i, wblk, W, acc, nrm);
+        emax = dots_pass<NW>(N, bi.v0, bi.len, Ub, lo, wblk, W, acc);
     }
     if (threadIdx.x == 0) wblk[Bn] = AT(0);
-    // block sums of ||u_i||^2 and the window dots in one round: each warp's sums (shuffle trees), then the warps'
-    // partials in warp order; the block's largest exponent of w' with them
+    // block sums of the window dots in one round: each warp's sums (shuffle trees), then the warps' partials in
+    // warp order; the block's largest exponent of w' with them
     {
-        AT (*red2)[16] = reinterpret_cast<AT (*)[16]>(red);  // [NW + 1][16]
-        const AT v = warp_sum(nrm);
-        if (lane == 0) red2[0][warp] = v;
+        AT (*red2)[16] = reinterpret_cast<AT (*)[16]>(red);  // [NW][16]
 #pragma unroll
         for (int q = 0; q < NW; ++q) {
             const AT d = warp_sum(acc[q]);
-            if (lane == 0) red2[1 + q][warp] = d;
+            if (lane == 0) red2[q][warp] = d;
         }
         emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
         if (lane == 0) emax_sh[warp] = emax;
         __syncthreads();
-        if (threadIdx.x <= NW) {
+        if (threadIdx.x < NW) {
             AT t = AT(0);
             for (int w = 0; w < nw; ++w) t += red2[threadIdx.x][w];
-            if (threadIdx.x == 0) ((AT*)P.normpart)[b] = t;
-            else ((AT*)P.hpart)[(int64_t)b * kMaxTrunc + threadIdx.x - 1] = t;
+            ((AT*)P.hpart)[(int64_t)b * kMaxTrunc + threadIdx.x] = t;
         }
     }
     Eb = 1;
@@ -367,21 +350,26 @@ __device__ __forceinline__ AT block_partials_sum(const AT* __restrict__ x, int64
     return warp_sum(a);
 }
 
-// Truncated-Arnoldi update kernel of the two-launch step (NW = window size).  Each thread first loads its first PF
-// rows of w' and of the window vectors (they do not depend on the scalars); meanwhile warp 0 sums the problem's
-// ||u_i||^2 partials and warps 1..NW its window-dot partials, each with all loads in flight at once.  After one
-// barrier thread 0 forms sigma_i and the coefficients; after a second, the sketched column S A b_i (one warp per
-// sketch row, rows spread over all of the problem's blocks) and the row update.
+// The truncated-Arnoldi update of a row block works on 64-row chunks (lane l of a warp: rows 64c + l and 64c + 32 + l)
+// and forms the block partial of ||u_{i+1}||^2 on the way: each lane accumulates the squares of the stored values of
+// its rows in the order of its chunks (one FMA per row), the block partial is the warps' shuffle-tree sums added in
+// warp order.  Warp w takes chunks w, w + nw, w + 2 nw, ... in both the two-launch update and the fused step, so
+// the two compute the same sums in the same order.  The norm partials alternate between two slots by step parity:
+// step i reads slot i & 1 (written by the update of step i - 1) and writes the other.
+__host__ __device__ constexpr int norm_chunks(int rows) { return (rows + 63) / 64; }
+
+// Truncated-Arnoldi update kernel of the two-launch step (NW = window size).  Warp w updates the 64-row chunks w,
+// w + nw, ... of the block (lane l: rows 64c + l and 64c + 32 + l) and its first chunk's rows of w' and of the window
+// vectors are loaded first (they do not depend on the scalars); meanwhile warp 0 sums the problem's ||u_i||^2
+// partials and warps 1..NW its window-dot partials, each with all loads in flight at once.  After one barrier thread
+// 0 forms sigma_i and the coefficients; after a second, the sketched column S A b_i (one warp per sketch row, rows
+// spread over all of the problem's blocks) and the row update with the block partial of ||u_{i+1}||^2.
 // Three 512-thread CTAs per SM (at most 42 registers; batches run many waves of blocks) for windows up to 3, two
 // for wider windows, which would spill within 42.
 template <int NW, typename VT, typename AT>
 __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last) {
-    // rows per thread loaded before the scalars (PF) and per round of the row loop (UR; all loads of a round are
-    // issued before its stores)
-    constexpr int PF = (sizeof(AT) == 8 && NW >= 5) ? 1 : 2;
-    constexpr int UR = (sizeof(AT) == 8 && NW >= 4) ? 1 : 2;
     __shared__ AT coef_sh[kMaxTrunc];
-    __shared__ AT part_sh[kMaxTrunc + 1];
+    __shared__ AT part_sh[32];  // [0..NW] the problem's sums; later the warps' norm sums
     __shared__ double sig_sh;
     __shared__ int stop_sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -392,7 +380,7 @@ __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last)
     VT* Ub = (VT*)P.U;
     const AT* W = (const AT*)P.W;
     const int lo = i - NW + 1;
-    AT wv[PF], uv[PF][NW > 0 ? NW : 1];
+    AT wv[2], uv[2][NW > 0 ? NW : 1];
     // last reads of w' and of the oldest window vector (the next step's window starts one later): L2 may drop them
     // (FP64 and FP32 bases; measured slower with a BF16 basis, which keeps plain loads)
     constexpr bool DROP = sizeof(VT) >= 4;
@@ -402,21 +390,24 @@ __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last)
         return (DROP && q == 0 && NW > 1) ? ld_keep(a, drop) : ld_plain(a);
     };
     auto wrd = [&](int r) -> AT { return DROP ? ld_keep(W + r, drop) : W[r]; };
-    if (!last) {
+    // the rows of chunk c for this lane, with their w' and window values
+    auto load_chunk = [&](int c, AT (&w)[2], AT (&uq)[2][NW > 0 ? NW : 1]) {
 #pragma unroll
-        for (int u = 0; u < PF; ++u) {
-            const int k = threadIdx.x + u * (int)blockDim.x;
+        for (int u = 0; u < 2; ++u) {
+            const int k = 64 * c + 32 * u + lane;
+            const bool ok = k < bi.len;
             const int r = bi.v0 + k;
-            wv[u] = (k < bi.len) ? wrd(r) : AT(0);
+            w[u] = ok ? wrd(r) : AT(0);
 #pragma unroll
-            for (int q = 0; q < NW; ++q) uv[u][q] = (k < bi.len) ? win(q, r) : AT(0);
+            for (int q = 0; q < NW; ++q) uq[u][q] = ok ? win(q, r) : AT(0);
         }
-    }
+    };
+    if (!last) load_chunk(warp, wv, uv);
     if (threadIdx.x == 0) stop_sh = cycle_idle(P, p, i) ? 1 : 0;
     const int b0 = P.prob_b0[p], b1 = P.prob_b0[p + 1];
     // ||u_i||^2 (warp 0; sigma_0 is known at i = 0) and the window dots u_l^T w' (warp 1 + q) over the blocks
     if (warp == 0 && i > 0) {
-        const AT a = block_partials_sum((const AT*)P.normpart, 1, b0, b1, lane);
+        const AT a = block_partials_sum((const AT*)P.normpart + (int64_t)(i & 1) * P.nblk, 1, b0, b1, lane);
         if (lane == 0) part_sh[0] = a;
     } else if (warp >= 1 && warp <= NW) {
         const AT a = block_partials_sum((const AT*)P.hpart + (warp - 1), kMaxTrunc, b0, b1, lane);
@@ -481,34 +472,39 @@ __device__ __forceinline__ void inner_axpy_block(const Plan& P, int i, int last)
     for (int q = 0; q < NW; ++q) cf[q] = coef_sh[q];
     VT* un = Ub + (int64_t)(i + 1) * N;
     const unsigned long long pol = l2_keep_policy();
-    auto update = [&](int r, AT u, const AT (&uq)[NW > 0 ? NW : 1]) {
+    AT nsq = AT(0);  // the lane's part of ||u_{i+1}||^2
+    // updates the lane's rows of chunk c
+    auto update_chunk = [&](int c, const AT (&w)[2], const AT (&uq)[2][NW > 0 ? NW : 1]) {
 #pragma unroll
-        for (int q = 0; q < NW; ++q) u -= cf[q] * uq[q];
-        if constexpr (sizeof(AT) == 8) u = mul_pow2((double)u, p2);
-        else u = u * sc2;
-        st_keep(un + r, u, pol);  // the next step gathers it and reads it as a window row
+        for (int u = 0; u < 2; ++u) {
+            const int k = 64 * c + 32 * u + lane;
+            if (k < bi.len) {
+                AT v = w[u];
+#pragma unroll
+                for (int q = 0; q < NW; ++q) v -= cf[q] * uq[u][q];
+                if constexpr (sizeof(AT) == 8) v = mul_pow2((double)v, p2);
+                else v = v * sc2;
+                st_keep(un + bi.v0 + k, v, pol);  // the next step gathers it and reads it as a window row
+                const AT vs = stored_value(v, un);
+                nsq = fma_as(vs, vs, nsq);
+            }
+        }
     };
-#pragma unroll
-    for (int u = 0; u < PF; ++u) {
-        const int k = threadIdx.x + u * (int)blockDim.x;
-        if (k < bi.len) update(bi.v0 + k, wv[u], uv[u]);
+    const int nch = norm_chunks(bi.len);
+    if (warp < nch) update_chunk(warp, wv, uv);
+    for (int c = warp + nw; c < nch; c += nw) {
+        AT wr[2], uq[2][NW > 0 ? NW : 1];
+        load_chunk(c, wr, uq);
+        update_chunk(c, wr, uq);
     }
-    for (int k0 = threadIdx.x + PF * (int)blockDim.x; k0 < bi.len; k0 += UR * (int)blockDim.x) {
-        AT wr[UR], uq[UR][NW > 0 ? NW : 1];
-#pragma unroll
-        for (int u = 0; u < UR; ++u) {
-            const int k = k0 + u * (int)blockDim.x;
-            const bool ok = k < bi.len;
-            const int r = bi.v0 + k;
-            wr[u] = ok ? wrd(r) : AT(0);
-#pragma unroll
-            for (int q = 0; q < NW; ++q) uq[u][q] = ok ? win(q, r) : AT(0);
-        }
-#pragma unroll
-        for (int u = 0; u < UR; ++u) {
-            const int k = k0 + u * (int)blockDim.x;
-            if (k < bi.len) update(bi.v0 + k, wr[u], uq[u]);
-        }
+    // block partial of ||u_{i+1}||^2 into the slot of step i + 1
+    const AT ws = warp_sum(nsq);
+    if (lane == 0) part_sh[warp] = ws;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        AT t = AT(0);
+        for (int w = 0; w < nw; ++w) t += part_sh[w];
+        ((AT*)P.normpart)[(int64_t)((i + 1) & 1) * P.nblk + b] = t;
     }
 }
 
@@ -539,8 +535,9 @@ __device__ __forceinline__ bool wait_flag(const int* flag) {
 //    ||u_i||^2 partials and warps 1..NW its window-dot partials; thread 0 forms sigma_i and the coefficients and
 //    publishes them through a shared-memory flag;
 //  * the other warps: the block's sketch partials (every sketch row), then one arrival per CTA on grid counter 2;
-//  * then every warp claims chunks of 32 UR rows of the block and updates them (the chunk's loads are issued before
-//    the first wait for the coefficients);
+//  * then every warp updates its 64-row chunks of the block (those of the two-launch update; the first round's
+//    loads are issued before the first wait for the coefficients) and forms its part of ||u_{i+1}||^2; the last warp
+//    through the update adds the warps' parts into the block's partial;
 //  * last, the warps that own a row of the sketched column S A b_i (rows spread over all blocks) wait for every CTA's
 //    sketch partials (grid counter 2) and sum them.
 // The arithmetic of every value and its order are those of the two-launch step.
@@ -549,11 +546,11 @@ __device__ __forceinline__ void fused_phase2(const Plan& P, int i, int last, AT*
                                              const unsigned long long* target_ptr) {
     constexpr int NSW = NW + 1;  // warps of the scalar role
     constexpr bool WIDE = (sizeof(AT) == 8 && NW >= 3);
-    constexpr int UR = WIDE ? 2 : 4;  // rows per lane of an update chunk
     __shared__ AT coef_sh[kMaxTrunc];
     __shared__ AT part_sh[kMaxTrunc + 1];
     __shared__ double sig_sh;
-    __shared__ int stop_sh, ready_sh, chunk_sh, skdone_sh;
+    __shared__ AT nrm_sh[32];
+    __shared__ int stop_sh, ready_sh, skdone_sh, upd_sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int b = blockIdx.x;
     const BlockInfo bi = block_info(P, b);
@@ -561,8 +558,8 @@ __device__ __forceinline__ void fused_phase2(const Plan& P, int i, int last, AT*
     if (threadIdx.x == 0) {
         stop_sh = 0;
         ready_sh = 0;
-        chunk_sh = 0;
         skdone_sh = 0;
+        upd_sh = 0;
     }
     sketch_prepare(P, bi.len, wblk, Eb);  // ends with a block barrier: the flags above and *target_ptr are visible
     const unsigned long long target = *target_ptr;
@@ -573,7 +570,7 @@ __device__ __forceinline__ void fused_phase2(const Plan& P, int i, int last, AT*
         if (threadIdx.x == 0) grid_wait(P.gsync, target, P.gsync + 1);
         bar_sync_named(1, NSW * 32);
         if (warp == 0 && i > 0) {
-            const AT a = block_partials_sum((const AT*)P.normpart, 1, b0, b1, lane);
+            const AT a = block_partials_sum((const AT*)P.normpart + (int64_t)(i & 1) * P.nblk, 1, b0, b1, lane);
             if (lane == 0) part_sh[0] = a;
         } else if (warp >= 1) {
             const AT a = block_partials_sum((const AT*)P.hpart + (warp - 1), kMaxTrunc, b0, b1, lane);
@@ -649,8 +646,14 @@ __device__ __forceinline__ void fused_phase2(const Plan& P, int i, int last, AT*
         for (int q = 0; q < NW; ++q) cf[q] = coef_sh[q];
     };
     bool have = false;
+    AT nsq = AT(0);  // the lane's part of ||u_{i+1}||^2
     if (!last) {
-        // u_{i+1} = 2^p2 (w' - sum_q coef_q u_{lo+q}), 2^p2 the power of two just below sigma_i
+        // u_{i+1} = 2^p2 (w' - sum_q coef_q u_{lo+q}), 2^p2 the power of two just below sigma_i, over the chunks of
+        // the two-launch update (warp w: 64-row chunks w, w + nw, ...), CPI of them per round with all loads issued
+        // first
+        constexpr int CPI = WIDE ? 1 : 2;
+        const int nch = norm_chunks(bi.len);
+        const int cfirst = warp, cstep = nw, cend = nch;
         VT* Ub = (VT*)P.U;
         const AT* W = (const AT*)P.W;
         VT* un = Ub + (int64_t)(i + 1) * N;
@@ -661,24 +664,23 @@ __device__ __forceinline__ void fused_phase2(const Plan& P, int i, int last, AT*
         const unsigned long long drop = l2_drop_policy();
         int p2 = 0;
         AT sc2 = AT(1);
-        for (;;) {
-            int c = 0;
-            if (lane == 0) c = atomicAdd(&chunk_sh, 1);
-            c = __shfl_sync(0xffffffffu, c, 0);
-            const int k0 = c * 32 * UR;
-            if (k0 >= bi.len) break;
-            AT wr[UR], uq[UR][NW > 0 ? NW : 1];
+        for (int c0 = cfirst; c0 < cend; c0 += CPI * cstep) {
+            AT wr[CPI][2], uq[CPI][2][NW > 0 ? NW : 1];
 #pragma unroll
-            for (int u = 0; u < UR; ++u) {
-                const int k = k0 + 32 * u + lane;
-                const bool ok = k < bi.len;
-                const int r = bi.v0 + k;
-                if constexpr (sizeof(AT) == 8) wr[u] = ok ? (DROP ? ld_keep(W + r, drop) : W[r]) : AT(0);
-                else wr[u] = ok ? wblk[k] : AT(0);  // FP32: w' is still the shared block
+            for (int j = 0; j < CPI; ++j) {
 #pragma unroll
-                for (int q = 0; q < NW; ++q) {
-                    const VT* ap = Ub + (int64_t)(lo + q) * N + r;
-                    uq[u][q] = ok ? ((DROP && q == 0 && NW > 1) ? ld_keep(ap, drop) : ld_plain(ap)) : AT(0);
+                for (int u = 0; u < 2; ++u) {
+                    const int c = c0 + j * cstep;
+                    const int k = 64 * c + 32 * u + lane;
+                    const bool ok = c < cend && k < bi.len;
+                    const int r = bi.v0 + k;
+                    if constexpr (sizeof(AT) == 8) wr[j][u] = ok ? (DROP ? ld_keep(W + r, drop) : W[r]) : AT(0);
+                    else wr[j][u] = ok ? wblk[k] : AT(0);  // FP32: w' is still the shared block
+#pragma unroll
+                    for (int q = 0; q < NW; ++q) {
+                        const VT* ap = Ub + (int64_t)(lo + q) * N + r;
+                        uq[j][u][q] = ok ? ((DROP && q == 0 && NW > 1) ? ld_keep(ap, drop) : ld_plain(ap)) : AT(0);
+                    }
                 }
             }
             if (!have) {
@@ -690,21 +692,44 @@ __device__ __forceinline__ void fused_phase2(const Plan& P, int i, int last, AT*
                 sc2 = (AT)ldexp(1.0, p2);
             }
 #pragma unroll
-            for (int u = 0; u < UR; ++u) {
-                const int k = k0 + 32 * u + lane;
-                if (k < bi.len) {
-                    AT v = wr[u];
+            for (int j = 0; j < CPI; ++j) {
 #pragma unroll
-                    for (int q = 0; q < NW; ++q) v -= cf[q] * uq[u][q];
-                    if constexpr (sizeof(AT) == 8) v = mul_pow2((double)v, p2);
-                    else v = v * sc2;
-                    st_keep(un + bi.v0 + k, v, keep);  // the next step gathers it and reads it as a window row
+                for (int u = 0; u < 2; ++u) {
+                    const int c = c0 + j * cstep;
+                    const int k = 64 * c + 32 * u + lane;
+                    if (c < cend && k < bi.len) {
+                        AT v = wr[j][u];
+#pragma unroll
+                        for (int q = 0; q < NW; ++q) v -= cf[q] * uq[j][u][q];
+                        if constexpr (sizeof(AT) == 8) v = mul_pow2((double)v, p2);
+                        else v = v * sc2;
+                        st_keep(un + bi.v0 + k, v, keep);  // the next step gathers it and reads it as a window row
+                        const AT vs = stored_value(v, un);
+                        nsq = fma_as(vs, vs, nsq);
+                    }
                 }
             }
         }
     }
     if (!have) get_scalars();
     if (stop) return;
+    if (!last) {
+        // the block partial of ||u_{i+1}||^2: the warps' sums in warp order, added by the last warp through the update
+        const AT ws = warp_sum(nsq);
+        int fin = 0;
+        if (lane == 0) {
+            nrm_sh[warp] = ws;
+            __threadfence_block();
+            fin = (atomicAdd(&upd_sh, 1) == nw - 1) ? 1 : 0;
+            if (fin) {
+                __threadfence_block();
+                AT t = AT(0);
+                for (int w = 0; w < nw; ++w) t += nrm_sh[w];
+                ((AT*)P.normpart)[(int64_t)((i + 1) & 1) * P.nblk + b] = t;
+            }
+        }
+        __syncwarp();
+    }
     // sketched column S A b_i = sigma_i S w': sketch row rr to warp rr / nb of the problem's block rr % nb, once every
     // CTA's sketch partials are in place
     const double csc = P.sk_scale * sig_i;
