@@ -406,54 +406,54 @@ int build_sketch(sfgmres_ctx* h, int s) {
     h->sk_s = -1;
     int maxn = 0;
     for (int q = 0; q < h->nsys; ++q) maxn = std::max(maxn, h->sys_n[q]);
-    const int64_t tot = (int64_t)h->n * zeta;
-    const int64_t nseg = (int64_t)h->nl * s + 1;
-    if (nseg > INT32_MAX || tot + 8 * nseg >= INT32_MAX)
+    const int ng = (s + 31) / 32;  // groups of 32 sketch rows per list block
+    const int64_t ncnt = (int64_t)h->nl * s;
+    const int64_t nseg = (int64_t)h->nl * ng + 1;
+    if (ncnt >= INT32_MAX || nseg >= INT32_MAX)
         return fail(h, SFGMRES_ERR_INVALID_ARG, "sketch too large for 32-bit gather lists");
     int* rows = nullptr;
     int8_t* neg = nullptr;
     int* counts = nullptr;
+    int* units = nullptr;
     const int64_t tq = (int64_t)maxn * zeta;
     CK(cudaMalloc(&rows, tq * sizeof(int)));
     CK(cudaMalloc(&neg, tq));
-    CK(cudaMalloc(&counts, nseg * sizeof(int)));
+    CK(cudaMalloc(&counts, ncnt * sizeof(int)));
+    CK(cudaMalloc(&units, nseg * sizeof(int)));
     CK(cudaMalloc(&h->seg, nseg * sizeof(int)));
-    CK(cudaMemsetAsync(counts, 0, nseg * sizeof(int), h->st));
+    CK(cudaMemsetAsync(counts, 0, ncnt * sizeof(int), h->st));
     for (int q = 0; q < h->nsys; ++q) {
         launch_sketch_pattern(h->sys_n[q], s, zeta, h->kind, h->seed, rows, neg, h->st);
         launch_sketch_count(h->sys_n[q], s, zeta, h->sys_Bq[q], rows, counts + (int64_t)h->sys_l0[q] * s, h->st);
     }
-    launch_list_scan(counts, h->seg, (int)(nseg - 1), h->st);
+    launch_group_units(h->nl, s, counts, units, h->st);
+    launch_list_scan(units, h->seg, (int)(nseg - 1), h->st);
     std::vector<int> hs(nseg);
     CK(cudaMemcpyAsync(hs.data(), h->seg, nseg * sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    const int64_t total = hs[nseg - 1];
-    // +8: the gather loop may read one 16-byte group past the end of the last list
-    CK(cudaMalloc(&h->ent, (total + 8) * sizeof(uint16_t)));
-    launch_fill_u16(total + 8, (uint16_t)h->Bn, h->ent, h->st);  // padding points at the zero slot
+    const int64_t total = (int64_t)hs[nseg - 1] * 8;  // entries
+    if (hs[nseg - 1] < 0 || total >= ((int64_t)1 << 34))
+        return fail(h, SFGMRES_ERR_INVALID_ARG, "sketch too large for 32-bit gather lists");
+    CK(cudaMalloc(&h->ent, std::max<int64_t>(total, 8) * sizeof(uint16_t)));
+    launch_fill_u16(total, (uint16_t)h->Bn, h->ent, h->st);  // padding points at the zero slot
     for (int q = 0; q < h->nsys; ++q) {
         launch_sketch_pattern(h->sys_n[q], s, zeta, h->kind, h->seed, rows, neg, h->st);
-        launch_sketch_fill(h->sys_n[q], s, zeta, h->sys_Bq[q], rows, neg, h->seg + (int64_t)h->sys_l0[q] * s,
+        launch_sketch_fill(h->sys_n[q], s, zeta, h->sys_Bq[q], rows, neg, h->seg + (int64_t)h->sys_l0[q] * ng,
                            h->ent, h->st);
     }
-    {
-        const int G = 128 / word;
-        int max_group = 0;
-        for (int64_t k = 0; k < h->nl; ++k)
-            for (int r0 = 0; r0 < s; r0 += G)
-                max_group = std::max(max_group, hs[k * s + std::min(s, r0 + G)] - hs[k * s + r0]);
-        launch_sketch_schedule(h->nl, s, word, max_group, h->seg, h->ent, h->st);
-    }
+    // the longest list (padding included), in entries: E * 8 for the group with the most units
+    int longest = 0;
+    for (int64_t q = 0; q + 1 < nseg; ++q) longest = std::max(longest, (hs[q + 1] - hs[q]) / 32 * 8);
+    launch_sketch_schedule(h->nl, s, word, (128 / word) * longest, h->seg, h->ent, h->st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->st));
     cudaFree(rows);
     cudaFree(neg);
     cudaFree(counts);
+    cudaFree(units);
     {
         // FP64 sketch terms are 53-bit integers summed exactly in 64 bits: lists longer than 1023 entries get
-        // extra right shifts so that no sum can overflow
-        int longest = 0;
-        for (int64_t q = 0; q + 1 < nseg; ++q) longest = std::max(longest, hs[q + 1] - hs[q]);
+        // extra right shifts so that no sum can overflow (padding entries add zero)
         int H = 0;
         while ((longest >> H) >= 1023) ++H;
         h->sk_headroom = H;

@@ -213,10 +213,11 @@ __device__ __forceinline__ int exp_of(double w) {
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Sketch gather lists.  For row block b and sketch row r the list ent[seg[b*s + r] .. seg[b*s + r + 1]) holds one
-// 16-bit entry per nonzero S_rj with j in the block: bits 0..14 the offset of j in the block, bit 15 the sign.  Every
-// list starts at a multiple of 8 entries and is padded to a multiple of 8 with entries that point at the block's
-// zero slot (offset Bn), so a list is read with aligned 16-byte loads and no bounds checks.
+// Sketch gather lists.  For row block b and sketch row r the list holds one 16-bit entry per nonzero S_rj with j in
+// the block: bits 0..14 the offset of j in the block, bit 15 the sign.  The lists of the 32 rows of group g = r / 32
+// are interleaved in 16-byte units (unit u of lane r % 32 at unit index seg[b*ng + g] + 32u + r % 32, ng = ceil(s /
+// 32)) and padded to the group's longest list with entries that point at the block's zero slot (offset Bn), so a
+// warp reads them with contiguous 16-byte loads and no bounds checks.
 template <typename T>
 __device__ __forceinline__ T sum8(const uint4 d, const T* __restrict__ x) {
     const unsigned w[4] = {d.x, d.y, d.z, d.w};
@@ -230,21 +231,23 @@ __device__ __forceinline__ T sum8(const uint4 d, const T* __restrict__ x) {
     return acc;
 }
 
-// Sum of +-x[offset] over the list [a, e) in list order (deterministic), four 16-byte loads in flight.
+// Sum of +-x[offset] over the gather list of one lane of a group (E units of 8 entries, unit u at unit index
+// u0 + 32u + lane: the group's lists interleaved, so a warp's loads are contiguous), in list order (deterministic),
+// four 16-byte loads in flight.
 template <typename T>
-__device__ __forceinline__ T sum_list(const uint16_t* __restrict__ ent, int a, int e, const T* __restrict__ x) {
-    const uint4* p = reinterpret_cast<const uint4*>(ent + a);
-    const int ng = (e - a) >> 3;
+__device__ __forceinline__ T sum_group(const uint16_t* __restrict__ ent, int u0, int E, int lane,
+                                       const T* __restrict__ x) {
+    const uint4* p = reinterpret_cast<const uint4*>(ent) + u0 + lane;
     T acc = T(0);
-    int g = 0;
-    for (; g + 4 <= ng; g += 4) {
+    int u = 0;
+    for (; u + 4 <= E; u += 4) {
         uint4 d[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) d[k] = __ldg(p + g + k);
+        for (int k = 0; k < 4; ++k) d[k] = __ldg(p + 32 * (u + k));
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc += sum8(d[k], x);
     }
-    for (; g < ng; ++g) acc += sum8(__ldg(p + g), x);
+    for (; u < E; ++u) acc += sum8(__ldg(p + 32 * u), x);
     return acc;
 }
 

@@ -281,19 +281,23 @@ __device__ __forceinline__ void sketch_prepare(const Plan& P, int len, AT* __res
 template <typename AT>
 __device__ __forceinline__ void sketch_rows(const Plan& P, int b, int list, const AT* __restrict__ wblk, int Eb, int r0,
                                             int rstep) {
-    const int s = P.s;
-    const int* sg = P.seg + (int64_t)list * s;
+    const int s = P.s, ng = (s + 31) / 32;
+    const int* sg = P.seg + (int64_t)list * ng;  // the block's group starts (units)
     AT* cpart = (AT*)P.cpart;
     if constexpr (sizeof(AT) == 8) {
         const long long* qblk = reinterpret_cast<const long long*>(wblk);
         const double unit = fixed_unit(0.0, Eb, P.sk_headroom);
         const bool bad = exp_nonfinite(0.0, Eb);
         for (int rr = r0; rr < s; rr += rstep) {
-            const long long v = sum_list(P.ent, sg[rr], sg[rr + 1], qblk);
+            const int g = rr >> 5;
+            const long long v = sum_group(P.ent, sg[g], (sg[g + 1] - sg[g]) >> 5, rr & 31, qblk);
             cpart[(int64_t)b * s + rr] = bad ? (AT)NAN : (AT)((double)v * unit);
         }
     } else {
-        for (int rr = r0; rr < s; rr += rstep) cpart[(int64_t)b * s + rr] = sum_list(P.ent, sg[rr], sg[rr + 1], wblk);
+        for (int rr = r0; rr < s; rr += rstep) {
+            const int g = rr >> 5;
+            cpart[(int64_t)b * s + rr] = sum_group(P.ent, sg[g], (sg[g + 1] - sg[g]) >> 5, rr & 31, wblk);
+        }
     }
 }
 

@@ -84,7 +84,8 @@ struct Plan {
     unsigned long long* gsync = nullptr;  // fused step: [0], [2] grid arrival counters (reset per cycle), [1] a wait gave up
     int gwait_extra = 0;           // fused step: arrivals waited for beyond the launch's blocks (0; > 0 tests give-up)
 
-    // sketch: for list block L and sketch row r the list ent[seg[L*s + r] .. seg[L*s + r + 1])
+    // sketch: the gather lists of list block L, group g of 32 sketch rows start at unit seg[L*ng + g] of ent
+    // (ng = ceil(s / 32); 16-byte units, the group's lists interleaved, see common.cuh)
     int s = 0, zeta = 0, kind = 0;
     const int* seg = nullptr;
     const uint16_t* ent = nullptr;
@@ -171,22 +172,23 @@ __device__ __forceinline__ void block_bins(const Plan& p, const BlockInfo& bi, i
 // Pattern of one system's sketch: rows[j*zeta + l], neg[j*zeta + l] for its n columns.
 void launch_sketch_pattern(int n, int s, int zeta, int kind, uint64_t seed, int* rows, int8_t* neg,
                            cudaStream_t st);
-// Gather lists of one system's list blocks (block k holds its columns k*Bq .. min(n, (k+1)*Bq)).  Three steps:
+// Gather lists of one system's list blocks (block k holds its columns k*Bq .. min(n, (k+1)*Bq)).  Steps:
 // launch_sketch_count adds the list lengths of the system into counts[k*s + r] (zeroed by the caller); once the
-// counts of every system are in place, launch_list_scan turns all of them into list starts seg[0 .. len] (lengths
-// padded to multiples of 8, so every list starts on a 16-byte boundary); the caller reads seg[len], allocates ent,
-// pre-fills it with the zero-slot offset (launch_fill_u16) and calls launch_sketch_fill per system with seg pointing
-// at the system's first list.
+// counts of every system are in place, launch_group_units turns them into the 16-byte units of every group of 32
+// sketch rows (32 x the group's longest list in units of 8 entries) and launch_list_scan into group starts
+// seg[0 .. nl*ng] (units); the caller reads seg[nl*ng], allocates ent (8 entries per unit), pre-fills it with the
+// zero-slot offset (launch_fill_u16) and calls launch_sketch_fill per system with seg pointing at the system's first
+// group.
 void launch_sketch_count(int n, int s, int zeta, int Bq, const int* rows, int* counts, cudaStream_t st);
+void launch_group_units(int nl, int s, const int* counts, int* units, cudaStream_t st);
 void launch_list_scan(const int* counts, int* seg, int len, cudaStream_t st);
-void launch_sketch_fill(int n, int s, int zeta, int Bq, const int* rows, const int8_t* neg, const int* seg,
+void launch_sketch_fill(int n, int s, int zeta, int Bq, const int* rows, const int8_t* neg, const int* gseg,
                         uint16_t* ent, cudaStream_t st);
 void launch_fill_u16(int64_t cnt, uint16_t v, uint16_t* out, cudaStream_t st);
 // Reorders the entries within every list of the nl list blocks for the shared-memory banks of the kernels that sum
-// them (word = 8: the FP64 fixed-point image, 4: FP32 data); max_group = the largest number of entries of G = 128 /
-// word consecutive lists (G aligned) of one block (above 80K entries the lists keep their fill order).  After the
-// fill, before any use of the lists.
-void launch_sketch_schedule(int nl, int s, int word, int max_group, const int* seg, uint16_t* ent, cudaStream_t st);
+// them (word = 8: the FP64 fixed-point image, 4: FP32 data); max_group = G = 128 / word times the longest list,
+// padding included (above 80K entries the lists keep their fill order).  After the fill, before any use of the lists.
+void launch_sketch_schedule(int nl, int s, int word, int max_group, const int* gseg, uint16_t* ent, cudaStream_t st);
 // part[b*s + r] = per-block sketch sums of (scale_p * x) with scale_p = xscale[p * xstride] (1 if xscale is NULL);
 // optionally stores (VT)(scale_p * x) into dst.  Skips done problems.
 void launch_sketch_partials(const Plan& p, const double* x, const double* xscale, int xstride, void* dst,

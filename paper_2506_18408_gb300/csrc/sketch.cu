@@ -5,6 +5,11 @@
 // fused inner kernel uses) and each sketch row r, the list of (local offset, sign) of the columns j in the block
 // with S_rj != 0.  A kernel that holds the block of a vector in shared memory then forms its partial S x by summing
 // each sketch row's list in a fixed order -- deterministic, no atomics on floating-point data.
+//
+// Layout: the sketch rows of a block form groups of 32 (group g: rows 32g .. 32g + 31, summed by the 32 lanes of one
+// warp in lockstep).  A group's lists are stored interleaved in 16-byte units of 8 entries -- unit u of lane l at
+// unit index gseg[k*ng + g] + 32u + l -- so that each load of a warp reads 512 contiguous bytes; every list of the
+// group is padded to the group's longest (E units), with entries that point at the block's zero slot.
 #include "kernels.h"
 
 #include <algorithm>
@@ -58,15 +63,14 @@ __global__ void k_seg_count(int n, int s, int zeta, int Bq, const int* __restric
     for (int l = 0; l < zeta; ++l) atomicAdd(counts + (int64_t)k * s + rows[j * zeta + l], 1);
 }
 
-// seg[0..len] = base + exclusive prefix sum of the list lengths rounded up to multiples of 8 (counts[0..len)), so
-// every list starts on a 16-byte boundary (single block).
+// seg[0..len] = base + exclusive prefix sum of counts[0..len) (single block).
 __global__ void k_scan_single(const int* __restrict__ counts, int* __restrict__ seg, int len, int base) {
     __shared__ int sums[1024];
     const int tid = threadIdx.x, T = blockDim.x;
     const int chunk = (len + T - 1) / T;
     const int a = min(len, tid * chunk), bnd = min(len, a + chunk);
     int local = 0;
-    for (int i = a; i < bnd; ++i) local += (counts[i] + 7) & ~7;
+    for (int i = a; i < bnd; ++i) local += counts[i];
     sums[tid] = local;
     __syncthreads();
     for (int off = 1; off < T; off <<= 1) {  // Hillis-Steele inclusive scan of the per-thread totals
@@ -78,9 +82,21 @@ __global__ void k_scan_single(const int* __restrict__ counts, int* __restrict__ 
     int run = base + sums[tid] - local;
     for (int i = a; i < bnd; ++i) {
         seg[i] = run;
-        run += (counts[i] + 7) & ~7;
+        run += counts[i];
     }
     if (tid == T - 1) seg[len] = base + sums[T - 1];
+}
+
+// units[k*ng + g] = 32 * E(k, g): the 16-byte units of group g of block k, E the group's longest list in units of
+// 8 entries (counts[k*s + r]: the list lengths).
+__global__ void k_group_units(int nl, int s, const int* __restrict__ counts, int* __restrict__ units) {
+    const int ng = (s + 31) / 32;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nl * ng) return;
+    const int k = (int)(t / ng), g = (int)(t % ng);
+    int e = 0;
+    for (int r = 32 * g; r < min(s, 32 * g + 32); ++r) e = max(e, (counts[(int64_t)k * s + r] + 7) >> 3);
+    units[t] = 32 * e;
 }
 
 __global__ void k_fill_u16(int64_t cnt, uint16_t v, uint16_t* __restrict__ o) {
@@ -88,11 +104,13 @@ __global__ void k_fill_u16(int64_t cnt, uint16_t v, uint16_t* __restrict__ o) {
         o[i] = v;
 }
 
-// Fill the gather lists of block k (one warp per block).  Entries of a list appear in the order
-// (column chunk of 32, slot l, lane), which is fixed, so the sums formed from them are reproducible.
+// Fill the gather lists of block k (one warp per block; gseg: the block's group starts in units).  Entries of a list
+// appear in the order (column chunk of 32, slot l, lane), which is fixed, so the sums formed from them are
+// reproducible.
 __global__ void k_seg_fill(int n, int s, int zeta, int Bq, const int* __restrict__ rows,
-                           const int8_t* __restrict__ neg, const int* __restrict__ seg,
+                           const int8_t* __restrict__ neg, const int* __restrict__ gseg,
                            uint16_t* __restrict__ ent) {
+    const int ng = (s + 31) / 32;
     extern __shared__ int cursor[];
     const int k = blockIdx.x, lane = threadIdx.x;
     for (int r = lane; r < s; r += 32) cursor[r] = 0;
@@ -106,9 +124,9 @@ __global__ void k_seg_fill(int n, int s, int zeta, int Bq, const int* __restrict
             const int r = ok ? rows[(int64_t)j * zeta + l] : -1;
             const unsigned peers = __match_any_sync(0xffffffffu, r);
             if (ok) {
-                const int rank = __popc(peers & lt);
-                const int pos = seg[(int64_t)k * s + r] + cursor[r] + rank;
-                ent[pos] = (uint16_t)((j - c0) | (neg[(int64_t)j * zeta + l] ? 0x8000 : 0));
+                const int e = cursor[r] + __popc(peers & lt);  // entry e of the list of row r
+                const int64_t unit = (int64_t)gseg[(int64_t)k * ng + (r >> 5)] + 32 * (e >> 3) + (r & 31);
+                ent[unit * 8 + (e & 7)] = (uint16_t)((j - c0) | (neg[(int64_t)j * zeta + l] ? 0x8000 : 0));
             }
             __syncwarp();
             if (ok && lane == __ffs(peers) - 1) cursor[r] += __popc(peers);
@@ -117,40 +135,44 @@ __global__ void k_seg_fill(int n, int s, int zeta, int Bq, const int* __restrict
     }
 }
 
-// Reorders the entries within each gather list for the shared-memory banks.  The lists of G consecutive sketch rows
-// (G aligned) are summed in lockstep by G lanes that share one shared-memory wavefront -- entry e of every list at
-// step e -- and two lanes whose entries at a step lie in the same bank (offset mod G, for words of 128/G bytes: G = 16
-// for the FP64 fixed-point image, read in half-warps, 32 for FP32 data) serialise.  Each CTA takes one such group of
-// one row block: its lists are bucketed by residue (stably, in shared memory), then step by step the lanes, in an
-// order rotating with the step, each take the next entry of the residue that is least used at this step so far
-// (ties: the lane's fullest bucket, then the lowest residue).  Only the order within a list changes, and it is a
-// fixed function of the list contents, so the sums stay reproducible (the FP64 ones are exact in any order).
+// Reorders the entries within each gather list for the shared-memory banks.  The lanes of a warp sum the lists of
+// their group in lockstep (entry e of every list at step e), and two lanes that share one shared-memory wavefront
+// and read the same bank at a step serialise: G = 16 lanes (a half-warp) for the 8-byte words of the FP64
+// fixed-point image, 32 for FP32 data; the bank of an entry is its offset mod G.  Each CTA takes the G lists of one
+// half-group or group (G aligned) of one row block, all E * 8 entries long (padding included): they are bucketed by
+// residue (stably, in shared memory), then step by step the lanes, in an order rotating with the step, each take the
+// next entry of the residue that is least used at this step so far (ties: the lane's fullest bucket, then the lowest
+// residue).  Only the order within a list changes, and it is a fixed function of the list contents, so the sums stay
+// reproducible (the FP64 ones are exact in any order).
 template <int G>
-__global__ void k_seg_schedule(int nl, int s, const int* __restrict__ seg, uint16_t* __restrict__ ent) {
+__global__ void k_seg_schedule(int nl, int s, const int* __restrict__ gseg, uint16_t* __restrict__ ent) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int cnt[G * G], pos[G * G], cur[G * G], rem[G], outp[G];
     uint16_t* buf = reinterpret_cast<uint16_t*>(smem_raw);
+    const int ng = (s + 31) / 32;
     const int l = threadIdx.x;
-    const int r0 = blockIdx.x * G, r1 = min(s, r0 + G);
-    const int nr = r1 - r0;
+    const int r0 = blockIdx.x * G, nr = min(G, s - r0);
+    const int g = r0 >> 5, lo = r0 & 31;
+    // position (in entries) of entry e of lane q of this group of lanes
+    auto at = [&](int64_t gstart, int q, int e) -> int64_t { return (gstart + 32 * (e >> 3) + lo + q) * 8 + (e & 7); };
     for (int k = blockIdx.y; k < nl; k += gridDim.y) {
-        const int* sg = seg + (int64_t)k * s;
-        const int base = sg[r0];
+        const int64_t gstart = gseg[(int64_t)k * ng + g];
+        const int L = 8 * ((gseg[(int64_t)k * ng + g + 1] - (int)gstart) / 32);  // entries per list
         for (int i = l; i < G * G; i += blockDim.x) cnt[i] = 0;
         __syncthreads();
         if (l < nr) {
-            const int a = sg[r0 + l] - base, e = sg[r0 + l + 1] - base;
-            rem[l] = e - a;
-            outp[l] = a;
-            for (int p = a; p < e; ++p) ++cnt[l * G + (ent[base + p] & 0x7fff) % G];
+            const int a = l * L;  // the lane's region of buf
+            rem[l] = L;
+            outp[l] = 0;
+            for (int e = 0; e < L; ++e) ++cnt[l * G + (ent[at(gstart, l, e)] & 0x7fff) % G];
             int run = a;
             for (int r = 0; r < G; ++r) {
                 pos[l * G + r] = run;
                 cur[l * G + r] = run;
                 run += cnt[l * G + r];
             }
-            for (int p = a; p < e; ++p) {
-                const uint16_t v = ent[base + p];
+            for (int e = 0; e < L; ++e) {
+                const uint16_t v = ent[at(gstart, l, e)];
                 buf[cur[l * G + (v & 0x7fff) % G]++] = v;
             }
         }
@@ -176,7 +198,7 @@ __global__ void k_seg_schedule(int nl, int s, const int* __restrict__ seg, uint1
                     ++used[pick];
                     --cnt[li * G + pick];
                     --rem[li];
-                    ent[base + outp[li]++] = buf[pos[li * G + pick]++];
+                    ent[at(gstart, li, outp[li]++)] = buf[pos[li * G + pick]++];
                 }
                 if (!any) break;
             }
@@ -185,16 +207,22 @@ __global__ void k_seg_schedule(int nl, int s, const int* __restrict__ seg, uint1
     }
 }
 
-void launch_sketch_schedule(int nl, int s, int word, int max_group, const int* seg, uint16_t* ent, cudaStream_t st) {
+void launch_sketch_schedule(int nl, int s, int word, int max_group, const int* gseg, uint16_t* ent, cudaStream_t st) {
     const size_t sm = ((size_t)max_group * sizeof(uint16_t) + 15) & ~(size_t)15;
     if (sm > 160 * 1024) return;  // very few sketch rows per block: the lists keep their fill order
     if (word == 8) {
         set_smem((const void*)k_seg_schedule<16>, sm);
-        k_seg_schedule<16><<<dim3((s + 15) / 16, std::min(nl, 65535)), 32, sm, st>>>(nl, s, seg, ent);
+        k_seg_schedule<16><<<dim3((s + 15) / 16, std::min(nl, 65535)), 32, sm, st>>>(nl, s, gseg, ent);
     } else {
         set_smem((const void*)k_seg_schedule<32>, sm);
-        k_seg_schedule<32><<<dim3((s + 31) / 32, std::min(nl, 65535)), 32, sm, st>>>(nl, s, seg, ent);
+        k_seg_schedule<32><<<dim3((s + 31) / 32, std::min(nl, 65535)), 32, sm, st>>>(nl, s, gseg, ent);
     }
+    ++g_launches;
+}
+
+void launch_group_units(int nl, int s, const int* counts, int* units, cudaStream_t st) {
+    const int64_t t = (int64_t)nl * ((s + 31) / 32);
+    k_group_units<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(nl, s, counts, units);
     ++g_launches;
 }
 
@@ -208,10 +236,10 @@ void launch_list_scan(const int* counts, int* seg, int len, cudaStream_t st) {
     ++g_launches;
 }
 
-void launch_sketch_fill(int n, int s, int zeta, int Bq, const int* rows, const int8_t* neg, const int* seg,
+void launch_sketch_fill(int n, int s, int zeta, int Bq, const int* rows, const int8_t* neg, const int* gseg,
                         uint16_t* ent, cudaStream_t st) {
     const int nl = (n + Bq - 1) / Bq;
-    k_seg_fill<<<nl, 32, s * sizeof(int), st>>>(n, s, zeta, Bq, rows, neg, seg, ent);
+    k_seg_fill<<<nl, 32, s * sizeof(int), st>>>(n, s, zeta, Bq, rows, neg, gseg, ent);
     ++g_launches;
 }
 
@@ -248,7 +276,8 @@ __global__ void __launch_bounds__(512) k_sketch_partials(const Plan P, const dou
         xb[r] = v;
         emax = max(emax, exp_of(v));
     }
-    const int* sg = P.seg + (int64_t)bi.list * s;
+    const int ng = (s + 31) / 32;
+    const int* sg = P.seg + (int64_t)bi.list * ng;  // the block's group starts (units)
     if constexpr (sizeof(AT) == 8) {
         emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
         if ((threadIdx.x & 31) == 0) emax_sh[threadIdx.x >> 5] = emax;
@@ -261,13 +290,16 @@ __global__ void __launch_bounds__(512) k_sketch_partials(const Plan P, const dou
         const double unit = fixed_unit(0.0, Eb, P.sk_headroom);
         const bool bad = exp_nonfinite(0.0, Eb);
         for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
-            const long long v = sum_list(P.ent, sg[rr], sg[rr + 1], qb);
+            const int g = rr >> 5;
+            const long long v = sum_group(P.ent, sg[g], (sg[g + 1] - sg[g]) >> 5, rr & 31, qb);
             part[(int64_t)b * s + rr] = bad ? (AT)NAN : (AT)((double)v * unit);
         }
     } else {
         __syncthreads();
-        for (int rr = threadIdx.x; rr < s; rr += blockDim.x)
-            part[(int64_t)b * s + rr] = sum_list(P.ent, sg[rr], sg[rr + 1], xb);
+        for (int rr = threadIdx.x; rr < s; rr += blockDim.x) {
+            const int g = rr >> 5;
+            part[(int64_t)b * s + rr] = sum_group(P.ent, sg[g], (sg[g + 1] - sg[g]) >> 5, rr & 31, xb);
+        }
     }
 }
 

@@ -27,8 +27,10 @@ Tolerances, with eps32 = 2^-24 and the BF16 unit u16 = 2^-8:
   (the first-order bound delta ||S A B_k|| ||y_k|| / rho_k is of order one for the 60- and 100-column cycles of the
   full-size workloads, kappa(S A B_k) ~ 7e4; the differences measured there are about 1e-3, and an FP32 oracle differs
   from the FP64 oracle by as much), BF16 within 2^-4.  The inner lengths of the leading cycles that the oracle ended
-  by rule C1 agree for FP64 and FP32; with a BF16 basis the estimates that decide rule C3 drift apart by the 8-bit
-  noise, so only counts and residuals are compared.  With a BF16 basis each outer step reduces the
+  by rule C1 and that start from a residual above 10 tol agree for FP64 and FP32 (closer to tol, rule C3 can end a
+  cycle as soon as its sketched residual falls below tol / ||r~_{j-1}|| > 0.1, a point that moves with the rounding);
+  with a BF16 basis the estimates that decide rule C3 drift apart by the 8-bit noise, so only counts and residuals
+  are compared.  With a BF16 basis each outer step reduces the
   residual by about the accuracy of the 8-bit basis, so which of two close steps meets 1e-8 depends on the roundings:
   the GPU's storage (the vector scaled by a power of two) and the oracle's (the normalised vector) round
   independently, and on the 12-system batch that alone moves single counts by up to 2 (an oracle copy storing the
@@ -157,9 +159,14 @@ def _check_solve_against_golden(info, rel, g, est_tol, count_tol=1):
     assert abs(est[0] - g["est_hist"][0]) <= est_tol * g["est_hist"][0], (est[0], g["est_hist"][0])
     if g["inner"] == "bf16":
         return
-    # the leading cycles that the oracle ended by rule C1 (k = m) have the same length on the GPU; the cycles ended by
-    # rule C3 near convergence compare two nearly equal numbers and may end a step apart
-    lead = next((j for j, r in enumerate(g["inner_reason"]) if r != 1), len(g["inner_reason"]))
+    # the leading cycles that the oracle ended by rule C1 (k = m) have the same length on the GPU, as long as they start
+    # from a residual above 10 tol: rule C3 (the Eq. 5 bound ||r~_{j-1}|| rho_k against tol ||b||) can end a cycle
+    # that starts closer to tol as soon as its sketched residual rho_k falls below tol ||b|| / ||r~_{j-1}|| > 0.1,
+    # which these 60-step cycles reach, and where it fires then depends on the rounding of the low-precision cycles
+    start = [g["est_hist"][j - 1] if j > 0 else np.inf for j in range(len(g["inner_reason"]))]
+    lead = next((j for j, r in enumerate(g["inner_reason"]) if r != 1 or start[j] <= 10 * g["tol"]),
+                len(g["inner_reason"]))
+    print("GPU inner_k", info["inner_k"], "reasons", info["inner_reason"], "est", ["%.3e" % e for e in est])
     assert info["inner_k"][:lead] == g["inner_k"][:lead], (info["inner_k"], g["inner_k"])
 
 
