@@ -288,10 +288,12 @@ void set_list_geometry(sfgmres_ctx* h) {
     ++h->geo_ver;
 }
 
-// CTAs per problem of the sketched-QR update: as many as the batch leaves room for.  The update is bound by the
-// latency of its reads, so even small sketches run faster on a cluster of eight CTAs than on one (measured on the 2D
-// 64^2 workload, s = 120, m = 30: 19 us per update on one CTA against 13 us on eight).
-int qr_cluster_for(int P) {
+// CTAs per problem of the sketched-QR update.  Small sketches of few problems: 0, the single-CTA kernel (512 threads;
+// its reductions cost shared-memory barriers instead of cluster barriers and distributed-shared-memory exchanges).
+// Otherwise a cluster with as many CTAs as the batch leaves room for: the update is bound by the latency of its
+// reads, which more SMs hide better.
+int qr_cluster_for(int P, int s, int m) {
+    if (P <= kQrSmallProblems && qr_small_fits(s, m)) return 0;  // one CTA per problem
     if (P <= 16) return kQrCluster;
     if (P <= 32) return 4;
     if (P <= 64) return 2;
@@ -927,7 +929,7 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     P.coef = (double*)h->coef.p;
     P.hco = (double*)h->hco.p;
     P.cyc = (CycleState*)h->cyc.p;
-    P.qr_cluster = qr_cluster_for(g->P);
+    P.qr_cluster = qr_cluster_for(g->P, s, m);
     P.jmax = jmax;
     P.Vb = (double*)h->Vb.p;
     P.Z = (double*)h->Z.p;

@@ -49,13 +49,13 @@ __device__ __forceinline__ double qr_rank_sum(cg::cluster_group& cl, double* bas
     return acc;
 }
 
-// Sum over the CTA's 128 threads of v (warp trees, then the 4 warps in order); valid in every thread.
+// Sum over the CTA's 128 threads of v (warp trees, then the 4 warps in order); valid in thread 0 (0 elsewhere).
 __device__ __forceinline__ double qr_block_sum(double v, double* red4) {
     v = warp_sum(v);
     __syncthreads();  // red4 is free (its previous values have been read)
     if ((threadIdx.x & 31) == 0) red4[threadIdx.x >> 5] = v;
     __syncthreads();
-    return (red4[0] + red4[1]) + (red4[2] + red4[3]);
+    return (threadIdx.x == 0) ? (red4[0] + red4[1]) + (red4[2] + red4[3]) : 0.0;
 }
 
 // Sum of x[u] * y[u] for u in [0, cnt), x contiguous (each lane of a warp streams its own stretch of Q, so every load
@@ -103,6 +103,8 @@ __global__ void __launch_bounds__(kQrThreads, 9) k_inner_qr(const Plan P, int i)
     double* a = apart + 2 * m;     // [m] full projections
     __shared__ double red4[4];
     __shared__ double scal[4];
+    __shared__ double bc[4];            // scalars formed by thread 0 for the CTA (FP64 division and square roots
+                                        // cost tens of FP64-pipe cycles per warp: once per CTA, not per thread)
     __shared__ double grp[kQrThreads];  // group partials of a split projection or subtraction
     const int tid = threadIdx.x;
     // the cycle state as earlier launches left it (the same for every CTA of the cluster)
@@ -179,11 +181,19 @@ __global__ void __launch_bounds__(kQrThreads, 9) k_inner_qr(const Plan P, int i)
         scal[1] = pe;
     }
     cl.sync();
-    const double rii = sqrt(qr_rank_sum(cl, scal, 0, nq));
-    const double pet = qr_rank_sum(cl, scal, 1, nq);
+    if (tid == 0) {
+        const double rii0 = sqrt(qr_rank_sum(cl, scal, 0, nq));
+        const double dmx = fmax(dmax0, rii0);
+        const double dmn = (i == 0) ? rii0 : fmin(dmin0, rii0);
+        bc[0] = rii0;
+        bc[1] = qr_rank_sum(cl, scal, 1, nq);
+        bc[2] = (dmn > 0.0) ? dmx / dmn : INFINITY;  // the condition proxy
+        bc[3] = 1.0 / rii0;
+    }
+    __syncthreads();
+    const double rii = bc[0], pet = bc[1], kappa = bc[2], inv = bc[3];
     const double dmax = fmax(dmax0, rii);
     const double dmin = (i == 0) ? rii : fmin(dmin0, rii);
-    const double kappa = (dmin > 0.0) ? dmax / dmin : INFINITY;
     if (!(kappa <= thr)) {  // C2 (also rii == 0 or NaN): drop column i, keep k = i
         if (q == 0 && tid == 0) {
             cyc->stopped = 1;
@@ -193,7 +203,6 @@ __global__ void __launch_bounds__(kQrThreads, 9) k_inner_qr(const Plan P, int i)
         cl.sync();  // no CTA leaves while another may still read its shared memory
         return;
     }
-    const double inv = 1.0 / rii;
     const double di = pet * inv;
     double ee = 0.0;
     for (int r = tid; r < nr; r += kQrThreads) {
@@ -207,8 +216,8 @@ __global__ void __launch_bounds__(kQrThreads, 9) k_inner_qr(const Plan P, int i)
     ee = qr_block_sum(ee, red4);
     if (tid == 0) scal[2] = ee;
     cl.sync();
-    const double rh = sqrt(qr_rank_sum(cl, scal, 2, nq));
     if (q == 0 && tid == 0) {
+        const double rh = sqrt(qr_rank_sum(cl, scal, 2, nq));
         R[(int64_t)i * m + i] = rii;
         d[i] = di;
         rho[i] = rh;
@@ -225,6 +234,163 @@ __global__ void __launch_bounds__(kQrThreads, 9) k_inner_qr(const Plan P, int i)
         }
     }
     cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// The same sketched QR update for small sketches (qr_small_fits, few problems), one CTA of kQrSmallThreads
+// threads per problem and no cluster.  An update of a small sketch is a chain of dependent steps whose cost is the
+// number of round trips to memory, so every global input -- the columns 0..i-1 of Q, the new column of C, the
+// residual sketch e, the cycle state -- is loaded into shared memory in one wave of loads at the start, and the two
+// Gram-Schmidt passes, the norms and the stop tests then run on shared memory (block barriers instead of cluster
+// barriers and distributed-shared-memory exchanges).  Projections: warp w takes columns w, w + 16, ..., its lanes
+// strided over the rows, then the warp's shuffle tree.  Subtraction: G threads per row (G s <= the CTA), each over a
+// contiguous share of the columns, the G partials added by a shuffle tree.  Block sums: warp trees, then the warps
+// in order.  Only Q is written (not its row-major copy Qt, which only the cluster kernel reads).  The decisions
+// (rules C1-C3, the breakdown and C2 stops) are those of k_inner_qr.
+constexpr int kQrSmallThreads = 512;
+
+// Sum of v over the threads of the first nws warps (the others hold no rows): warp trees, then the warps in order;
+// valid in thread 0 (0 elsewhere).  FP64 arithmetic is scarce on this GPU, so no thread adds what it does not need.
+__device__ __forceinline__ double qr_small_sum(double v, double* red, int nws) {
+    const int warp = threadIdx.x >> 5;
+    if (warp < nws) v = warp_sum(v);
+    __syncthreads();  // red is free (its previous values have been read)
+    if (warp < nws && (threadIdx.x & 31) == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nws; ++w) t += red[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(kQrSmallThreads) k_inner_qr_small(const Plan P, int i) {
+    constexpr int nw = kQrSmallThreads / 32;
+    const int prob = blockIdx.x;
+    const int s = P.s, m = P.m;
+    const double* __restrict__ C = P.C + (int64_t)prob * m * s;
+    double* __restrict__ Q = P.Q + (int64_t)prob * m * s;
+    double* __restrict__ R = P.R + (int64_t)prob * m * m;
+    double* __restrict__ d = P.d + (int64_t)prob * m;
+    double* __restrict__ e = P.e + (int64_t)prob * s;
+    double* __restrict__ rho = P.rho + (int64_t)prob * m;
+    CycleState* cyc = P.cyc + prob;
+    extern __shared__ double qsm[];
+    double* qs = qsm;              // [i s] columns 0..i-1 of Q (column-major)
+    double* p = qs + (int64_t)i * s;  // [s] the working vector
+    double* es = p + s;            // [s] e
+    double* a1 = es + s;           // [m] first-pass projections
+    double* a = a1 + m;            // [m] projections of the current pass
+    __shared__ double red[nw];
+    __shared__ double cst[3];
+    __shared__ double bc[4];  // scalars formed by thread 0 (one square root and divisions per update, not per thread)
+    __shared__ int code_sh;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        cst[0] = cyc->dmax;
+        cst[1] = cyc->dmin;
+        cst[2] = cyc->cond_thr;
+        code_sh = (cyc->stopped || (P.pflag[prob] & 1)) ? 1 : (cyc->brk_step <= i ? 2 : 0);
+    }
+    const int nq = i * s;
+    for (int k = tid; k < nq; k += kQrSmallThreads) qs[k] = Q[k];
+    for (int r = tid; r < s; r += kQrSmallThreads) {
+        p[r] = C[(int64_t)i * s + r];
+        es[r] = e[r];
+    }
+    __syncthreads();
+    const int code = code_sh;
+    if (code) {
+        if (code == 2 && tid == 0) {
+            cyc->stopped = 1;  // u_i has zero (or non-finite) norm: the cycle keeps k = i columns
+            cyc->reason = cyc->brk_reason;
+        }
+        return;
+    }
+    int G = 1;
+    while (G < 32 && 2 * G * s <= kQrSmallThreads) G *= 2;
+    const int rg = tid / G, gg = tid % G;
+    const int c0 = i * gg / G, c1 = i * (gg + 1) / G;
+    for (int pass = 0; pass < 2; ++pass) {
+        // a = Q^T p: column l by warp l % nw
+        for (int l = warp; l < i; l += nw) {
+            const double* ql = qs + (int64_t)l * s;
+            double acc = 0.0;
+            for (int r = lane; r < s; r += 32) acc = fma(ql[r], p[r], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) a[l] = acc;
+        }
+        __syncthreads();
+        // p -= Q a: row r by its G threads
+        for (int base = 0; base < s; base += kQrSmallThreads / G) {  // the same trip count in every thread
+            const int r = base + rg;
+            double acc = 0.0;
+            if (r < s)
+                for (int l = c0; l < c1; ++l) acc = fma(qs[(int64_t)l * s + r], a[l], acc);
+            for (int o = 1; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);  // all lanes take part
+            if (r < s && gg == 0) p[r] -= acc;
+        }
+        if (pass == 0)
+            for (int l = tid; l < i; l += kQrSmallThreads) a1[l] = a[l];
+        __syncthreads();
+    }
+    for (int l = tid; l < i; l += kQrSmallThreads) R[(int64_t)i * m + l] = a1[l] + a[l];
+    // r_ii = ||p|| and p^T e
+    const int nws = (min(s, kQrSmallThreads) + 31) / 32;  // warps that hold rows
+    double v2 = 0.0, pe = 0.0;
+    for (int r = tid; r < s; r += kQrSmallThreads) {
+        v2 = fma(p[r], p[r], v2);
+        pe = fma(p[r], es[r], pe);
+    }
+    v2 = qr_small_sum(v2, red, nws);
+    pe = qr_small_sum(pe, red, nws);
+    if (tid == 0) {
+        const double rii0 = sqrt(v2);
+        const double dmx = fmax(cst[0], rii0);
+        const double dmn = (i == 0) ? rii0 : fmin(cst[1], rii0);
+        bc[0] = rii0;
+        bc[1] = pe;
+        bc[2] = (dmn > 0.0) ? dmx / dmn : INFINITY;  // the condition proxy
+        bc[3] = 1.0 / rii0;
+    }
+    __syncthreads();
+    const double rii = bc[0], pet = bc[1], kappa = bc[2], inv = bc[3];
+    const double dmax = fmax(cst[0], rii);
+    const double dmin = (i == 0) ? rii : fmin(cst[1], rii);
+    if (!(kappa <= cst[2])) {  // C2 (also rii == 0 or NaN): drop column i, keep k = i
+        if (tid == 0) {
+            cyc->stopped = 1;
+            cyc->k = i;
+            cyc->reason = (i == 0) ? 5 : 2;
+        }
+        return;
+    }
+    const double di = pet * inv;
+    double ee = 0.0;
+    for (int r = tid; r < s; r += kQrSmallThreads) {
+        const double qv = p[r] * inv;
+        Q[(int64_t)i * s + r] = qv;
+        const double ev = es[r] - di * qv;
+        e[r] = ev;
+        ee = fma(ev, ev, ee);
+    }
+    ee = qr_small_sum(ee, red, nws);
+    if (tid == 0) {
+        const double rh = sqrt(ee);
+        R[(int64_t)i * m + i] = rii;
+        d[i] = di;
+        rho[i] = rh;
+        cyc->dmax = dmax;
+        cyc->dmin = dmin;
+        cyc->k = i + 1;
+        cyc->rho = rh;
+        if (cyc->c3_on && cyc->c3_scale * rh <= cyc->c3_tol) {
+            cyc->stopped = 1;
+            cyc->reason = 3;
+        } else if (i + 1 == m) {
+            cyc->stopped = 1;
+            cyc->reason = 1;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------------------------------------
@@ -406,6 +572,13 @@ void launch_inner_axpy(const Plan& p, int i, bool last) {
 }
 
 cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st) {
+    if (p.qr_cluster == 0) {  // small sketch: one CTA per problem, Q's columns 0..i-1 in shared memory
+        const size_t sm = ((size_t)i * p.s + 2 * (size_t)p.s + 2 * (size_t)p.m) * sizeof(double);
+        set_smem((const void*)k_inner_qr_small, sm);
+        k_inner_qr_small<<<p.P, kQrSmallThreads, sm, st>>>(p, i);
+        ++g_launches;
+        return cudaGetLastError();
+    }
     const int nq = p.qr_cluster;
     const int nrmax = (p.s + nq - 1) / nq;
     const size_t sm = (size_t)(nrmax + 3 * p.m) * sizeof(double);

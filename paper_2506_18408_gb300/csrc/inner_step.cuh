@@ -252,7 +252,7 @@ __device__ __forceinline__ bool inner_spmv_part(const Plan& P, int i, const MT* 
         emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
         if (lane == 0) emax_sh[warp] = emax;
         __syncthreads();
-        if (threadIdx.x < NW) {
+        if ((int)threadIdx.x < NW) {
             AT t = AT(0);
             for (int w = 0; w < nw; ++w) t += red2[threadIdx.x][w];
             ((AT*)P.hpart)[(int64_t)b * kMaxTrunc + threadIdx.x] = t;

@@ -112,7 +112,7 @@ struct Plan {
     double* coef = nullptr;    // [P][m]     y_l * sigma_l
     double* hco = nullptr;     // [P][m][kMaxTrunc] truncated-Arnoldi coefficients
     CycleState* cyc = nullptr; // [P]
-    int qr_cluster = 8;        // CTAs per problem in the sketched-QR kernel (1 for small s m)
+    int qr_cluster = 8;        // CTAs per problem (one cluster) in the sketched-QR kernel; 0: the single-CTA kernel
 
     // outer FGMRES
     int jmax = 0;
@@ -216,7 +216,12 @@ void inner_axpy_f64(const Plan& p, int i, bool last);
 void inner_axpy_f32(const Plan& p, int i, bool last);
 void inner_axpy_bf16(const Plan& p, int i, bool last);
 void launch_inner_axpy(const Plan& p, int i, bool last);
-cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st);  // cluster launch on stream st
+// Sketches whose QR working set fits in kQrSmallElems doubles of shared memory (columns 0..m-2 of Q, the new column,
+// e, two projection vectors), for at most kQrSmallProblems problems, take the single-CTA sketched QR.
+constexpr int kQrSmallElems = 24576;  // 192 KB
+constexpr int kQrSmallProblems = 16;
+inline bool qr_small_fits(int s, int m) { return (int64_t)s * (m + 1) + 2 * (int64_t)m <= kQrSmallElems; }
+cudaError_t launch_inner_qr(const Plan& p, int i, cudaStream_t st);  // on stream st (cluster or single-CTA kernel)
 void launch_inner_finish(const Plan& p, double* z);  // y = R^{-1} d, z = sum_l y_l b_l (FP64)
 void launch_export_basis(const Plan& p, double* out, int count);  // out[l*N + r] = sigma_l * u_l[r] (FP64)
 
