@@ -409,6 +409,36 @@ __global__ void __launch_bounds__(kLsThreads) k_inner_ls(const Plan P) {
     double* y = P.y + (int64_t)p * m;
     double* coef = P.coef + (int64_t)p * m;
     const int k = P.cyc[p].k;
+    if (k <= 32) {
+        // one warp: lane q holds row q of the right-hand side, its row of R (one load wave) and 1 / r_qq (the
+        // divisions of all rows at once); step l forms y_l = rhs_l (1 / r_ll) in lane l, shuffles it to the other
+        // lanes, and the rows above l subtract r_ql y_l in parallel -- warp shuffles instead of block barriers and one
+        // FP64 multiply-add per step on the critical path
+        if (threadIdx.x >= 32) return;
+        const int q = threadIdx.x;
+        double r = (q < k) ? d[q] : 0.0;
+        double rq[32];
+#pragma unroll
+        for (int l = 0; l < 32; ++l) rq[l] = (l < k && q <= l) ? R[(int64_t)l * m + q] : 0.0;
+        double rqq = 1.0;
+#pragma unroll
+        for (int l = 0; l < 32; ++l)
+            if (l == q && q < k) rqq = rq[l];
+        const double inv = 1.0 / rqq;
+        for (int l = k - 1; l >= 0; --l) {
+            double rql = 0.0;  // r_ql of this lane's row
+#pragma unroll
+            for (int u = 0; u < 32; ++u)
+                if (u == l) rql = rq[u];
+            const double yl = __shfl_sync(0xffffffffu, r * inv, l);
+            if (q < l) r = fma(-rql, yl, r);
+            if (q == l) {
+                y[l] = yl;
+                coef[l] = yl * sigma[l];
+            }
+        }
+        return;
+    }
     for (int l = threadIdx.x; l < k; l += kLsThreads) rhs[l] = d[l];
     // this thread's rows q = threadIdx.x + 128 j; its entries of the current column l are loaded one column ahead
     constexpr int kRows = kMaxM / kLsThreads;

@@ -322,25 +322,38 @@ void launch_sketch_partials(const Plan& p, const double* x, const double* xscale
     ++g_launches;
 }
 
-// out[p*s + r] = sk_scale * sum over the blocks of problem p of part[b*s + r] (block order).
+// out[p*s + r] = sk_scale * sum over the blocks of problem p of part[b*s + r]: one warp per (p, r), lane l summing
+// blocks b0 + l, b0 + l + 32, ... in order with all its loads issued first, then the warp's shuffle tree (a fixed
+// order: reproducible).
 template <typename AT>
 __global__ void k_sketch_reduce(const Plan P, const AT* __restrict__ part, double* __restrict__ out,
                                 double* __restrict__ out2) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     const int s = P.s;
-    if (t >= (int64_t)P.P * s) return;
+    if (t >= (int64_t)P.P * s) return;  // warp-uniform
     const int p = (int)(t / s), r = (int)(t % s);
     if (P.pflag[p] & 1) return;
+    const int b0 = P.prob_b0[p], b1 = P.prob_b0[p + 1];
     AT acc = AT(0);
-    for (int b = P.prob_b0[p]; b < P.prob_b0[p + 1]; ++b) acc += part[(int64_t)b * s + r];
-    const double v = P.sk_scale * (double)acc;
-    out[t] = v;
-    if (out2) out2[t] = v;
+    for (int q0 = b0 + lane; q0 < b1; q0 += 128) {
+        AT v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (q0 + 32 * u < b1) ? part[(int64_t)(q0 + 32 * u) * s + r] : AT(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc += v[u];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        const double v = P.sk_scale * (double)acc;
+        out[t] = v;
+        if (out2) out2[t] = v;
+    }
 }
 
 void launch_sketch_reduce(const Plan& p, const void* part, double* out, double* out2) {
-    const int64_t tot = (int64_t)p.P * p.s;
-    const int th = 128, gr = (int)((tot + th - 1) / th);
+    const int64_t warps = (int64_t)p.P * p.s;
+    const int th = 256, gr = (int)((warps * 32 + th - 1) / th);
     if (p.prec == kFP64)
         k_sketch_reduce<double><<<gr, th, 0, p.st>>>(p, (const double*)part, out, out2);
     else
