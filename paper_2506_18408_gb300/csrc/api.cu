@@ -288,12 +288,15 @@ void set_list_geometry(sfgmres_ctx* h) {
     ++h->geo_ver;
 }
 
-// CTAs per problem of the sketched-QR update.  Small sketches of few problems: 0, the single-CTA kernel (512 threads;
-// its reductions cost shared-memory barriers instead of cluster barriers and distributed-shared-memory exchanges).
-// Otherwise a cluster with as many CTAs as the batch leaves room for: the update is bound by the latency of its
-// reads, which more SMs hide better.
-int qr_cluster_for(int P, int s, int m) {
-    if (P <= kQrSmallProblems && qr_small_fits(s, m)) return 0;  // one CTA per problem
+// CTAs per problem of the sketched-QR update.  Small sketches of few problems whose inner step leaves an SM with at
+// most one of its CTAs (nblk <= sms): 0, the single-CTA kernel (512 threads; its reductions cost shared-memory
+// barriers instead of cluster barriers and distributed-shared-memory exchanges).  It needs a large share of an SM's
+// registers and shared memory, so beside an inner step that fills every SM it would wait for the step to end (the
+// random Zipf workload, s = 240: 335 -> 361 ms per FP64 solve).  Otherwise a cluster of small CTAs (they fit beside
+// the step's) with as many CTAs as the batch leaves room for: the update is bound by the latency of its reads, which
+// more SMs hide better.
+int qr_cluster_for(int P, int s, int m, int nblk, int sms) {
+    if (P <= kQrSmallProblems && qr_small_fits(s, m) && nblk <= sms) return 0;  // one CTA per problem
     if (P <= 16) return kQrCluster;
     if (P <= 32) return 4;
     if (P <= 64) return 2;
@@ -929,7 +932,7 @@ int prepare(sfgmres_ctx* h, int nrhs, int m, int s, int t, int jmax, Plan* p, Ge
     P.coef = (double*)h->coef.p;
     P.hco = (double*)h->hco.p;
     P.cyc = (CycleState*)h->cyc.p;
-    P.qr_cluster = qr_cluster_for(g->P, s, m);
+    P.qr_cluster = qr_cluster_for(g->P, s, m, g->nblk, h->sms);
     P.jmax = jmax;
     P.Vb = (double*)h->Vb.p;
     P.Z = (double*)h->Z.p;

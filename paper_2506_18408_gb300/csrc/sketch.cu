@@ -142,12 +142,12 @@ __global__ void k_seg_fill(int n, int s, int zeta, int Bq, const int* __restrict
 // half-group or group (G aligned) of one row block, all E * 8 entries long (padding included): they are bucketed by
 // residue (stably, in shared memory), then step by step the lanes, in an order rotating with the step, each take the
 // next entry of the residue that is least used at this step so far (ties: the lane's fullest bucket, then the lowest
-// residue).  Only the order within a list changes, and it is a fixed function of the list contents, so the sums stay
+// residue; bucket sizes compared up to 4095), each choice one warp-wide min-reduction over the residues.  Only the order within a list changes, and it is a fixed function of the list contents, so the sums stay
 // reproducible (the FP64 ones are exact in any order).
 template <int G>
 __global__ void k_seg_schedule(int nl, int s, const int* __restrict__ gseg, uint16_t* __restrict__ ent) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int cnt[G * G], pos[G * G], cur[G * G], rem[G], outp[G];
+    __shared__ int cnt[G * G], pos[G * G], cur[G * G], outp[G];
     uint16_t* buf = reinterpret_cast<uint16_t*>(smem_raw);
     const int ng = (s + 31) / 32;
     const int l = threadIdx.x;
@@ -162,7 +162,6 @@ __global__ void k_seg_schedule(int nl, int s, const int* __restrict__ gseg, uint
         __syncthreads();
         if (l < nr) {
             const int a = l * L;  // the lane's region of buf
-            rem[l] = L;
             outp[l] = 0;
             for (int e = 0; e < L; ++e) ++cnt[l * G + (ent[at(gstart, l, e)] & 0x7fff) % G];
             int run = a;
@@ -177,30 +176,25 @@ __global__ void k_seg_schedule(int nl, int s, const int* __restrict__ gseg, uint
             }
         }
         __syncthreads();
-        if (l == 0) {
-            for (int step = 0;; ++step) {
-                int used[G];
-                for (int r = 0; r < G; ++r) used[r] = 0;
-                bool any = false;
-                for (int q = 0; q < nr; ++q) {
-                    const int li = (step + q) % nr;
-                    if (rem[li] == 0) continue;
-                    any = true;
-                    int pick = 0, pu = INT_MAX, pc = 0;
-                    for (int r = 0; r < G; ++r) {
-                        const int c = cnt[li * G + r];
-                        if (c > 0 && (used[r] < pu || (used[r] == pu && c > pc))) {
-                            pick = r;
-                            pu = used[r];
-                            pc = c;
-                        }
-                    }
-                    ++used[pick];
+        // the greedy, one lane per residue: for each list in turn the warp picks the residue with the smallest key
+        // (uses at this step, then the list's fewer remaining entries of that residue, then the residue) with one
+        // min-reduction; lane `pick` counts the use
+        const bool own = l < G;  // this lane owns residue l
+        for (int step = 0; step < L; ++step) {
+            int used = 0;
+            for (int q = 0; q < nr; ++q) {
+                const int li = (step + q) % nr;
+                const int c = own ? cnt[li * G + l] : 0;
+                const unsigned key = (c > 0) ? ((unsigned)used << 20) | ((unsigned)(0xFFF - min(c, 0xFFF)) << 5) | (unsigned)l
+                                             : 0xFFFFFFFFu;
+                const unsigned best = __reduce_min_sync(0xffffffffu, key);
+                const int pick = (int)(best & 31u);
+                if (l == pick) {
+                    ++used;
                     --cnt[li * G + pick];
-                    --rem[li];
                     ent[at(gstart, li, outp[li]++)] = buf[pos[li * G + pick]++];
                 }
-                if (!any) break;
+                __syncwarp();
             }
         }
         __syncthreads();
