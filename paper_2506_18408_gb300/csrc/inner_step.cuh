@@ -734,12 +734,13 @@ __device__ __forceinline__ void fused_phase2(const Plan& P, int i, int last, AT*
         }
         __syncwarp();
     }
-    // sketched column S A b_i = sigma_i S w': sketch row rr to warp rr / nb of the problem's block rr % nb, once every
-    // CTA's sketch partials are in place
+    // sketched column S A b_i = sigma_i S w': sketch row rr to warp nw - 1 - rr / nb of the problem's block rr % nb,
+    // once every CTA's sketch partials are in place (the last warps first: with few rows per block the update's
+    // chunks fall to the first warps)
     const double csc = P.sk_scale * sig_i;
     const int nb = b1 - b0;
     bool waited = false;
-    for (int rr = warp * nb + (b - b0); rr < s; rr += nw * nb) {
+    for (int rr = (nw - 1 - warp) * nb + (b - b0); rr < s; rr += nw * nb) {
         if (!waited) {
             if (lane == 0) grid_wait(P.gsync + 2, target, P.gsync + 1);
             __syncwarp();

@@ -129,6 +129,10 @@ SOLVE_CASES = [
     ("cd2d_64_t0", workloads.CONFIGS["cd2d_64"].build_matrix, 30, 120, 0, 20, True),
     ("zipf_20011", lambda: workloads.random_zipf(20_011, seed=0), 30, 120, 4, 50, True),
     ("cd3d_21_ragged", lambda: workloads.convdiff(21, (50.0, 30.0, 10.0)), 40, 160, 2, 50, True),
+    # sketches larger than the single-CTA QR's 512 threads (several rows per thread) and not multiples of the 32-row
+    # gather-list groups
+    ("cd2d_48_s600", lambda: workloads.convdiff(48, (20.0, 10.0)), 30, 600, 2, 30, True),
+    ("cd2d_48_s1000", lambda: workloads.convdiff(48, (20.0, 10.0)), 16, 1000, 2, 40, True),
 ]
 
 
