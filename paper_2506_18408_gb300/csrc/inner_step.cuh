@@ -832,7 +832,7 @@ static bool inner_step_v(const Plan& p, int i, const MT* val, bool last) {
 
 template <int NW, typename MT, typename VT, typename AT>
 static bool inner_step_nw(const Plan& p, int i, const MT* val, bool last) {
-    if (p.vec == 0) {  // length-binned SpMV: fused in FP32 only (FP64 measured slower fused: 399 vs 380 ms, Zipf 2M)
+    if (p.vec == 0) {  // length-binned SpMV: fused in FP32 only (FP64 measured slower fused: 353 vs 334 ms, Zipf 2M)
         if constexpr (sizeof(MT) == 8) return false;
         else return inner_step_v<0, 1, NW, MT, VT, AT>(p, i, val, last);
     }
