@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -513,12 +514,13 @@ def run_batch(args, dev, stream):
         abytes += alg_bytes_solve(int(A.sys_n[q]), sys_nnz[q], cfg.t, 4, 4, info["inner_steps_p"][p],
                                   info["outer_iters_p"][p])
     hbm, peak_src = _peaks()
-    # the plain FP64 solver on the same inputs, problem by problem, on a seeded sample of problems
+    # the plain FP64 solver on the same inputs, problem by problem, on a seeded simple random sample of problems;
+    # the batch total is extrapolated from the sample mean, with its standard error (finite-population corrected)
     rng = np.random.default_rng([0, workloads.STREAM_SAMPLE])
-    sample = sorted(rng.choice(P, size=16, replace=False).tolist())
+    sample = sorted(rng.choice(P, size=min(P, args.batch_sample), replace=False).tolist())
     blocks = workloads.split_blocks(A)
     sl = workloads.problem_slices(A.sys_n, cfg.nrhs)
-    t_plain = 0.0
+    t_each = []
     for p in sample:
         q, a0, nq = sl[p]
         Aq = blocks[q]
@@ -526,9 +528,13 @@ def run_batch(args, dev, stream):
                      max_outer=cfg.max_outer, stream=stream.cuda_stream)
         bq = bd[a0:a0 + nq].contiguous()
         tq, _ = _event_time(lambda: one.solve(bq, m=cfg.m, s=cfg.s, k=cfg.t, tol=cfg.tol), stream, 1, 1)
-        t_plain += tq
+        t_each.append(tq)
         one.close()
-    plain_est = t_plain * P / len(sample)
+    t_plain = float(sum(t_each))
+    ns = len(t_each)
+    plain_est = t_plain * P / ns
+    sd = statistics.stdev(t_each) if ns > 1 else 0.0
+    plain_se = P * sd / math.sqrt(ns) * math.sqrt(max(0.0, 1.0 - ns / P))
     return {"workload": "batch_512: 512 2D convection-diffusion systems, sides U{32..512}, beta~U(0,50)^2, "
                         "4 RHS ~N(0,1) each; m=40, k=2, s=160, FP32 inner + FP64 outer, tol 1e-8",
             "value": P / sec, "unit": "solves/s", "time_s": sec, "steps": args.batch_steps,
@@ -541,8 +547,9 @@ def run_batch(args, dev, stream):
                          "unit": "GB/s", "frac": abytes / sec / 1e9 / hbm, "peak_source": peak_src,
                          "counted": "per problem: inner steps (A in FP32, basis FP32), z = B y per cycle, outer "
                                     "steps (FP64 SpMV + CGS2)"},
-            "plain_fp64_per_problem": {"sample_problems": sample, "sample_s": t_plain,
-                                       "extrapolated_s": plain_est, "batched_speedup": plain_est / sec}}
+            "plain_fp64_per_problem": {"sample_size": ns, "sample_s": t_plain, "extrapolated_s": plain_est,
+                                       "extrapolated_stderr_s": plain_se, "batched_speedup": plain_est / sec,
+                                       "batched_speedup_stderr": plain_se / sec}}
 
 
 def _oracle_outer_iters():
@@ -618,6 +625,8 @@ def main():
     ap.add_argument("--no-others", action="store_true", help="skip the other workloads' lines")
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--batch-warmup", type=int, default=1)
+    ap.add_argument("--batch-sample", type=int, default=64,
+                    help="problems solved one by one with the plain FP64 solver for the batch's baseline")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
