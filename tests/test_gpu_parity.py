@@ -41,7 +41,7 @@ def test_sketch_pattern_bit_exact(n, s, zeta, seed):
     assert np.array_equal(signs.cpu().numpy(), s_ref)
 
 
-@pytest.mark.parametrize("n,s,zeta", [(4096, 120, 8), (70001, 400, 8), (5000, 64, 1)])
+@pytest.mark.parametrize("n,s,zeta", [(4096, 120, 8), (70001, 400, 8), (5000, 64, 1), (33333, 250, 16), (9000, 33, 3)])
 def test_sketch_apply(n, s, zeta):
     A = workloads.convdiff(n, (1.0,))
     sv = _solver(A, seed=5, zeta=zeta)
