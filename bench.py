@@ -206,12 +206,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         return
 
-    def timed(precision, K, W, profile=False):
+    def timed(precision, K, W, profile=0):
         solver.set("precision", precision)
         solver.set("profile", 0)
         for _ in range(W):
             solver.solve(bd, m=CFG.m, s=CFG.s, k=CFG.t, tol=CFG.tol, out=xd)
-        solver.set("profile", 1 if profile else 0)
+        solver.set("profile", int(profile))
         times, infos = [], []
         for _ in range(K):
             flush.zero_()
@@ -234,7 +234,10 @@ def run_ours(args):
         # the same solves with the kernels bracketed by CUDA events (event nodes in the captured graphs): the
         # per-launch duration of the fused inner kernel for the roofline.  The events lengthen the solve, so the
         # headline time comes from the unprofiled solves above.
-        tp, ip = timed("fp64", max(3, args.steps // 2), 1, profile=True)
+        tp, ip = timed("fp64", max(3, args.steps // 2), 1, profile=1)
+        # and with one pair of events around each full inner cycle's chain of m step launches: no event between two
+        # launches, so the span per launch includes the gaps between them but no event's own cost
+        ts, isp = timed("fp64", max(3, args.steps // 2), 1, profile=2)
     t32, i32 = timed("fp32", args.steps, max(3, args.warmup // 2))
     t16, i16 = timed("bf16", args.steps, max(3, args.warmup // 2))
     sec = max_over_ranks(dist, statistics.mean(t64), dev)
@@ -273,6 +276,8 @@ def run_ours(args):
         abytes = alg_bytes_inner_spmv(n, nnz, CFG.t, CFG.zeta, CFG.s, nblk, 8)
         tkey = "inner_spmv_fp64_cd3d_128"
     achieved = abytes / (k1_ms / 1e3) / 1e9
+    n_span = sum(i["n_step_span"] for i in isp)
+    span_ms = sum(i["t_step_span_ms"] for i in isp) / n_span if n_span else None
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -307,7 +312,13 @@ def run_ours(args):
                          "frac": achieved / hbm, "peak_source": peak_src, "traffic": traffic,
                          "alg_bytes_per_launch": abytes, "avg_launch_ms": k1_ms,
                          "launches_timed": int(sum(i["n_inner_spmv"] for i in ip)),
-                         "profiled_solve_s": statistics.mean(tp)},
+                         "profiled_solve_s": statistics.mean(tp),
+                         "cycle_span": None if span_ms is None else {
+                             "avg_launch_ms": span_ms, "launches_timed": int(n_span),
+                             "achieved": abytes / (span_ms / 1e3) / 1e9,
+                             "frac": abytes / (span_ms / 1e3) / 1e9 / hbm,
+                             "profiled_solve_s": statistics.mean(ts),
+                             "how": "events around each full cycle's m step launches; span / m"}},
             "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n},
             "batch": batch,

@@ -61,7 +61,9 @@ extern "C" {
 #define SFGMRES_OPT_C3 4             /* rule C3 (Eq. 5 bound stops the inner cycle): 1 = on (default), 0 = off */
 #define SFGMRES_OPT_MAX_OUTER 5      /* outer FGMRES iteration budget (default 50) */
 #define SFGMRES_OPT_SKETCH_KIND 6    /* 0 = sparse-sign (default), 1 = identity (requires s == n; tests) */
-#define SFGMRES_OPT_PROFILE 7        /* 1 = time the kernels with CUDA events (see sfgmres_stats), default 0 */
+#define SFGMRES_OPT_PROFILE 7        /* 1 = time the kernels with CUDA events around every launch, 2 = time each
+                                        inner cycle's chain of step launches with one pair of events (see
+                                        sfgmres_stats), default 0 */
 #define SFGMRES_OPT_SPMV_VECTOR 8    /* lanes per CSR row in the SpMV (2,4,8,16,32), or 0 (default) = chosen by the
                                         library: one thread per row when no row has more than 16 entries, else the
                                         length-binned SpMV (each row block's rows ordered by length: short rows one
@@ -143,6 +145,10 @@ typedef struct {
                                 norm, so this is also its relative residual) */
     double* inner_rho;       /* the sketched residual rho_k = ||S v_j - S A B_k y_k|| the cycle ended with, its
                                 estimate of ||r_hat_j|| (used by rule C3) */
+    /* with SFGMRES_OPT_PROFILE = 2 (otherwise 0), over the inner cycles whose m steps all built a basis vector, for
+       single-system solves that run each step as one launch: */
+    double t_step_span_ms;   /* device time from before the first step launch to after the last, summed */
+    int64_t n_step_span;     /* the step launches these spans hold */
 } sfgmres_stats;
 
 /* Filled by sfgmres_solve_batch when a non-NULL pointer is passed.  The arrays are caller-owned host arrays of

@@ -1025,13 +1025,16 @@ double ev_sum(const std::vector<EventPair>& pool, size_t base, size_t count) {
 int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const double* vscale, int vstride, int c3,
               double* z, size_t ev = SIZE_MAX, bool capturing = false) {
     launch_cycle_start(P, j, v, vscale, vstride, c3, h->cond_thr);
-    const bool prof = (ev != SIZE_MAX);
+    // profile 1: events around every inner-kernel launch; profile 2: one pair of events around the cycle's chain of
+    // step launches on the step stream (pair ev: before step 0, after step m - 1), nothing between the launches
+    const bool prof = (ev != SIZE_MAX) && h->profile == 1;
+    const bool span = (ev != SIZE_MAX) && h->profile == 2;
     h->step_fused = false;
     for (int i = 0; i < P.m; ++i) {
         const bool last = (i == P.m - 1);
         // right preconditioning: the step multiplies t_i = M^{-1} u_i (the passes return at once after a stop)
         if (P.ilu_host) launch_ilu_apply(P, i, (const double*)P.U + (int64_t)i * P.N, const_cast<double*>(P.xin));
-        if (prof) ev_rec(h->ev_spmv[ev + i].a, h->st, capturing);
+        if (prof || (span && i == 0)) ev_rec(h->ev_spmv[ev + i].a, h->st, capturing);
         const bool fused = launch_inner_step(P, i, last);  // one launch, timed as the inner kernel
         if (!fused) launch_inner_spmv(P, i);
         if (prof) ev_rec(h->ev_spmv[ev + i].b, h->st, capturing);
@@ -1040,6 +1043,7 @@ int run_cycle(sfgmres_ctx* h, const Plan& P, int j, const double* v, const doubl
             launch_inner_axpy(P, i, last);
             if (prof) ev_rec(h->ev_axpy[ev + i].b, h->st, capturing);
         }
+        if (span && last) ev_rec(h->ev_spmv[ev].b, h->st, capturing);
         h->step_fused |= fused;
         CK(cudaEventRecord(h->ev_c, h->st));
         CK(cudaStreamWaitEvent(h->qst, h->ev_c, 0));
@@ -1398,7 +1402,20 @@ int solve_single(sfgmres_t h, bool transpose, const double* b, const double* x0,
         float tms = 0.f;
         cudaEventElapsedTime(&tms, h->ev_t0, h->ev_t1);
         st->t_total_ms = tms;
-        if (h->profile) {
+        st->t_step_span_ms = 0.0;
+        st->n_step_span = 0;
+        if (h->profile == 2) {
+            // the cycles whose m step launches all built a basis vector, timed from before the first launch to after
+            // the last (fused single launches on the step stream only)
+            st->t_inner_spmv_ms = st->t_inner_axpy_ms = st->t_qr_ms = 0.0;
+            st->n_inner_spmv = st->n_inner_axpy = st->n_qr = 0;
+            if (h->step_fused && !P.ilu_host)
+                for (const auto& js : h->ev_steps) {
+                    if (js.first >= cnt || kh[js.first] != P.m) continue;
+                    st->t_step_span_ms += ev_sum(h->ev_spmv, js.second, 1);
+                    st->n_step_span += P.m;
+                }
+        } else if (h->profile) {
             // the launches of inner steps i < k_j of each outer step j (those that built a basis vector); the
             // launches after the cycle stopped only read the stop flag and return
             st->t_inner_spmv_ms = st->t_inner_axpy_ms = st->t_qr_ms = 0.0;
@@ -1640,7 +1657,7 @@ int sfgmres_set_option(sfgmres_t h, int32_t key, double v) {
             h->kind = iv;
             return 0;
         case SFGMRES_OPT_PROFILE:
-            if (iv != 0 && iv != 1) return fail(h, SFGMRES_ERR_INVALID_ARG, "profile must be 0 or 1");
+            if (iv < 0 || iv > 2) return fail(h, SFGMRES_ERR_INVALID_ARG, "profile must be 0, 1 or 2");
             h->profile = iv;
             return 0;
         case SFGMRES_OPT_SPMV_VECTOR:
@@ -2298,6 +2315,8 @@ int sfgmres_solve_multilevel(sfgmres_t h, const double* b, const double* x0, dou
         st->t_total_ms = tms;
         st->t_inner_spmv_ms = st->t_inner_axpy_ms = st->t_qr_ms = 0.0;
         st->n_inner_spmv = st->n_inner_axpy = st->n_qr = 0;
+        st->t_step_span_ms = 0.0;
+        st->n_step_span = 0;
     }
     return status;
 }

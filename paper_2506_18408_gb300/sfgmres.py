@@ -44,7 +44,8 @@ class Stats(C.Structure):
                 ("t_inner_spmv_ms", C.c_double), ("n_inner_spmv", C.c_int64), ("t_inner_axpy_ms", C.c_double),
                 ("n_inner_axpy", C.c_int64), ("t_qr_ms", C.c_double), ("n_qr", C.c_int64),
                 ("t_total_ms", C.c_double), ("inner_res", C.POINTER(C.c_double)),
-                ("inner_rho", C.POINTER(C.c_double))]
+                ("inner_rho", C.POINTER(C.c_double)), ("t_step_span_ms", C.c_double),
+                ("n_step_span", C.c_int64)]
 
 
 class BatchStats(C.Structure):
@@ -343,7 +344,7 @@ class Solver:
                 "kernel_launches": st.kernel_launches, "t_total_ms": st.t_total_ms,
                 "t_inner_spmv_ms": st.t_inner_spmv_ms, "n_inner_spmv": st.n_inner_spmv,
                 "t_inner_axpy_ms": st.t_inner_axpy_ms, "n_inner_axpy": st.n_inner_axpy, "t_qr_ms": st.t_qr_ms,
-                "n_qr": st.n_qr}
+                "n_qr": st.n_qr, "t_step_span_ms": st.t_step_span_ms, "n_step_span": st.n_step_span}
         return out, info
 
     def solve_batch(self, b, x0=None, *, nrhs: int, m: int, s: int, k: int, tol: float = 1e-8, out=None,

@@ -251,6 +251,33 @@ def test_profiled_solves_time_the_working_launches_with_and_without_graphs():
             assert 0.0 < info["t_%s_ms" % key] < info["t_total_ms"]
 
 
+def test_cycle_span_profile_times_full_cycles_only():
+    """Profile mode 2 records one pair of events around each inner cycle's chain of m step launches: the solve is
+    bit for bit the unprofiled one (graphs captured, replayed, and off), the spans cover exactly the cycles whose m
+    steps all built a basis vector, and their sum lies inside the solve's time."""
+    from paper_2506_18408_gb300 import Solver
+
+    mat = workloads.convdiff(64, (20.0, 10.0))
+    bd = dev_vec(workloads.rhs(mat.n, seed=0))
+    sv = Solver(mat.n, mat.row_ptr, mat.col, mat.val, sketch_seed=1, max_outer=80)
+    x_ref, info_ref = sv.solve(bd, m=10, s=60, k=2, tol=1e-8)
+    assert info_ref["status"] == 0 and info_ref["n_step_span"] == 0
+    full = sum(1 for k in info_ref["inner_k"] if k == 10)
+    assert full > 0
+    for graph in (1, 1, 0):
+        sv.set("graph", graph)
+        sv.set("profile", 2)
+        x, info = sv.solve(bd, m=10, s=60, k=2, tol=1e-8)
+        sv.set("profile", 0)
+        assert info["status"] == 0
+        assert np.array_equal(x.cpu().numpy(), x_ref.cpu().numpy())
+        assert info["inner_k"] == info_ref["inner_k"]
+        assert info["n_step_span"] == 10 * full
+        assert info["n_inner_spmv"] == 0
+        assert 0.0 < info["t_step_span_ms"] < info["t_total_ms"]
+    sv.close()
+
+
 def test_fused_inner_step_matches_the_two_kernel_step():
     """One launch per inner step (the inner SpMV kernel's work, a grid-wide arrival, then the Arnoldi update of the
     CTA's own rows) runs the same arithmetic in the same order as the two kernels: FP64 and FP32-inner solves agree
