@@ -23,6 +23,13 @@ __device__ __forceinline__ bool cycle_idle(const Plan& P, int p, int i) {
 }
 
 __device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// The one-thread-per-row SpMVs request into L2, this many row groups (CTA-wide rounds of rows) ahead, the line of x
+// that holds each row's own entry (the diagonal's column).  A block's first rows are otherwise first fetched from
+// HBM by the row's own gather (no earlier block has touched them: with a banded matrix the rows of the block below
+// read them only as their far band, later in the launch), so the lines come in a round trip later than the rest.
+constexpr int kXPrefetchAhead = 2;
 
 // ---------------------------------------------------------------------------------------------------------------
 // Entries pk .. pk+CNT-1 of the thread's row in the SELL-32 copy (cp, vp: the lane's first entry; consecutive
@@ -81,6 +88,8 @@ __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ sof
             o1n = __ldg(soff + sid + 1);
             rln = __ldg(slen + (int64_t)sid * 32 + lane);
         }
+        const int kp = k + kXPrefetchAhead * (int)blockDim.x;
+        if (kp < len) prefetch_l2(xg + v0 + kp);  // x of the row's own column, kXPrefetchAhead row groups ahead
         const int w = o1 - o0;
         // every 128-byte line of the slice's columns and values requested at once (one line per lane; w <= 16
         // entries, so at most 32 lines of FP64 values): the later chunks' loads then find their lines in flight
@@ -147,6 +156,8 @@ __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ r
             an = __ldg(rpm + kn);
             rln = __ldg(rpm + kn + 1) - an;
         }
+        const int kp = k + kXPrefetchAhead * (int)blockDim.x;
+        if (kp < len) prefetch_l2(xg + v0 + kp);  // x of the row's own column, kXPrefetchAhead row groups ahead
         const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)rl);
         AT sum = AT(0);
         for (int pk = 0; pk < maxlen; pk += 4) {
