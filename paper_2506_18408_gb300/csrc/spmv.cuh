@@ -247,23 +247,4 @@ __device__ __forceinline__ void spmv_rows_to_smem(const int* __restrict__ rp, co
         default: { constexpr int VV = 32, UU = 2; CALL; } break; \
     }
 
-// Sum over the block with few floating-point instructions: every thread's value goes to shared memory, then one
-// warp adds 16 values per lane in a fixed order and finishes with a shuffle tree.  Result valid in every thread.
-// `red` holds blockDim.x values (blockDim.x <= 1024, a multiple of 32).
-template <typename T>
-__device__ __forceinline__ T block_sum_lean(T v, T* red) {
-    __syncthreads();
-    red[threadIdx.x] = v;
-    __syncthreads();
-    __shared__ T res;
-    if (threadIdx.x < 32) {
-        T acc = T(0);
-        for (int q = threadIdx.x; q < (int)blockDim.x; q += 32) acc += red[q];
-        acc = warp_sum(acc);
-        if (threadIdx.x == 0) res = acc;
-    }
-    __syncthreads();
-    return res;
-}
-
 }  // namespace sfg
