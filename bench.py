@@ -6,10 +6,11 @@ nnz = 14,581,760; beta = (50, 30, 10); b ~ N(0,1) seed 0; inner m = 100, truncat
 nonzeros per column, seed 1; tol 1e-8), with b and A resident in HBM.  The headline is the plain FP64 solver; the
 FP32-inner and BF16-basis forms are reported beside it on the same inputs.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--profile-case [cd3d_128|zipf_2m|qr_cd3d]]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--profile-case [cd3d_128|zipf_2m|qr_cd3d|cd2d_64]]
 
 ``--impl reference`` times the CPU oracle (plain FP64 NumPy/SciPy restatement of the method) on a bounded sample
-of the same workload.  ``--profile-case`` runs two short solves for ncu captures and prints nothing else.
+of the same workload.  ``--profile-case`` runs short solves for ncu captures and prints nothing else.
 """
 from __future__ import annotations
 
@@ -188,6 +189,19 @@ def run_ours(args):
             zs.solve(zb, m=20, s=zc.s, k=zc.t, tol=zc.tol)
         torch.cuda.synchronize()
         zs.close()
+        return
+    if args.profile_case == "cd2d_64":
+        # the small 2D workload (latency bound): one warm-up solve (sketch lists, graphs), then one full FP64 solve
+        solver.close()
+        sc = workloads.CONFIGS["cd2d_64"]
+        S2 = sc.build_matrix()
+        sb = torch.from_numpy(sc.build_rhs(S2.n)).to(dev)
+        ss = Solver(S2.n, S2.row_ptr, S2.col, S2.val, sketch_seed=sc.sketch_seed, zeta=sc.zeta, max_outer=sc.max_outer,
+                    stream=stream.cuda_stream)
+        for _ in range(2):
+            ss.solve(sb, m=sc.m, s=sc.s, k=sc.t, tol=sc.tol)
+        torch.cuda.synchronize()
+        ss.close()
         return
     if args.profile_case == "qr_cd3d":
         # one full inner cycle (m = 100, C3 off: sketched-QR updates i = 0..99) of the same workload
@@ -636,8 +650,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile-case", nargs="?", const="cd3d_128", default=None,
-                    help="short solves for ncu captures: cd3d_128 (default), zipf_2m, or qr_cd3d (one inner cycle "
-                         "of m = 100)")
+                    help="short solves for ncu captures: cd3d_128 (default), zipf_2m, qr_cd3d (one inner cycle "
+                         "of m = 100), or cd2d_64 (two full solves of the small 2D workload)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve line")
     ap.add_argument("--no-others", action="store_true", help="skip the other workloads' lines")
