@@ -29,7 +29,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefe
 // that holds each row's own entry (the diagonal's column).  A block's first rows are otherwise first fetched from
 // HBM by the row's own gather (no earlier block has touched them: with a banded matrix the rows of the block below
 // read them only as their far band, later in the launch), so the lines come in a round trip later than the rest.
-constexpr int kXPrefetchAhead = 2;
+// One group ahead measured best (128^3 FP64 solve: 46.0 ms, against 46.7 ms two groups and 46.8 ms three ahead).
+constexpr int kXPrefetchAhead = 1;
 
 // ---------------------------------------------------------------------------------------------------------------
 // Entries pk .. pk+CNT-1 of the thread's row in the SELL-32 copy (cp, vp: the lane's first entry; consecutive
@@ -89,7 +90,7 @@ __device__ __forceinline__ int spmv_dots_sell(int N, const int* __restrict__ sof
             rln = __ldg(slen + (int64_t)sid * 32 + lane);
         }
         const int kp = k + kXPrefetchAhead * (int)blockDim.x;
-        if (kp < len) prefetch_l2(xg + v0 + kp);  // x of the row's own column, kXPrefetchAhead row groups ahead
+        if (kp < len) prefetch_l2(xg + v0 + kp);  // x of the row's own column, kXPrefetchAhead row group(s) ahead
         const int w = o1 - o0;
         // every 128-byte line of the slice's columns and values requested at once (one line per lane; w <= 16
         // entries, so at most 32 lines of FP64 values): the later chunks' loads then find their lines in flight
@@ -157,7 +158,7 @@ __device__ __forceinline__ int spmv_dots_scalar(int N, const int* __restrict__ r
             rln = __ldg(rpm + kn + 1) - an;
         }
         const int kp = k + kXPrefetchAhead * (int)blockDim.x;
-        if (kp < len) prefetch_l2(xg + v0 + kp);  // x of the row's own column, kXPrefetchAhead row groups ahead
+        if (kp < len) prefetch_l2(xg + v0 + kp);  // x of the row's own column, kXPrefetchAhead row group(s) ahead
         const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)rl);
         AT sum = AT(0);
         for (int pk = 0; pk < maxlen; pk += 4) {
