@@ -78,7 +78,7 @@ extern "C" {
                                         FGMRES update) is captured once into a CUDA graph and replayed; the graphs
                                         are kept while the solve's parameters and workspaces stay the same.  0: the
                                         kernels are launched one by one.  Results are identical either way.
-                                        With SFGMRES_OPT_PROFILE = 1 the timing events are part of the graphs. */
+                                        With SFGMRES_OPT_PROFILE = 1 or 2 the timing events are part of the graphs. */
 /* (keys 11 and 12 are not used) */
 #define SFGMRES_OPT_FUSED_STEP 13    /* 1 (default): where all row blocks of a plan fit on the GPU at once (one system
                                         of up to about 2 x SMs blocks), the truncation window is at most 4 and the

@@ -263,7 +263,9 @@ class Solver:
 
     ``row_ptr``/``col``/``val`` may be NumPy arrays (host; copied by the library) or CUDA tensors (int64, int32,
     float64).  ``options`` are set through :meth:`set` (``precision`` in {"fp64","fp32","bf16"}, ``zeta``,
-    ``cond_threshold``, ``c3``, ``max_outer``, ``sketch_kind`` in {"sparse_sign","identity"}, ``profile``,
+    ``cond_threshold``, ``c3``, ``max_outer``, ``sketch_kind`` in {"sparse_sign","identity"}, ``profile`` (0; 1 =
+    events around every kernel launch, reported as ``t_inner_spmv_ms`` etc.; 2 = events around each full inner
+    cycle's chain of step launches, reported as ``t_step_span_ms`` / ``n_step_span``),
     ``spmv_vector``).
     """
 
